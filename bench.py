@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the inpainting hot path on GB300.
+
+A step is one whole inpainting of a synthetic layered-motion clip through the
+C ABI (vi_upload + vi_run + vi_fetch_result): pyramid and features, shift-map
+initialisation, onion-peel initialisation, per level the PatchMatch search
+and reconstruction until the stopping rule, level transitions and the final
+best-patch step. Default workload: 320x240 px x 60 frames RGB, 3 sprites,
+8% occlusion tube, 4 levels, colour + 2 texture channels, FP32 storage.
+
+Output: one JSON line (rank 0). `value` is patch-distance evaluations per
+second over the whole job (all ranks), inputs resident in device memory when
+the timed region starts. `e2e` is the same metric through the same calls with
+host buffers (host->device upload and device->host fetch inside the timed
+region). `roofline` is the PatchMatch step kernel's algorithmic gather bytes
+(125 voxels x C channels x 4 bytes per evaluation) over its CUDA-event time,
+against the measured HBM copy bandwidth. `cpu_baseline` times the CPU oracle
+(sequential PatchMatch, one thread) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): replicas only -- each rank inpaints its own clip; no
+collective on the data path; barrier + max-over-ranks timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "patch-distance evals/s (and inpainted voxels/s) vs HBM roofline"
+UNIT = "evals/s"
+WORKLOAD = "layered_320x240x60"
+BYTES_PER_EVAL_FP32_C5 = 125 * 5 * 4      # algorithmic gather of one source patch
+
+# dram bytes (read + write) per launch of the PatchMatch step kernel and the
+# evaluations of that launch, from one ncu capture (see profiles/); None when
+# the kernel changed since the capture.
+NCU_STEP_TRAFFIC = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id=None):
+        self.proc = None
+        self.device_id = device_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_clip(rank):
+    from paper_1503_05528_gb300 import synth
+    # weak scaling: every rank inpaints its own clip of the same size
+    return synth.layered_clip(320, 240, 60, 3, (20, 50), 0.08, 4, synth.BASE_SEED + 2 + rank,
+                              name=WORKLOAD)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline field and the --impl reference arm)
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Level-0 state of the workload for timing the oracle's PatchMatch:
+    the oracle's own pyramid level, occluded voxels set to mid-grey, a random
+    shift map from the oracle's initialisation."""
+
+    def __init__(self, clip):
+        import numpy as np
+        from oracle import oracle as O
+        self.O = O
+        lv = O.build_pyramid(clip.rgb, clip.mask, clip.levels, True)[0]
+        lv.x[lv.hole == 1] = 0.5
+        lv.phi = O.init_nnf(lv.htilde, lv.dtilde, (1503, 0), O.tag(O.PURPOSE_INIT, 0))
+        lv.d2 = np.full(lv.hole.shape, np.inf, np.float32)
+        self.lv = lv
+        self.T = lv.hole.shape[0]
+        self.next_t = 2
+
+    def slab(self, frames):
+        """One ANN search (rescore + 10 sequential PatchMatch iterations,
+        Algorithm 1 as printed) over the targets of `frames` consecutive frames.
+        Returns (evals, seconds)."""
+        import numpy as np
+        lv = self.lv
+        t0 = self.next_t
+        self.next_t = 2 + (self.next_t - 2 + frames) % max(self.T - 4 - frames, 1)
+        tgt = np.zeros_like(lv.htilde)
+        tgt[t0:t0 + frames] = lv.htilde[t0:t0 + frames]
+        phi = lv.phi.copy()
+        d2 = lv.d2.copy()
+        s = time.perf_counter()
+        ev = self.O.ann(lv.x, tgt, lv.dtilde, phi, d2, n_pm=10, schedule="SEQ", key=(1503, 0),
+                        tag_base=self.O.tag(self.O.PURPOSE_SEARCH, 0, 0))
+        return ev, time.perf_counter() - s
+
+
+def cpu_baseline(clip, seconds):
+    smp = OracleSample(clip)
+    evals, el, frames = 0, 0.0, 0
+    while el < seconds:
+        ev, dt = smp.slab(2)
+        evals += ev
+        el += dt
+        frames += 2
+    return {"value": evals / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"sequential ANN search (rescore + 10 PatchMatch iterations) over the "
+                      f"level-0 targets of {frames} frames of {WORKLOAD}: {evals} evaluations "
+                      f"in {el:.1f} s, one thread"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    clip = make_clip(0)
+    smp = OracleSample(clip)
+    frames = 2
+    for _ in range(args.warmup):
+        smp.slab(frames)
+    evals, el = 0, 0.0
+    for _ in range(args.steps):
+        ev, dt = smp.slab(frames)
+        evals += ev
+        el += dt
+    value = evals / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{frames} frames per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: sequential ANN search over the level-0 "
+                                       f"targets of {frames} frames of {WORKLOAD}, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1503_05528_gb300 import vi
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vi.load(build_if_missing=True)
+    clip = make_clip(rank)
+    rgb_d = torch.from_numpy(clip.rgb).cuda()
+    mask_d = torch.from_numpy(clip.mask).cuda()
+    out_d = torch.empty_like(rgb_d)
+    stream = torch.cuda.current_stream()
+    ctx = vi.Context(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank,
+                     stream=stream.cuda_stream)
+    n_hole = int(clip.mask.sum())
+
+    def step():
+        ctx.upload(rgb_d, mask_d)
+        ctx.run()
+        ctx.fetch_result(out_d)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.profile(True)
+    s0 = ctx.stats()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    s1 = ctx.stats()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1)
+    evals = s1["evals"] - s0["evals"]
+    step_evals = s1["step_evals"] - s0["step_evals"]
+    step_ms = s1["step_ms"] - s0["step_ms"]
+    step_launches = s1["step_timed"] - s0["step_timed"]
+    launches = s1["launches"] - s0["launches"]
+    outer = s1["outer"]
+
+    # end to end through host buffers: upload from pinned memory, fetch to host
+    rgb_h = torch.from_numpy(clip.rgb).pin_memory()
+    mask_h = torch.from_numpy(clip.mask).pin_memory()
+    out_h = torch.empty_like(rgb_h).pin_memory()
+    ctx.upload(rgb_h.numpy(), mask_h.numpy())
+    ctx.run()
+    ctx.fetch_result(out_h.numpy())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    se = ctx.stats()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.upload(rgb_h.numpy(), mask_h.numpy())
+        ctx.run()
+        ctx.fetch_result(out_h.numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    e2e_evals = ctx.stats()["evals"] - se["evals"]
+
+    vals = torch.tensor([ms, float(evals), float(n_hole), e2e_s, float(e2e_evals)], dtype=torch.float64,
+                        device="cuda")
+    if dist:
+        mx = vals.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = vals.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_max, evals_tot, hole_tot = mx[0].item(), sm[1].item(), sm[2].item()
+        e2e_max, e2e_evals_tot = mx[3].item(), sm[4].item()
+    else:
+        ms_max, evals_tot, hole_tot = ms, float(evals), float(n_hole)
+        e2e_max, e2e_evals_tot = e2e_s, float(e2e_evals)
+    ctx.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    achieved = step_evals * BYTES_PER_EVAL_FP32_C5 / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    traffic = None
+    if NCU_STEP_TRAFFIC and step_launches:
+        per_eval = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["evals"]
+        traffic = per_eval * step_evals / step_launches
+    line = {
+        "metric": METRIC, "value": evals_tot / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "levels": clip.levels, "channels": 5, "storage": "fp32",
+                   "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
+        "inpainted_voxels_per_s": hole_tot * args.steps / (ms_max / 1e3),
+        "evals_per_step": evals / args.steps,
+        "outer_iterations_per_level": outer[:clip.levels],
+        "roofline": {"bound": "hbm", "kernel": "k_ann_step (PatchMatch propagation + random search)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                     "traffic": traffic, "bytes_per_eval": BYTES_PER_EVAL_FP32_C5,
+                     "launches_timed": step_launches,
+                     "evals_per_launch": step_evals / step_launches if step_launches else None,
+                     "kernel_ms_share": step_ms / ms if ms > 0 else None},
+        "e2e": {"value": e2e_evals_tot / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": int(clip.rgb.nbytes + clip.mask.nbytes),
+                "d2h_bytes_per_step": int(clip.rgb.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(clip, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

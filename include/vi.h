@@ -1,0 +1,240 @@
+/*
+ * vi.h -- C ABI of the GB300 video-inpainting library.
+ *
+ * The library runs the per-pyramid-level hot path of the global patch-based
+ * video inpainting method of Newson, Almansa, Fradet, Gousseau and Perez,
+ * "Video Inpainting of Complex Scenes" (SIAM J. Imaging Sciences 7(4), 2014;
+ * arXiv:1503.05528), Algorithm 4 without the affine realignment of
+ * Algorithm 2: pyramids and texture features (Sec. 3.3, Eq. 7, Eq. 8), shift-
+ * map initialisation, onion-peel initialisation (Sec. 3.5, Algorithm 3),
+ * spatio-temporal PatchMatch (Sec. 3.1, Algorithm 1, Eq. 2, Eq. 3, Eq. 7b),
+ * weighted reconstruction (Sec. 3.2, Eq. 4, Eq. 5, Eq. 9), level transition
+ * (Sec. 3.6), final best-patch reconstruction (Eq. 6), energy (Eq. 1) and the
+ * stopping rule (Sec. 3.7). Every step runs in CUDA kernels for sm_103a.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a vi_status; no exception crosses the ABI. On error
+ *    vi_last_error() returns a message for the context.
+ *  - Videos are float32 [T][H][W][3] (frame, row, column, RGB), values in [0, 1].
+ *    Masks are uint8 [T][H][W], 1 = occluded (the set H of Sec. 2), 0 = known.
+ *    Level l of the pyramid is ceil(W/2^l) x ceil(H/2^l) x T; level 0 is the
+ *    input resolution (the paper's finest level).
+ *  - Channels at a level are float32 [T][H][W][C]: R, G, B and, when texture
+ *    features are on (C = 5), sqrt(lambda) T_x and sqrt(lambda) T_y, so that the
+ *    distance of Eq. 7b is a plain sum of squares over C channels.
+ *  - Shift maps are int32 [T][H][W][3] (dx, dy, dt): the correspondent of p is
+ *    p + phi(p) (Sec. 2). Distances d2 are float32 [T][H][W], the squared patch
+ *    distance d^2 of Eq. 2 / Eq. 7b. Both are meaningful on the target set H~
+ *    (the dilated occlusion) only.
+ *  - Pointers named *host* or taking ptr_is_device = 0 are host memory; with
+ *    ptr_is_device = 1 they are device memory of the context's device. The
+ *    caller owns every buffer it passes; the library copies what it keeps.
+ *    The context owns all device state until vi_ctx_destroy.
+ *  - Calls are ordered on the context's stream. Calls that return data to a
+ *    host pointer synchronise that stream; the others are asynchronous unless
+ *    stated otherwise.
+ *  - A context is used by one thread at a time.
+ *  - Limits: W, H, T <= 32767; W*H*T < 2^31; rho a power of two (1/2^m, m >= 1).
+ */
+#ifndef VI_H
+#define VI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vi_ctx vi_ctx;
+
+typedef enum {
+    VI_OK = 0,
+    VI_ERR_ARG = 1,        /* invalid argument (null pointer, size, level, config) */
+    VI_ERR_OOM = 2,        /* device or host allocation failed */
+    VI_ERR_CUDA = 3,       /* a CUDA call failed; vi_last_error() has the text */
+    VI_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+    VI_ERR_NO_SOURCE = 5,  /* D~ is empty at some level: nothing to copy from */
+    VI_ERR_STATE = 6,      /* call out of order (e.g. iterate before upload) */
+    VI_ERR_NO_DEVICE = 7   /* no CUDA device is available */
+} vi_status;
+
+/* Parameters of the method (Sec. 3.7 gives the paper's values). */
+typedef struct {
+    float lambda;        /* texture-feature weight of Eq. 7b (paper: 50) */
+    int n_pm;            /* PatchMatch iterations per ANN search, Algorithm 1 (10) */
+    float rho;           /* random-search radius factor of Eq. 3 (0.5); 1/2^m only */
+    int levels;          /* pyramid levels L >= 1 (0: choose by the rule of Sec. 3.6) */
+    int max_outer;       /* cap on search/reconstruction iterations per level (20) */
+    float stop;          /* threshold on e, the mean absolute colour change per
+                            channel and voxel of H between iterations (0.1/255) */
+    int weighted;        /* 1: weights of Eq. 5; 0: the unweighted mean (s = 1) */
+    int use_texture;     /* 1: C = 5 channels (Sec. 3.3); 0: RGB only (C = 3) */
+    int storage;         /* 0: FP32 channel storage (the only value accepted) */
+    uint64_t seed;       /* Philox4x32-10 key (key words: low, high 32 bits) */
+    uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
+} vi_config;
+
+/* Per-context counters. evals, step_*: since vi_ctx_create; outer and
+ * onion_layers: since the last vi_upload. */
+typedef struct {
+    unsigned long long evals;          /* patch-distance evaluations (Eq. 2 / 7b / 11) */
+    unsigned long long step_evals;     /* those made inside the PatchMatch step kernel */
+    unsigned long long step_launches;  /* launches of the PatchMatch step kernel */
+    double step_ms;                    /* device time of those launches (profiling on) */
+    unsigned long long step_timed;     /* launches included in step_ms */
+    int outer[16];                     /* search/reconstruction iterations run per level */
+    int onion_layers;                  /* layers peeled by the initialisation */
+    int levels;                        /* levels of the current pyramid */
+    unsigned long long launches;       /* kernels launched by the library in this
+                                          process, all contexts together */
+} vi_stats;
+
+/* Fills cfg with the paper's parameters (Sec. 3.7), L = 0 (automatic), FP32,
+ * texture features on, seed 1503. */
+void vi_config_default(vi_config *cfg);
+
+/* Creates a context on the current CUDA device. cuda_stream is a cudaStream_t
+ * to order work on, or NULL for a stream the context creates and owns.
+ * Errors: VI_ERR_ARG (bad config), VI_ERR_NO_DEVICE, VI_ERR_CUDA. */
+vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out);
+
+/* Releases every device buffer and the owned stream. NULL is ignored. */
+void vi_ctx_destroy(vi_ctx *ctx);
+
+/* Message of the last failed call on ctx ("" if none). Valid until the next call. */
+const char *vi_last_error(const vi_ctx *ctx);
+
+/* The number of levels the rule of Sec. 3.6 picks for a mask: the smallest L
+ * such that the largest per-frame occlusion extent (width or height of its
+ * bounding box) divided by 2^(L-1) is at most 9, just under twice the patch
+ * size of 5, keeping the coarsest frame side >= 16 px. Host-only. */
+int vi_auto_levels(const uint8_t *mask_host, int W, int H, int T);
+
+/* Device bytes a context will hold for a W x H x T clip with the given
+ * number of occluded voxels (an upper bound used for admission). */
+size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long hole_voxels);
+
+/* Copies a video and its occlusion mask into the context and allocates the
+ * pyramid. rgb: [T][H][W][3] float32; mask: [T][H][W] uint8. Values of rgb
+ * under the mask are never read. Replaces any previous upload.
+ * Errors: VI_ERR_ARG (sizes, null), VI_ERR_OOM, VI_ERR_CUDA. */
+vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                    int ptr_is_device);
+
+/* Algorithm 4, first three lines: the texture features at full resolution
+ * (Eq. 7: mean over a square of side 2^(L-1) of the absolute central
+ * differences of the grey level), the colour and occlusion pyramids (2x2
+ * spatial means of known children, occlusion by OR, no temporal subsampling,
+ * Sec. 3.6), the texture pyramid by subsampling (Eq. 8), and per level the
+ * sets H~ and D~ of Sec. 2 with their raster-ordered voxel lists.
+ * Errors: VI_ERR_STATE (no upload), VI_ERR_NO_SOURCE, VI_ERR_CUDA. */
+vi_status vi_build_pyramid(vi_ctx *ctx);
+
+/* Shift-map initialisation (Sec. 3.1; Algorithm 4, "phi^L <- Random"): every
+ * voxel of H~ at the level takes a source drawn uniformly from D~.
+ * Errors: VI_ERR_ARG (level), VI_ERR_STATE, VI_ERR_CUDA. */
+vi_status vi_init_nnf(vi_ctx *ctx, int level);
+
+/* Onion-peel initialisation at the coarsest level (Sec. 3.5, Algorithm 3):
+ * layer by layer, the voxels of H' not kept by a 3x3x3 erosion are inpainted
+ * from the patches that meet them and are centred outside H' (Eq. 10-12),
+ * after an ANN search with the partial distance of Eq. 11.
+ * Synchronises the stream once per layer. Errors: VI_ERR_STATE, VI_ERR_CUDA. */
+vi_status vi_onion_peel(vi_ctx *ctx);
+
+/* vi_build_pyramid + vi_init_nnf(levels-1) + vi_onion_peel. */
+vi_status vi_prepare(vi_ctx *ctx);
+
+/* Distances of every voxel of H~ at the level to its current correspondent
+ * (d2 = d^2(W_p, W_{p+phi(p)}), Eq. 2 / 7b). */
+vi_status vi_rescore(vi_ctx *ctx, int level);
+
+/* One ANN search (Algorithm 1) at the level: vi_rescore, then n_pm
+ * iterations of propagation and random search with the parallel (Jacobi)
+ * schedule: in iteration k every target reads its neighbours' shifts as they
+ * were when iteration k began; neighbours -e_x, -e_y, -e_t on even k, +e_x,
+ * +e_y, +e_t on odd k; a candidate replaces the current shift only if it is
+ * in D~ and strictly closer. The random candidate of iteration k is
+ * p + phi(p) + floor(r_max rho^k delta) (Eq. 3), r_max the largest dimension
+ * of the level and delta from Philox4x32-10 with counter (voxel index,
+ * 0x2 << 28 | level << 24 | call << 8 | k, clip, 0). */
+vi_status vi_ann(vi_ctx *ctx, int level, int call);
+
+/* Reconstruction (Eq. 4, Eq. 5, and Eq. 9 for the texture channels) of every
+ * occluded voxel at the level from the current shift map and distances:
+ * sigma_p^2 is the 75th percentile (nearest rank) of the d2 of the patches
+ * containing p. e_host (nullable) receives e = sum |u_new - u_old| over the
+ * occluded voxels and the 3 colour channels / (3 |H|); a non-null e_host
+ * synchronises the stream. */
+vi_status vi_reconstruct(vi_ctx *ctx, int level, float *e_host);
+
+/* The inner loop of Algorithm 4 at one level: repeat vi_ann + vi_reconstruct.
+ * n_outer >= 0 runs exactly that many iterations; n_outer < 0 applies the
+ * stopping rule of Sec. 3.7 (stop when e <= cfg.stop or after cfg.max_outer
+ * iterations; synchronises once per iteration). n_done_host and e_last_host
+ * are nullable. The call index of the k-th iteration is first_call + k. */
+vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n_done_host,
+                     float *e_last_host);
+
+/* Level transition (Sec. 3.6; Algorithm 4): the shift map of `level` is
+ * upsampled to level-1 by nearest neighbour with its spatial components
+ * doubled; shifts that leave D~ are redrawn uniformly (Philox purpose 3);
+ * the occluded voxels of level-1 first take their coarse parent's values, then
+ * distances are computed and level-1 is reconstructed with Eq. 4/5/9. */
+vi_status vi_next_level(vi_ctx *ctx, int level);
+
+/* Final reconstruction at level 0 (Eq. 6): each occluded voxel takes the
+ * value of its best contributor u(p + phi(q*)), q* = argmin over the patches
+ * containing p of the current d2 (ties: first in dt, dy, dx order). */
+vi_status vi_final(vi_ctx *ctx);
+
+/* The whole method after vi_upload: vi_prepare, then for every level from
+ * the coarsest: vi_iterate with the stopping rule and vi_next_level, and
+ * vi_final at level 0. */
+vi_status vi_run(vi_ctx *ctx);
+
+/* Energy of Eq. 1 at the level for the current channels and shift map:
+ * E_H = sum over H of d^2 and E_H~ = the same sum over H~ (FP32 distances,
+ * FP64 sums). Synchronises. Either output may be NULL. */
+vi_status vi_energy(vi_ctx *ctx, int level, double *E_H_host, double *E_Ht_host);
+
+/* Sizes of a level: dims, channels, |H|, |H~| and |D~|. Outputs nullable. */
+vi_status vi_level_info(vi_ctx *ctx, int level, int *W, int *H, int *T, int *C,
+                        long long *n_hole, long long *n_target, long long *n_source);
+
+/* Channels of a level, float32 [T][H][W][C] (C from vi_level_info). */
+vi_status vi_get_channels(vi_ctx *ctx, int level, float *out, int ptr_is_device);
+vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_device);
+
+/* Shift map (int32 [T][H][W][3]) and distances (float32 [T][H][W]) of a level;
+ * entries outside H~ read as 0 / +inf and are ignored on set. Host memory.
+ * Either pointer may be NULL. */
+vi_status vi_get_nnf(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host);
+vi_status vi_set_nnf(vi_ctx *ctx, int level, const int32_t *phi_host, const float *d2_host);
+
+/* Per-voxel set codes of a level, uint8 [T][H][W]: bit 0 occluded (H),
+ * bit 1 target (H~), bit 2 source (D~). Host memory. */
+vi_status vi_get_masks(vi_ctx *ctx, int level, uint8_t *code_host);
+
+/* Squared patch distances (Eq. 2 / 7b) at a level for n (target, source)
+ * pairs given as int32 [n][6] = (px, py, pt, sx, sy, st) in host memory;
+ * +inf where the source patch leaves the video. out_host: float32 [n]. */
+vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n, float *out_host);
+
+/* The inpainted video (level-0 colour), float32 [T][H][W][3]. Known voxels
+ * are the input values. Synchronises when out is host memory. */
+vi_status vi_fetch_result(vi_ctx *ctx, float *rgb_out, int ptr_is_device);
+
+/* Device-time profiling of the PatchMatch step kernel: with enable = 1 every
+ * launch is bracketed by CUDA events on the context's stream. */
+vi_status vi_profile(vi_ctx *ctx, int enable);
+
+/* The context's counters (synchronises to read event times). */
+vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VI_H */

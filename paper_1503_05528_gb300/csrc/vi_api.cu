@@ -1,0 +1,1068 @@
+// vi_api.cu -- host runtime and C ABI of the library (declared in vi.h).
+//
+// A context owns one clip: its input copy, the per-level device buffers of the
+// pyramid (channels, set codes, voxel lists, two shift/distance buffers for the
+// Jacobi sweeps) and the scratch of the reductions. Every kernel is launched on
+// the context's stream; host synchronisation happens only where a value must
+// come back (list sizes after the pyramid, the stopping criterion, onion-peel
+// layer sizes, fetches).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vi.h"
+#include "vi_launch.h"
+
+using namespace vi;
+
+std::atomic<unsigned long long> vi::g_launch_count{0};
+
+namespace {
+
+// Philox tag word: purpose (4 bits) | level (4) | call (16) | k (8).
+enum : uint32_t { PURPOSE_INIT = 1, PURPOSE_SEARCH = 2, PURPOSE_UPSAMPLE = 3, PURPOSE_ONION = 4 };
+
+uint32_t make_tag(uint32_t purpose, int level, int call)
+{
+    return ((purpose & 0xFu) << 28) | (((uint32_t)level & 0xFu) << 24) | (((uint32_t)call & 0xFFFFu) << 8);
+}
+
+struct Level {
+    int W = 0, H = 0, T = 0;
+    int V = 0;
+    float4 *x4 = nullptr;
+    float *x1 = nullptr;
+    uint8_t *code = nullptr;
+    Shift *phi[2] = {nullptr, nullptr};
+    float *d2[2] = {nullptr, nullptr};
+    int *targets = nullptr, *holes = nullptr, *sources = nullptr;
+    int nT = 0, nH = 0, nS = 0;
+
+    LevelView view() const
+    {
+        LevelView v;
+        v.W = W;
+        v.H = H;
+        v.T = T;
+        v.HW = W * H;
+        v.V = V;
+        v.x4 = x4;
+        v.x1 = x1;
+        v.code = code;
+        return v;
+    }
+};
+
+}  // namespace
+
+struct vi_ctx {
+    vi_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool c5 = true;
+    int rho_log2 = 1;
+
+    int W = 0, H = 0, T = 0;
+    int V0 = 0;
+    int L = 0;
+    float *rgb = nullptr;
+    uint8_t *mask = nullptr;
+    float *out_rgb = nullptr;      // staging of vi_fetch_result to host memory
+    float2 *T0 = nullptr;
+    std::vector<Level> lv;
+
+    uint8_t *tmpA = nullptr, *tmpB = nullptr;
+    int *block_counts = nullptr;
+    int *count_dev = nullptr;      // 64 ints
+    float *partials = nullptr;
+    int partials_cap = 0;
+    double *partials2 = nullptr;
+    int partials2_cap = 0;
+    double *scal = nullptr;        // device scalars
+    double *host_scal = nullptr;   // pinned
+    int *host_counts = nullptr;    // pinned, 64 ints
+    unsigned long long *evals_dev = nullptr;  // [0] all, [1] step kernel
+
+    uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
+    int *layer_list = nullptr, *ltgt_list = nullptr;
+
+    bool uploaded = false, built = false;
+    unsigned long long step_launches = 0;
+    int outer[16] = {0};
+    int onion_layers = 0;
+
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    double step_ms = 0.0;
+    unsigned long long step_timed = 0;
+};
+
+namespace {
+
+vi_status fail(vi_ctx *ctx, vi_status st, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, VI_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+#define CK_LAUNCH()                                                                               \
+    do {                                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                                      \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, VI_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)                                                                                 \
+    do {                                                                                          \
+        vi_status s_ = (expr);                                                                    \
+        if (s_ != VI_OK)                                                                          \
+            return s_;                                                                            \
+    } while (0)
+
+template <typename P>
+vi_status dalloc(vi_ctx *ctx, P **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0)
+        bytes = 16;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(ctx, e == cudaErrorMemoryAllocation ? VI_ERR_OOM : VI_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return VI_OK;
+}
+
+template <typename P>
+void dfree(P *&ptr)
+{
+    if (ptr)
+        cudaFree((void *)ptr);
+    ptr = nullptr;
+}
+
+void free_state(vi_ctx *ctx)
+{
+    if (ctx->stream)
+        cudaStreamSynchronize(ctx->stream);
+    for (Level &l : ctx->lv) {
+        dfree(l.x4);
+        dfree(l.x1);
+        dfree(l.code);
+        dfree(l.phi[0]);
+        dfree(l.phi[1]);
+        dfree(l.d2[0]);
+        dfree(l.d2[1]);
+        dfree(l.targets);
+        dfree(l.holes);
+        dfree(l.sources);
+    }
+    ctx->lv.clear();
+    dfree(ctx->rgb);
+    dfree(ctx->mask);
+    dfree(ctx->out_rgb);
+    dfree(ctx->T0);
+    dfree(ctx->tmpA);
+    dfree(ctx->tmpB);
+    dfree(ctx->block_counts);
+    dfree(ctx->partials);
+    dfree(ctx->partials2);
+    dfree(ctx->hp);
+    dfree(ctx->layer);
+    dfree(ctx->ltgt);
+    dfree(ctx->layer_list);
+    dfree(ctx->ltgt_list);
+    ctx->partials_cap = ctx->partials2_cap = 0;
+    ctx->uploaded = ctx->built = false;
+}
+
+vi_status check_config(vi_ctx *ctx, const vi_config *c)
+{
+    if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
+        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || c->storage != 0)
+        return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
+    // rho must be 2^-m, m >= 1
+    int m = 0;
+    float r = c->rho;
+    while (r < 1.0f && r > 0.0f && m < 30) {
+        r *= 2.0f;
+        ++m;
+    }
+    if (!(r == 1.0f) || m < 1)
+        return fail(ctx, VI_ERR_ARG, "rho must be 1/2^m with m >= 1");
+    ctx->rho_log2 = m;
+    return VI_OK;
+}
+
+bool level_ok(vi_ctx *ctx, int level) { return ctx->built && level >= 0 && level < ctx->L; }
+
+vi_status ensure_partials(vi_ctx *ctx, int n_blocks)
+{
+    if (n_blocks <= ctx->partials_cap)
+        return VI_OK;
+    dfree(ctx->partials);
+    TRY(dalloc(ctx, &ctx->partials, sizeof(float) * (size_t)n_blocks));
+    ctx->partials_cap = n_blocks;
+    return VI_OK;
+}
+
+vi_status ensure_partials2(vi_ctx *ctx, int n_blocks)
+{
+    if (n_blocks <= ctx->partials2_cap)
+        return VI_OK;
+    dfree(ctx->partials2);
+    TRY(dalloc(ctx, &ctx->partials2, 2 * sizeof(double) * (size_t)n_blocks));
+    ctx->partials2_cap = n_blocks;
+    return VI_OK;
+}
+
+// One launch of the PatchMatch step kernel, bracketed by events when profiling.
+vi_status step_launch(vi_ctx *ctx, const AnnArgs &a)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->profiling) {
+        if (ctx->events_used == ctx->events.size()) {
+            cudaEvent_t x, y;
+            CK(cudaEventCreate(&x));
+            CK(cudaEventCreate(&y));
+            ctx->events.emplace_back(x, y);
+        }
+        e0 = ctx->events[ctx->events_used].first;
+        e1 = ctx->events[ctx->events_used].second;
+        ++ctx->events_used;
+        CK(cudaEventRecord(e0, ctx->stream));
+    }
+    launch_ann_step(a, ctx->c5, ctx->stream);
+    CK_LAUNCH();
+    if (ctx->profiling)
+        CK(cudaEventRecord(e1, ctx->stream));
+    ++ctx->step_launches;
+    return VI_OK;
+}
+
+// Distances, then n_pm Jacobi sweeps (Algorithm 1) over a target list. The
+// current shift map is buffer 0; sweep k reads buffer (k-1)&1 and writes k&1,
+// so only target entries are ever read from buffer 1; after an odd count the
+// targets are copied back to buffer 0.
+vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint8_t *tmask,
+                  uint8_t tbit, const uint8_t *excl, uint32_t tag)
+{
+    Level &l = ctx->lv[level];
+    const LevelView v = l.view();
+    launch_rescore(v, targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream);
+    CK_LAUNCH();
+    const int rmax = std::max(l.W, std::max(l.H, l.T));
+    for (int k = 1; k <= ctx->cfg.n_pm; ++k) {
+        AnnArgs a;
+        a.L = v;
+        a.targets = targets;
+        a.nT = nT;
+        a.phi_in = l.phi[(k - 1) & 1];
+        a.d_in = l.d2[(k - 1) & 1];
+        a.phi_out = l.phi[k & 1];
+        a.d_out = l.d2[k & 1];
+        a.tmask = tmask;
+        a.tbit = tbit;
+        a.excl = excl;
+        a.k = k;
+        a.rmax = rmax;
+        a.rho_log2 = ctx->rho_log2;
+        a.key0 = (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull);
+        a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
+        a.tag = tag;
+        a.clip = ctx->cfg.clip;
+        a.evals = ctx->evals_dev + 1;
+        TRY(step_launch(ctx, a));
+    }
+    if (ctx->cfg.n_pm & 1) {
+        launch_copy_targets(targets, nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], ctx->stream);
+        CK_LAUNCH();
+    }
+    return VI_OK;
+}
+
+vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
+{
+    Level &l = ctx->lv[level];
+    TRY(ensure_partials(ctx, vote_blocks(std::max(l.nH, 1))));
+    VoteArgs a;
+    a.L = l.view();
+    a.list = l.holes;
+    a.n = l.nH;
+    a.phi = l.phi[0];
+    a.d2 = l.d2[0];
+    a.allowed = l.code;
+    a.abit = CODE_TARGET;
+    a.weighted = ctx->cfg.weighted;
+    a.hp = nullptr;
+    a.partials = ctx->partials;
+    launch_vote(a, ctx->c5, ctx->stream);
+    CK_LAUNCH();
+    if (change_dev) {
+        launch_sum_partials(ctx->partials, vote_blocks(std::max(l.nH, 1)), change_dev, ctx->stream);
+        CK_LAUNCH();
+    }
+    return VI_OK;
+}
+
+int host_auto_levels(const uint8_t *mask, int W, int H, int T)
+{
+    int ext = 0;
+    for (int t = 0; t < T; ++t) {
+        int x0 = W, x1 = -1, y0 = H, y1 = -1;
+        const uint8_t *m = mask + (size_t)t * W * H;
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                if (m[(size_t)y * W + x]) {
+                    x0 = std::min(x0, x);
+                    x1 = std::max(x1, x);
+                    y0 = std::min(y0, y);
+                    y1 = std::max(y1, y);
+                }
+        if (x1 >= 0)
+            ext = std::max(ext, std::max(x1 - x0 + 1, y1 - y0 + 1));
+    }
+    int L = 1;
+    while (true) {
+        const int scale = 1 << (L - 1);
+        if ((ext + scale - 1) / scale <= 9)
+            break;
+        const int side = (std::min(W, H) + 2 * scale - 1) / (2 * scale);   // next level's side
+        if (side < 16 || L >= 15)
+            break;
+        ++L;
+    }
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vi_config_default(vi_config *cfg)
+{
+    if (!cfg)
+        return;
+    cfg->lambda = 50.0f;
+    cfg->n_pm = 10;
+    cfg->rho = 0.5f;
+    cfg->levels = 0;
+    cfg->max_outer = 20;
+    cfg->stop = 0.1f / 255.0f;
+    cfg->weighted = 1;
+    cfg->use_texture = 1;
+    cfg->storage = 0;
+    cfg->seed = 1503;
+    cfg->clip = 0;
+}
+
+vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
+{
+    if (!out)
+        return VI_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return VI_ERR_NO_DEVICE;
+    }
+    vi_ctx *ctx = new (std::nothrow) vi_ctx();
+    if (!ctx)
+        return VI_ERR_OOM;
+    if (cfg)
+        ctx->cfg = *cfg;
+    else
+        vi_config_default(&ctx->cfg);
+    vi_status s = check_config(ctx, &ctx->cfg);
+    if (s != VI_OK) {
+        delete ctx;
+        return s;
+    }
+    ctx->c5 = ctx->cfg.use_texture != 0;
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return VI_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc((void **)&ctx->count_dev, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->evals_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->host_scal, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->host_counts, 64 * sizeof(int)) != cudaSuccess) {
+        vi_ctx_destroy(ctx);
+        return VI_ERR_OOM;
+    }
+    cudaMemsetAsync(ctx->evals_dev, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    *out = ctx;
+    return VI_OK;
+}
+
+void vi_ctx_destroy(vi_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    free_state(ctx);
+    dfree(ctx->count_dev);
+    dfree(ctx->scal);
+    dfree(ctx->evals_dev);
+    if (ctx->host_scal)
+        cudaFreeHost(ctx->host_scal);
+    if (ctx->host_counts)
+        cudaFreeHost(ctx->host_counts);
+    for (auto &e : ctx->events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (ctx->own_stream && ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *vi_last_error(const vi_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int vi_auto_levels(const uint8_t *mask_host, int W, int H, int T)
+{
+    if (!mask_host || W <= 0 || H <= 0 || T <= 0)
+        return 1;
+    return host_auto_levels(mask_host, W, H, T);
+}
+
+size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long hole_voxels)
+{
+    (void)hole_voxels;
+    const int L = (cfg && cfg->levels > 0) ? cfg->levels : 6;
+    const bool c5 = !cfg || cfg->use_texture;
+    size_t total = 0;
+    int w = W, h = H;
+    for (int l = 0; l < L; ++l) {
+        const size_t V = (size_t)w * h * T;
+        // x4, x1, code, 2 shift + 2 distance buffers, three lists (upper bound)
+        total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 12);
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    const size_t V0 = (size_t)W * H * T;
+    total += V0 * (12 + 1 + 2 + (c5 ? 8 + 8 + 1 + 8 + 4 : 0));
+    return total + (16u << 20);
+}
+
+vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                    int ptr_is_device)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!rgb || !mask || W <= 0 || H <= 0 || T <= 0 || W > 32767 || H > 32767 || T > 32767 ||
+        (long long)W * H * T >= (1ll << 31))
+        return fail(ctx, VI_ERR_ARG, "vi_upload: bad pointer or size");
+    free_state(ctx);
+    ctx->W = W;
+    ctx->H = H;
+    ctx->T = T;
+    ctx->V0 = W * H * T;
+    const size_t V0 = (size_t)ctx->V0;
+    const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+    int L = ctx->cfg.levels;
+    if (L <= 0) {
+        if (ptr_is_device) {
+            std::vector<uint8_t> hm(V0);
+            CK(cudaMemcpy(hm.data(), mask, V0, cudaMemcpyDeviceToHost));
+            L = host_auto_levels(hm.data(), W, H, T);
+        } else {
+            L = host_auto_levels(mask, W, H, T);
+        }
+    }
+    ctx->L = L;
+
+    TRY(dalloc(ctx, &ctx->rgb, V0 * 3 * sizeof(float)));
+    TRY(dalloc(ctx, &ctx->mask, V0));
+    CK(cudaMemcpyAsync(ctx->rgb, rgb, V0 * 3 * sizeof(float), kind, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->mask, mask, V0, kind, ctx->stream));
+    TRY(dalloc(ctx, &ctx->tmpA, V0));
+    TRY(dalloc(ctx, &ctx->tmpB, V0));
+    TRY(dalloc(ctx, &ctx->block_counts, sizeof(int) * (size_t)(compact_blocks(ctx->V0) + 1)));
+
+    ctx->lv.assign(L, Level());
+    int w = W, h = H;
+    for (int l = 0; l < L; ++l) {
+        Level &lv = ctx->lv[l];
+        lv.W = w;
+        lv.H = h;
+        lv.T = T;
+        lv.V = w * h * T;
+        const size_t V = (size_t)lv.V;
+        TRY(dalloc(ctx, &lv.x4, V * sizeof(float4)));
+        if (ctx->c5)
+            TRY(dalloc(ctx, &lv.x1, V * sizeof(float)));
+        TRY(dalloc(ctx, &lv.code, V));
+        for (int b = 0; b < 2; ++b) {
+            TRY(dalloc(ctx, &lv.phi[b], V * sizeof(Shift)));
+            TRY(dalloc(ctx, &lv.d2[b], V * sizeof(float)));
+            CK(cudaMemsetAsync(lv.phi[b], 0, V * sizeof(Shift), ctx->stream));
+            launch_fill_f32(lv.d2[b], INFINITY, (long long)V, ctx->stream);
+            CK_LAUNCH();
+        }
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    // evaluation / launch / time counters accumulate over the context's life;
+    // the per-run counters restart with every upload
+    ctx->onion_layers = 0;
+    std::memset(ctx->outer, 0, sizeof(ctx->outer));
+    ctx->uploaded = true;
+    ctx->err.clear();
+    return VI_OK;
+}
+
+vi_status vi_build_pyramid(vi_ctx *ctx)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded)
+        return fail(ctx, VI_ERR_STATE, "vi_build_pyramid: no upload");
+    cudaStream_t st = ctx->stream;
+    const int W = ctx->W, H = ctx->H, T = ctx->T;
+    const size_t V0 = (size_t)ctx->V0;
+    const float s = (float)std::sqrt((double)ctx->cfg.lambda);
+
+    if (ctx->c5) {
+        float2 *g = nullptr, *sum = nullptr;
+        uint16_t *cnt = nullptr;
+        if (!ctx->T0)
+            TRY(dalloc(ctx, &ctx->T0, V0 * sizeof(float2)));
+        TRY(dalloc(ctx, &g, V0 * sizeof(float2)));
+        vi_status r = dalloc(ctx, &sum, V0 * sizeof(float2));
+        if (r == VI_OK)
+            r = dalloc(ctx, &cnt, V0 * 2 * sizeof(uint16_t));
+        if (r == VI_OK) {
+            // ctx->tmpA holds the validity bits of the derivative samples
+            launch_gradients(ctx->rgb, ctx->mask, W, H, T, g, ctx->tmpA, st);
+            launch_box_mean(g, ctx->tmpA, W, H, T, 1 << (ctx->L - 1), sum, cnt, ctx->T0, st);
+            cudaStreamSynchronize(st);
+        }
+        dfree(g);
+        dfree(sum);
+        dfree(cnt);
+        TRY(r);
+        CK_LAUNCH();
+    }
+    launch_level0_channels(ctx->rgb, ctx->mask, ctx->T0, s, ctx->c5, ctx->lv[0].view(), st);
+    CK_LAUNCH();
+    launch_codes(ctx->lv[0].view(), ctx->tmpA, ctx->tmpB, st);
+    CK_LAUNCH();
+    for (int l = 1; l < ctx->L; ++l) {
+        launch_downsample(ctx->lv[l - 1].view(), ctx->lv[l].view(), l, ctx->T0, W, H, s, ctx->c5, st);
+        CK_LAUNCH();
+        launch_codes(ctx->lv[l].view(), ctx->tmpA, ctx->tmpB, st);
+        CK_LAUNCH();
+    }
+    // list sizes (one synchronisation), then the lists
+    for (int l = 0; l < ctx->L; ++l) {
+        Level &lv = ctx->lv[l];
+        launch_compact(lv.code, CODE_TARGET, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l, st);
+        launch_compact(lv.code, CODE_HOLE, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l + 1, st);
+        launch_compact(lv.code, CODE_SOURCE, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l + 2, st);
+        CK_LAUNCH();
+    }
+    CK(cudaMemcpyAsync(ctx->host_counts, ctx->count_dev, sizeof(int) * 3 * ctx->L, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int max_list = 1, max_t = 1;
+    for (int l = 0; l < ctx->L; ++l) {
+        Level &lv = ctx->lv[l];
+        dfree(lv.targets);
+        dfree(lv.holes);
+        dfree(lv.sources);
+        lv.nT = ctx->host_counts[3 * l];
+        lv.nH = ctx->host_counts[3 * l + 1];
+        lv.nS = ctx->host_counts[3 * l + 2];
+        if (lv.nS == 0 && lv.nH > 0)
+            return fail(ctx, VI_ERR_NO_SOURCE,
+                        "no whole known 5x5x5 patch (D~ empty) at level " + std::to_string(l));
+        TRY(dalloc(ctx, &lv.targets, sizeof(int) * (size_t)std::max(lv.nT, 1)));
+        TRY(dalloc(ctx, &lv.holes, sizeof(int) * (size_t)std::max(lv.nH, 1)));
+        TRY(dalloc(ctx, &lv.sources, sizeof(int) * (size_t)std::max(lv.nS, 1)));
+        launch_compact(lv.code, CODE_TARGET, lv.V, ctx->block_counts, lv.targets, ctx->count_dev, st);
+        launch_compact(lv.code, CODE_HOLE, lv.V, ctx->block_counts, lv.holes, ctx->count_dev, st);
+        launch_compact(lv.code, CODE_SOURCE, lv.V, ctx->block_counts, lv.sources, ctx->count_dev, st);
+        CK_LAUNCH();
+        max_list = std::max(max_list, lv.nH);
+        max_t = std::max(max_t, lv.nT);
+    }
+    TRY(ensure_partials(ctx, vote_blocks(max_list)));
+    TRY(ensure_partials2(ctx, energy_blocks(max_t)));
+    ctx->built = true;
+    return VI_OK;
+}
+
+vi_status vi_init_nnf(vi_ctx *ctx, int level)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_init_nnf: bad level or no pyramid");
+    Level &l = ctx->lv[level];
+    if (l.nS == 0)
+        return l.nT ? fail(ctx, VI_ERR_NO_SOURCE, "vi_init_nnf: D~ empty") : VI_OK;
+    launch_init_nnf(l.view(), l.targets, l.nT, l.sources, l.nS, l.phi[0],
+                    (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull), (uint32_t)(ctx->cfg.seed >> 32),
+                    make_tag(PURPOSE_INIT, level, 0), ctx->cfg.clip, ctx->stream);
+    CK_LAUNCH();
+    return VI_OK;
+}
+
+vi_status vi_onion_peel(vi_ctx *ctx)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!ctx->built)
+        return fail(ctx, VI_ERR_STATE, "vi_onion_peel: no pyramid");
+    const int level = ctx->L - 1;
+    Level &l = ctx->lv[level];
+    const LevelView v = l.view();
+    cudaStream_t st = ctx->stream;
+    const size_t V = (size_t)l.V;
+    if (!ctx->hp) {
+        TRY(dalloc(ctx, &ctx->hp, V));
+        TRY(dalloc(ctx, &ctx->layer, V));
+        TRY(dalloc(ctx, &ctx->ltgt, V));
+        TRY(dalloc(ctx, &ctx->layer_list, V * sizeof(int)));
+        TRY(dalloc(ctx, &ctx->ltgt_list, V * sizeof(int)));
+    }
+    TRY(ensure_partials(ctx, vote_blocks(l.V)));
+    launch_extract_bit(l.code, CODE_HOLE, ctx->hp, l.V, st);
+    CK_LAUNCH();
+    launch_count(ctx->hp, l.V, ctx->count_dev + 60, st);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(ctx->host_counts + 60, ctx->count_dev + 60, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int remaining = ctx->host_counts[60];
+    int n_layer = 0;
+    while (remaining > 0) {
+        launch_onion_layer(v, ctx->hp, ctx->layer, st);
+        launch_onion_targets(v, ctx->hp, ctx->layer, ctx->ltgt, st);
+        launch_compact(ctx->layer, 1, l.V, ctx->block_counts, ctx->layer_list, ctx->count_dev + 61, st);
+        launch_compact(ctx->ltgt, 1, l.V, ctx->block_counts, ctx->ltgt_list, ctx->count_dev + 62, st);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(ctx->host_counts + 61, ctx->count_dev + 61, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int n_lay = ctx->host_counts[61], n_tgt = ctx->host_counts[62];
+        TRY(run_ann(ctx, level, ctx->ltgt_list, n_tgt, ctx->ltgt, 1, ctx->hp,
+                    make_tag(PURPOSE_ONION, level, n_layer)));
+        VoteArgs a;
+        a.L = v;
+        a.list = ctx->layer_list;
+        a.n = n_lay;
+        a.phi = l.phi[0];
+        a.d2 = l.d2[0];
+        a.allowed = ctx->ltgt;
+        a.abit = 1;
+        a.weighted = ctx->cfg.weighted;
+        a.hp = ctx->hp;
+        a.partials = ctx->partials;
+        launch_vote(a, ctx->c5, st);
+        CK_LAUNCH();
+        launch_count(ctx->hp, l.V, ctx->count_dev + 60, st);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(ctx->host_counts + 60, ctx->count_dev + 60, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int now = ctx->host_counts[60];
+        ++n_layer;
+        if (now >= remaining)
+            return fail(ctx, VI_ERR_STATE, "vi_onion_peel: a layer filled no voxel");
+        remaining = now;
+    }
+    ctx->onion_layers = n_layer;
+    return VI_OK;
+}
+
+vi_status vi_prepare(vi_ctx *ctx)
+{
+    TRY(vi_build_pyramid(ctx));
+    TRY(vi_init_nnf(ctx, ctx->L - 1));
+    return vi_onion_peel(ctx);
+}
+
+vi_status vi_rescore(vi_ctx *ctx, int level)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_rescore: bad level or no pyramid");
+    Level &l = ctx->lv[level];
+    launch_rescore(l.view(), l.targets, l.nT, l.phi[0], l.d2[0], nullptr, ctx->c5, ctx->evals_dev,
+                   ctx->stream);
+    CK_LAUNCH();
+    return VI_OK;
+}
+
+vi_status vi_ann(vi_ctx *ctx, int level, int call)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || call < 0 || call > 0xFFFF)
+        return fail(ctx, VI_ERR_ARG, "vi_ann: bad level or call index");
+    Level &l = ctx->lv[level];
+    return run_ann(ctx, level, l.targets, l.nT, l.code, CODE_TARGET, nullptr,
+                   make_tag(PURPOSE_SEARCH, level, call));
+}
+
+vi_status vi_reconstruct(vi_ctx *ctx, int level, float *e_host)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_reconstruct: bad level or no pyramid");
+    TRY(vote_level(ctx, level, e_host ? ctx->scal : nullptr));
+    if (e_host) {
+        CK(cudaMemcpyAsync(ctx->host_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int nH = ctx->lv[level].nH;
+        *e_host = nH ? (float)(ctx->host_scal[0] / (3.0 * nH)) : 0.0f;
+    }
+    return VI_OK;
+}
+
+vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n_done_host,
+                     float *e_last_host)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || first_call < 0)
+        return fail(ctx, VI_ERR_ARG, "vi_iterate: bad level or no pyramid");
+    int k = 0;
+    float e = INFINITY;
+    const bool rule = n_outer < 0;
+    while (rule ? (e > ctx->cfg.stop && k < ctx->cfg.max_outer) : (k < n_outer)) {
+        TRY(vi_ann(ctx, level, first_call + k));
+        TRY(vi_reconstruct(ctx, level, (rule || e_last_host) ? &e : nullptr));
+        ++k;
+    }
+    if (level < 16)
+        ctx->outer[level] += k;
+    if (n_done_host)
+        *n_done_host = k;
+    if (e_last_host)
+        *e_last_host = e;
+    return VI_OK;
+}
+
+vi_status vi_next_level(vi_ctx *ctx, int level)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || level == 0)
+        return fail(ctx, VI_ERR_ARG, "vi_next_level: level must be in [1, L)");
+    Level &c = ctx->lv[level];
+    Level &f = ctx->lv[level - 1];
+    launch_upsample_nnf(c.view(), c.phi[0], f.view(), f.targets, f.nT, f.sources, f.nS, f.phi[0],
+                        (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull), (uint32_t)(ctx->cfg.seed >> 32),
+                        make_tag(PURPOSE_UPSAMPLE, level - 1, 0), ctx->cfg.clip, ctx->stream);
+    CK_LAUNCH();
+    launch_provisional_fill(c.view(), f.view(), f.holes, f.nH, ctx->c5, ctx->stream);
+    CK_LAUNCH();
+    TRY(vi_rescore(ctx, level - 1));
+    return vote_level(ctx, level - 1, nullptr);
+}
+
+vi_status vi_final(vi_ctx *ctx)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, 0))
+        return fail(ctx, VI_ERR_STATE, "vi_final: no pyramid");
+    Level &l = ctx->lv[0];
+    launch_final(l.view(), l.holes, l.nH, l.phi[0], l.d2[0], ctx->c5, ctx->stream);
+    CK_LAUNCH();
+    return VI_OK;
+}
+
+vi_status vi_run(vi_ctx *ctx)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    TRY(vi_prepare(ctx));
+    for (int l = ctx->L - 1; l >= 0; --l) {
+        TRY(vi_iterate(ctx, l, -1, 0, nullptr, nullptr));
+        if (l > 0)
+            TRY(vi_next_level(ctx, l));
+    }
+    return vi_final(ctx);
+}
+
+vi_status vi_energy(vi_ctx *ctx, int level, double *E_H_host, double *E_Ht_host)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_energy: bad level or no pyramid");
+    Level &l = ctx->lv[level];
+    const int nb = energy_blocks(std::max(l.nT, 1));
+    TRY(ensure_partials2(ctx, nb));
+    if (l.nT == 0) {
+        if (E_H_host) *E_H_host = 0.0;
+        if (E_Ht_host) *E_Ht_host = 0.0;
+        return VI_OK;
+    }
+    launch_energy(l.view(), l.targets, l.nT, l.phi[0], ctx->c5, ctx->partials2, ctx->stream);
+    launch_sum_partials2(ctx->partials2, nb, ctx->scal + 2, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(ctx->host_scal + 2, ctx->scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (E_H_host) *E_H_host = ctx->host_scal[2];
+    if (E_Ht_host) *E_Ht_host = ctx->host_scal[3];
+    return VI_OK;
+}
+
+vi_status vi_level_info(vi_ctx *ctx, int level, int *W, int *H, int *T, int *C, long long *n_hole,
+                        long long *n_target, long long *n_source)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded || level < 0 || level >= ctx->L)
+        return fail(ctx, VI_ERR_ARG, "vi_level_info: bad level or no upload");
+    const Level &l = ctx->lv[level];
+    if (W) *W = l.W;
+    if (H) *H = l.H;
+    if (T) *T = l.T;
+    if (C) *C = ctx->c5 ? 5 : 3;
+    if (n_hole) *n_hole = ctx->built ? l.nH : -1;
+    if (n_target) *n_target = ctx->built ? l.nT : -1;
+    if (n_source) *n_source = ctx->built ? l.nS : -1;
+    return VI_OK;
+}
+
+vi_status vi_get_channels(vi_ctx *ctx, int level, float *out, int ptr_is_device)
+{
+    if (!ctx || !out)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded || level < 0 || level >= ctx->L)
+        return fail(ctx, VI_ERR_ARG, "vi_get_channels: bad level");
+    const Level &l = ctx->lv[level];
+    const int C = ctx->c5 ? 5 : 3;
+    const size_t bytes = (size_t)l.V * C * sizeof(float);
+    if (ptr_is_device) {
+        launch_get_channels(l.view(), out, C, ctx->stream);
+        CK_LAUNCH();
+        return VI_OK;
+    }
+    float *tmp = nullptr;
+    TRY(dalloc(ctx, &tmp, bytes));
+    launch_get_channels(l.view(), tmp, C, ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess)
+        return fail(ctx, VI_ERR_CUDA, std::string("vi_get_channels: ") + cudaGetErrorString(e));
+    return VI_OK;
+}
+
+vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_device)
+{
+    if (!ctx || !in)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded || level < 0 || level >= ctx->L)
+        return fail(ctx, VI_ERR_ARG, "vi_set_channels: bad level");
+    const Level &l = ctx->lv[level];
+    const int C = ctx->c5 ? 5 : 3;
+    const size_t bytes = (size_t)l.V * C * sizeof(float);
+    if (ptr_is_device) {
+        launch_set_channels(l.view(), in, C, ctx->stream);
+        CK_LAUNCH();
+        return VI_OK;
+    }
+    float *tmp = nullptr;
+    TRY(dalloc(ctx, &tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        launch_set_channels(l.view(), tmp, C, ctx->stream);
+        e = cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(tmp);
+    if (e != cudaSuccess)
+        return fail(ctx, VI_ERR_CUDA, std::string("vi_set_channels: ") + cudaGetErrorString(e));
+    return VI_OK;
+}
+
+vi_status vi_get_nnf(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_get_nnf: bad level or no pyramid");
+    const Level &l = ctx->lv[level];
+    const size_t V = (size_t)l.V;
+    std::vector<Shift> ph(V);
+    std::vector<float> dd(V);
+    std::vector<uint8_t> code(V);
+    CK(cudaMemcpyAsync(ph.data(), l.phi[0], V * sizeof(Shift), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(dd.data(), l.d2[0], V * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(code.data(), l.code, V, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t v = 0; v < V; ++v) {
+        const bool t = (code[v] & CODE_TARGET) != 0;
+        if (phi_host) {
+            phi_host[3 * v] = t ? ph[v].dx : 0;
+            phi_host[3 * v + 1] = t ? ph[v].dy : 0;
+            phi_host[3 * v + 2] = t ? ph[v].dt : 0;
+        }
+        if (d2_host)
+            d2_host[v] = t ? dd[v] : INFINITY;
+    }
+    return VI_OK;
+}
+
+vi_status vi_set_nnf(vi_ctx *ctx, int level, const int32_t *phi_host, const float *d2_host)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_set_nnf: bad level or no pyramid");
+    const Level &l = ctx->lv[level];
+    const size_t V = (size_t)l.V;
+    if (phi_host) {
+        std::vector<Shift> ph(V);
+        for (size_t v = 0; v < V; ++v) {
+            const int32_t a = phi_host[3 * v], b = phi_host[3 * v + 1], c = phi_host[3 * v + 2];
+            if (a < -32767 || a > 32767 || b < -32767 || b > 32767 || c < -32767 || c > 32767)
+                return fail(ctx, VI_ERR_ARG, "vi_set_nnf: shift out of range");
+            ph[v].dx = (short)a;
+            ph[v].dy = (short)b;
+            ph[v].dt = (short)c;
+            ph[v].pad = 0;
+        }
+        CK(cudaMemcpyAsync(l.phi[0], ph.data(), V * sizeof(Shift), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (d2_host) {
+        CK(cudaMemcpyAsync(l.d2[0], d2_host, V * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return VI_OK;
+}
+
+vi_status vi_get_masks(vi_ctx *ctx, int level, uint8_t *code_host)
+{
+    if (!ctx || !code_host)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_get_masks: bad level or no pyramid");
+    const Level &l = ctx->lv[level];
+    CK(cudaMemcpyAsync(code_host, l.code, (size_t)l.V, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return VI_OK;
+}
+
+vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n, float *out_host)
+{
+    if (!ctx || (n > 0 && (!pairs_host || !out_host)) || n < 0)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded || level < 0 || level >= ctx->L)
+        return fail(ctx, VI_ERR_ARG, "vi_patch_dist: bad level");
+    if (n == 0)
+        return VI_OK;
+    int *dp = nullptr;
+    float *dout = nullptr;
+    TRY(dalloc(ctx, &dp, sizeof(int) * 6 * (size_t)n));
+    vi_status r = dalloc(ctx, &dout, sizeof(float) * (size_t)n);
+    if (r != VI_OK) {
+        cudaFree(dp);
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(dp, pairs_host, sizeof(int) * 6 * (size_t)n, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) {
+        launch_patch_dist(ctx->lv[level].view(), dp, n, dout, ctx->c5, ctx->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, dout, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dp);
+    cudaFree(dout);
+    if (e != cudaSuccess)
+        return fail(ctx, VI_ERR_CUDA, std::string("vi_patch_dist: ") + cudaGetErrorString(e));
+    return VI_OK;
+}
+
+vi_status vi_fetch_result(vi_ctx *ctx, float *rgb_out, int ptr_is_device)
+{
+    if (!ctx || !rgb_out)
+        return VI_ERR_ARG;
+    if (!ctx->built)
+        return fail(ctx, VI_ERR_STATE, "vi_fetch_result: nothing computed");
+    const Level &l = ctx->lv[0];
+    const size_t bytes = (size_t)l.V * 3 * sizeof(float);
+    if (ptr_is_device) {
+        launch_pack_rgb(l.view(), rgb_out, ctx->stream);
+        CK_LAUNCH();
+        return VI_OK;
+    }
+    if (!ctx->out_rgb)
+        TRY(dalloc(ctx, &ctx->out_rgb, bytes));
+    launch_pack_rgb(l.view(), ctx->out_rgb, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(rgb_out, ctx->out_rgb, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return VI_OK;
+}
+
+vi_status vi_profile(vi_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    ctx->profiling = enable != 0;
+    return VI_OK;
+}
+
+vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
+{
+    if (!ctx || !out)
+        return VI_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    unsigned long long ev[2] = {0, 0};
+    CK(cudaMemcpyAsync(ev, ctx->evals_dev, sizeof(ev), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < ctx->events_used; ++i) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ctx->events[i].first, ctx->events[i].second));
+        ctx->step_ms += ms;
+        ++ctx->step_timed;
+    }
+    ctx->events_used = 0;
+    out->evals = ev[0] + ev[1];
+    out->step_evals = ev[1];
+    out->step_launches = ctx->step_launches;
+    out->step_ms = ctx->step_ms;
+    out->step_timed = ctx->step_timed;
+    for (int i = 0; i < 16; ++i)
+        out->outer[i] = ctx->outer[i];
+    out->onion_layers = ctx->onion_layers;
+    out->levels = ctx->L;
+    out->launches = g_launch_count.load();
+    return VI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// vi_launch.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "vi_device.cuh"
+
+namespace vi {
+// Kernel launches issued by this library in this process (all contexts).
+extern std::atomic<unsigned long long> g_launch_count;
+}  // namespace vi
+#define VI_COUNT_LAUNCH() (::vi::g_launch_count.fetch_add(1, std::memory_order_relaxed))
+
+namespace vi {
+
+// ---- pyramid and sets (vi_pyramid.cu) --------------------------------------
+// Grey-level derivatives of the level-0 video: g = (|I_x|, |I_y|), valid bits
+// (1: I_x known, 2: I_y known) -- Eq. 7.
+void launch_gradients(const float *rgb, const uint8_t *hole, int W, int H, int T, float2 *g,
+                      uint8_t *valid, cudaStream_t st);
+// Box mean of g over the square nu of side `side` (Eq. 7) -> T0 = (T_x, T_y).
+void launch_box_mean(const float2 *g, const uint8_t *valid, int W, int H, int T, int side,
+                     float2 *tmp_sum, uint16_t *tmp_cnt, float2 *T0, cudaStream_t st);
+// Level-0 channels from the input video and T0 (occluded voxels zeroed).
+void launch_level0_channels(const float *rgb, const uint8_t *hole, const float2 *T0,
+                            float sqrt_lambda, bool c5, LevelView L, cudaStream_t st);
+// Coarse level from the finer one: 2x2 mean of known children, OR of the
+// occlusion, texture features subsampled from T0 (Eq. 8).
+void launch_downsample(LevelView fine, LevelView coarse, int level, const float2 *T0, int W0,
+                       int H0, float sqrt_lambda, bool c5, cudaStream_t st);
+// code = H | H~ | D~ of a level from its occlusion bits (3 separable dilations).
+void launch_codes(LevelView L, uint8_t *tmp_a, uint8_t *tmp_b, cudaStream_t st);
+// Raster-ordered compaction of {v : (flags[v] & bits) != 0} into list.
+// block_counts needs compact_blocks(V) + 1 ints; *count_dev receives the size.
+int compact_blocks(int V);
+void launch_compact(const uint8_t *flags, uint8_t bits, int V, int *block_counts, int *list,
+                    int *count_dev, cudaStream_t st);
+
+// ---- search (vi_search.cu) ----------------------------------------------------
+struct AnnArgs {
+    LevelView L;
+    const int *targets;
+    int nT;
+    const Shift *phi_in;
+    const float *d_in;
+    Shift *phi_out;
+    float *d_out;
+    const uint8_t *tmask;  // neighbour r is a target iff tmask[r] & tbit
+    uint8_t tbit;
+    const uint8_t *excl;   // partial distance (Eq. 11) when non-null
+    int k;                 // PatchMatch iteration 1..n_pm
+    int rmax;
+    int rho_log2;          // rho = 2^-rho_log2
+    uint32_t key0, key1, tag, clip;
+    unsigned long long *evals;
+};
+void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st);
+// d_out[p] = distance of target p to p + phi[p] (in place allowed).
+void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
+                    const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st);
+void launch_copy_targets(const int *targets, int nT, const Shift *phi_src, const float *d_src,
+                         Shift *phi_dst, float *d_dst, cudaStream_t st);
+void launch_init_nnf(LevelView L, const int *targets, int nT, const int *sources, int nS,
+                     Shift *phi, uint32_t key0, uint32_t key1, uint32_t tag, uint32_t clip,
+                     cudaStream_t st);
+void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, const int *targets_f,
+                         int nT, const int *sources_f, int nS, Shift *phi_f, uint32_t key0,
+                         uint32_t key1, uint32_t tag, uint32_t clip, cudaStream_t st);
+void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH,
+                             bool c5, cudaStream_t st);
+void launch_patch_dist(LevelView L, const int *pairs, int n, float *out, bool c5, cudaStream_t st);
+
+// ---- reconstruction (vi_vote.cu) -----------------------------------------------
+struct VoteArgs {
+    LevelView L;
+    const int *list;       // voxels to reconstruct
+    int n;
+    const Shift *phi;
+    const float *d2;
+    const uint8_t *allowed;  // q contributes iff allowed[q] & abit
+    uint8_t abit;
+    int weighted;
+    uint8_t *hp;           // onion peel: cleared for filled voxels (nullable)
+    float *partials;       // per-block sum of |change| over the colour channels
+};
+int vote_blocks(int n);
+void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st);
+// out[0] = sum of partials[0..n) in a fixed order.
+void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st);
+void launch_final(LevelView L, const int *holes, int nH, const Shift *phi, const float *d2,
+                  bool c5, cudaStream_t st);
+int energy_blocks(int n);
+void launch_energy(LevelView L, const int *targets, int nT, const Shift *phi, bool c5,
+                   double *partials2, cudaStream_t st);
+void launch_sum_partials2(const double *partials2, int n, double *out2, cudaStream_t st);
+// Onion peel sets on the coarsest level (Algorithm 3).
+void launch_onion_layer(LevelView L, const uint8_t *hp, uint8_t *layer, cudaStream_t st);
+void launch_onion_targets(LevelView L, const uint8_t *hp, const uint8_t *layer, uint8_t *ltgt,
+                          cudaStream_t st);
+void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st);
+// Packing helpers between the library layout and the ABI layout.
+void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st);
+void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st);
+void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st);
+
+}  // namespace vi
+
+namespace vi {
+// out[v] = (in[v] & bit) ? 1 : 0
+void launch_extract_bit(const uint8_t *in, uint8_t bit, uint8_t *out, int V, cudaStream_t st);
+// dst[v] = value for v < n
+void launch_fill_f32(float *dst, float value, long long n, cudaStream_t st);
+}  // namespace vi

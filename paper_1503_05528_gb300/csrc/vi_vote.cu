@@ -1,0 +1,475 @@
+// vi_vote.cu -- reconstruction of Sec. 3.2 (Eq. 4, Eq. 5, Eq. 9; Eq. 12 during
+// the initialisation), the final best-patch step (Eq. 6), the energy (Eq. 1),
+// the onion-peel sets of Algorithm 3 and layout packing.
+#include "vi_launch.h"
+
+namespace vi {
+
+static inline int blocks_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    return (int)(g < 1 ? 1 : g);
+}
+
+static constexpr int VOTE_BLOCK = 256;            // 8 warps, one occluded voxel per warp
+static constexpr int VOTE_WARPS = VOTE_BLOCK / 32;
+
+int vote_blocks(int n) { return blocks_for(n, VOTE_WARPS); }
+
+// One warp per voxel p. Lane l owns the patch offsets j = l, l+32, l+64, l+96
+// (j < 125; offset (j%5 - 2, (j/5)%5 - 2, j/25 - 2)), i.e. the q in N_p.
+//  1. each lane loads d2(q) of its contributors (q inside the video, allowed,
+//     finite);
+//  2. sigma_p^2 = the element of rank ceil(0.75 n) of the n values (nearest
+//     rank), found by a bitwise radix select over the IEEE bit patterns of the
+//     non-negative d2 with warp-wide counts;
+//  3. s_q = exp(-d2(q) / (2 sigma_p^2)) (limit 1/0 for sigma_p = 0; 1 when
+//     unweighted); each lane accumulates s_q u(p + phi(q)) over all channels;
+//  4. warp sums; lane 0 writes u(p) and adds |u_new - u_old| (RGB) to the
+//     block's change.
+template <bool C5>
+__global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
+{
+    __shared__ float block_change[VOTE_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int item = blockIdx.x * VOTE_WARPS + wid;
+    float change = 0.0f;
+    if (item < a.n) {
+        const LevelView &L = a.L;
+        const int p = a.list[item];
+        int px, py, pt;
+        decode(p, L.W, L.HW, px, py, pt);
+        float dq[4];
+        int qv[4];
+        unsigned okm = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int j = lane + 32 * m;
+            dq[m] = 0.0f;
+            qv[m] = 0;
+            if (j < 125) {
+                const int qx = px + (j % 5) - 2, qy = py + ((j / 5) % 5) - 2, qt = pt + (j / 25) - 2;
+                if (inside(L, qx, qy, qt)) {
+                    const int q = qt * L.HW + qy * L.W + qx;
+                    if (a.allowed[q] & a.abit) {
+                        const float d = a.d2[q];
+                        const Shift f = a.phi[q];
+                        // finite distance, and a source voxel p + phi(q) inside
+                        // the video (always true for a valid shift map; the
+                        // check keeps an injected map from reading outside)
+                        if (d < __int_as_float(0x7f800000) &&
+                            inside(L, px + f.dx, py + f.dy, pt + f.dt)) {
+                            dq[m] = d;
+                            qv[m] = q;
+                            okm |= 1u << m;
+                        }
+                    }
+                }
+            }
+        }
+        const int n = __reduce_add_sync(0xffffffffu, __popc(okm));
+        if (n > 0) {
+            float sigma2 = 0.0f;
+            if (a.weighted) {
+                const unsigned rank = (unsigned)((3 * n + 3) / 4 - 1);   // 0-based nearest rank
+                unsigned X = 0;
+                for (int b = 30; b >= 0; --b) {
+                    const unsigned Tt = X | (1u << b);
+                    unsigned c = 0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        c += ((okm >> m) & 1u) && (__float_as_uint(dq[m]) < Tt);
+                    c = __reduce_add_sync(0xffffffffu, c);
+                    if (c <= rank)
+                        X = Tt;
+                }
+                sigma2 = __uint_as_float(X);
+            }
+            float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f, n4 = 0.f, den = 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (!((okm >> m) & 1u))
+                    continue;
+                float w;
+                if (!a.weighted)
+                    w = 1.0f;
+                else if (sigma2 > 0.0f)
+                    w = expf(-(dq[m] / (2.0f * sigma2)));
+                else
+                    w = (dq[m] == 0.0f) ? 1.0f : 0.0f;
+                const Shift f = a.phi[qv[m]];
+                const int s = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
+                const float4 v = L.x4[s];
+                n0 = fmaf(w, v.x, n0);
+                n1 = fmaf(w, v.y, n1);
+                n2 = fmaf(w, v.z, n2);
+                n3 = fmaf(w, v.w, n3);
+                if (C5)
+                    n4 = fmaf(w, L.x1[s], n4);
+                den += w;
+            }
+            n0 = warp_sum(n0);
+            n1 = warp_sum(n1);
+            n2 = warp_sum(n2);
+            n3 = warp_sum(n3);
+            if (C5)
+                n4 = warp_sum(n4);
+            den = warp_sum(den);
+            if (lane == 0) {
+                const float4 old = L.x4[p];
+                const float4 nw = make_float4(n0 / den, n1 / den, n2 / den, n3 / den);
+                change = fabsf(nw.x - old.x) + fabsf(nw.y - old.y) + fabsf(nw.z - old.z);
+                L.x4[p] = nw;
+                if (C5)
+                    L.x1[p] = n4 / den;
+                if (a.hp)
+                    a.hp[p] = 0;
+            }
+        }
+    }
+    if (lane == 0)
+        block_change[wid] = change;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < VOTE_WARPS; ++w)
+            s += block_change[w];
+        a.partials[blockIdx.x] = s;
+    }
+}
+
+void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st)
+{
+    if (a.n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    if (c5)
+        k_vote<true><<<vote_blocks(a.n), VOTE_BLOCK, 0, st>>>(a);
+    else
+        k_vote<false><<<vote_blocks(a.n), VOTE_BLOCK, 0, st>>>(a);
+}
+
+// Deterministic sum of per-block partials: each thread a strided slice, then
+// a fixed-order tree in shared memory.
+__global__ void k_sum_partials(const float *__restrict__ partials, int n, double *out)
+{
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256)
+        acc += (double)partials[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        out[0] = s[0];
+}
+
+void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_sum_partials<<<1, 256, 0, st>>>(partials, n, out);
+}
+
+// Eq. 6: the occluded voxel p copies u(p + phi(q*)), q* = argmin d2(q) over
+// q in N_p inside the video, first in (dt, dy, dx) order on ties.
+template <bool C5>
+__global__ void k_final(LevelView L, const int *__restrict__ holes, int nH, const Shift *__restrict__ phi,
+                        const float *__restrict__ d2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nH)
+        return;
+    const int p = holes[i];
+    int px, py, pt;
+    decode(p, L.W, L.HW, px, py, pt);
+    float bd = 0.0f;
+    int bq = -1;
+    for (int dt = -2; dt <= 2; ++dt)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                if (!inside(L, px + dx, py + dy, pt + dt))
+                    continue;
+                const int q = p + dt * L.HW + dy * L.W + dx;
+                const float d = d2[q];
+                if (bq < 0 || d < bd) {
+                    bd = d;
+                    bq = q;
+                }
+            }
+    const Shift f = phi[bq];
+    if (!inside(L, px + f.dx, py + f.dy, pt + f.dt))   // only for an invalid injected map
+        return;
+    const int s = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
+    L.x4[p] = L.x4[s];
+    if (C5)
+        L.x1[p] = L.x1[s];
+}
+
+void launch_final(LevelView L, const int *holes, int nH, const Shift *phi, const float *d2, bool c5,
+                  cudaStream_t st)
+{
+    if (nH <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    if (c5)
+        k_final<true><<<blocks_for(nH, 256), 256, 0, st>>>(L, holes, nH, phi, d2);
+    else
+        k_final<false><<<blocks_for(nH, 256), 256, 0, st>>>(L, holes, nH, phi, d2);
+}
+
+// Eq. 1: per-block sums of d^2 over H and over H~ (FP32 distances, FP64 sums).
+int energy_blocks(int n) { return blocks_for(n, 256); }
+
+template <bool C5>
+__global__ void k_energy(LevelView L, const int *__restrict__ targets, int nT, const Shift *__restrict__ phi,
+                         double *partials2)
+{
+    __shared__ double sh[2][256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double eh = 0.0, et = 0.0;
+    if (i < nT) {
+        const int p = targets[i];
+        int px, py, pt;
+        decode(p, L.W, L.HW, px, py, pt);
+        const Shift f = phi[p];
+        const int sx = px + f.dx, sy = py + f.dy, st = pt + f.dt;
+        double d = __longlong_as_double(0x7ff0000000000000ll);
+        if (sx >= 2 && sx < L.W - 2 && sy >= 2 && sy < L.H - 2 && st >= 2 && st < L.T - 2)
+            d = (double)patch_d2<C5>(L, p, px, py, pt, st * L.HW + sy * L.W + sx, nullptr);
+        et = d;
+        if (L.code[p] & CODE_HOLE)
+            eh = d;
+    }
+    sh[0][threadIdx.x] = eh;
+    sh[1][threadIdx.x] = et;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials2[2 * blockIdx.x] = sh[0][0];
+        partials2[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+void launch_energy(LevelView L, const int *targets, int nT, const Shift *phi, bool c5, double *partials2,
+                   cudaStream_t st)
+{
+    if (nT <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    if (c5)
+        k_energy<true><<<energy_blocks(nT), 256, 0, st>>>(L, targets, nT, phi, partials2);
+    else
+        k_energy<false><<<energy_blocks(nT), 256, 0, st>>>(L, targets, nT, phi, partials2);
+}
+
+__global__ void k_sum_partials2(const double *__restrict__ p2, int n, double *out2)
+{
+    __shared__ double s[2][256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        a += p2[2 * i];
+        b += p2[2 * i + 1];
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s[0][threadIdx.x] += s[0][threadIdx.x + o];
+            s[1][threadIdx.x] += s[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = s[0][0];
+        out2[1] = s[1][0];
+    }
+}
+
+void launch_sum_partials2(const double *partials2, int n, double *out2, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_sum_partials2<<<1, 256, 0, st>>>(partials2, n, out2);
+}
+
+// Algorithm 3 sets. layer = H' minus its 3x3x3 erosion (voxels outside the
+// video are not in H'); ltgt = voxels outside H' whose patch meets the layer.
+__global__ void k_onion_layer(LevelView L, const uint8_t *__restrict__ hp, uint8_t *__restrict__ layer)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
+         v += (long long)gridDim.x * blockDim.x) {
+        uint8_t out = 0;
+        if (hp[v]) {
+            int x, y, t;
+            decode((int)v, L.W, L.HW, x, y, t);
+            bool all = true;
+            for (int dt = -1; dt <= 1 && all; ++dt)
+                for (int dy = -1; dy <= 1 && all; ++dy)
+                    for (int dx = -1; dx <= 1 && all; ++dx) {
+                        if (!inside(L, x + dx, y + dy, t + dt) ||
+                            !hp[(t + dt) * L.HW + (y + dy) * L.W + x + dx])
+                            all = false;
+                    }
+            out = all ? 0 : 1;
+        }
+        layer[v] = out;
+    }
+}
+
+void launch_onion_layer(LevelView L, const uint8_t *hp, uint8_t *layer, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_onion_layer<<<blocks_for(L.V, 256), 256, 0, st>>>(L, hp, layer);
+}
+
+__global__ void k_onion_targets(LevelView L, const uint8_t *__restrict__ hp, const uint8_t *__restrict__ layer,
+                                uint8_t *__restrict__ ltgt)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
+         v += (long long)gridDim.x * blockDim.x) {
+        uint8_t out = 0;
+        if (!hp[v]) {
+            int x, y, t;
+            decode((int)v, L.W, L.HW, x, y, t);
+            for (int dt = -2; dt <= 2 && !out; ++dt)
+                for (int dy = -2; dy <= 2 && !out; ++dy)
+                    for (int dx = -2; dx <= 2 && !out; ++dx)
+                        if (inside(L, x + dx, y + dy, t + dt) &&
+                            layer[(t + dt) * L.HW + (y + dy) * L.W + x + dx])
+                            out = 1;
+        }
+        ltgt[v] = out;
+    }
+}
+
+void launch_onion_targets(LevelView L, const uint8_t *hp, const uint8_t *layer, uint8_t *ltgt,
+                          cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_onion_targets<<<blocks_for(L.V, 256), 256, 0, st>>>(L, hp, layer, ltgt);
+}
+
+__global__ void k_count(const uint8_t *__restrict__ flags, int V, int *count)
+{
+    int c = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+        c += flags[v] ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c)
+        atomicAdd(count, c);
+}
+
+void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st)
+{
+    cudaMemsetAsync(count_dev, 0, sizeof(int), st);
+    int g = blocks_for(V, 256);
+    if (g > 152 * 8)
+        g = 152 * 8;
+    VI_COUNT_LAUNCH();
+    k_count<<<g, 256, 0, st>>>(flags, V, count_dev);
+}
+
+// Layout packing: [V] float4 (+ float) <-> [V][C] float32.
+__global__ void k_pack_rgb(LevelView L, float *__restrict__ rgb)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
+         v += (long long)gridDim.x * blockDim.x) {
+        const float4 a = L.x4[v];
+        rgb[3 * v] = a.x;
+        rgb[3 * v + 1] = a.y;
+        rgb[3 * v + 2] = a.z;
+    }
+}
+
+void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_pack_rgb<<<blocks_for(L.V, 256), 256, 0, st>>>(L, rgb);
+}
+
+__global__ void k_get_channels(LevelView L, float *__restrict__ out, int C)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
+         v += (long long)gridDim.x * blockDim.x) {
+        const float4 a = L.x4[v];
+        out[C * v] = a.x;
+        out[C * v + 1] = a.y;
+        out[C * v + 2] = a.z;
+        if (C == 5) {
+            out[C * v + 3] = a.w;
+            out[C * v + 4] = L.x1[v];
+        }
+    }
+}
+
+void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_get_channels<<<blocks_for(L.V, 256), 256, 0, st>>>(L, out, C);
+}
+
+__global__ void k_set_channels(LevelView L, const float *__restrict__ in, int C)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
+         v += (long long)gridDim.x * blockDim.x) {
+        float4 a = make_float4(in[C * v], in[C * v + 1], in[C * v + 2], 0.0f);
+        if (C == 5) {
+            a.w = in[C * v + 3];
+            L.x1[v] = in[C * v + 4];
+        }
+        L.x4[v] = a;
+    }
+}
+
+void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_set_channels<<<blocks_for(L.V, 256), 256, 0, st>>>(L, in, C);
+}
+
+}  // namespace vi
+
+namespace vi {
+
+__global__ void k_extract_bit(const uint8_t *__restrict__ in, uint8_t bit, uint8_t *__restrict__ out, int V)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+        out[v] = (in[v] & bit) ? 1 : 0;
+}
+
+void launch_extract_bit(const uint8_t *in, uint8_t bit, uint8_t *out, int V, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_extract_bit<<<blocks_for(V, 256), 256, 0, st>>>(in, bit, out, V);
+}
+
+__global__ void k_fill_f32(float *__restrict__ dst, float value, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = value;
+}
+
+void launch_fill_f32(float *dst, float value, long long n, cudaStream_t st)
+{
+    long long g = (n + 255) / 256;
+    if (g > 152 * 16)
+        g = 152 * 16;
+    if (g < 1)
+        g = 1;
+    VI_COUNT_LAUNCH();
+    k_fill_f32<<<(int)g, 256, 0, st>>>(dst, value, n);
+}
+
+}  // namespace vi

@@ -77,7 +77,7 @@ def translating_texture(W, H, T, sigma=2.0, seed=BASE_SEED + 1, speed=1):
     f = smooth_noise(rng, H, W, sigma)
     xs = np.arange(W)
     frames = [f[:, (xs - speed * t) % W, :] for t in range(T)]
-    return np.stack(frames).astype(np.float32)
+    return np.ascontiguousarray(np.stack(frames), dtype=np.float32)
 
 
 def box_mask(W, H, T, x0, x1, y0, y1, t0, t1):

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the C ABI declared in ``include/vi.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libvi.so``. Loading fails loudly when the library has not been
+built; there is no fallback implementation.
+
+Arrays: numpy arrays are host memory (``ptr_is_device = 0``); torch CUDA
+tensors are passed by ``data_ptr()`` as device memory (``ptr_is_device = 1``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VI_OK = 0
+STATUS = {0: "VI_OK", 1: "VI_ERR_ARG", 2: "VI_ERR_OOM", 3: "VI_ERR_CUDA", 4: "VI_ERR_TIMEOUT",
+          5: "VI_ERR_NO_SOURCE", 6: "VI_ERR_STATE", 7: "VI_ERR_NO_DEVICE"}
+
+# every entry point declared in include/vi.h
+EXPORTS = [
+    "vi_config_default", "vi_ctx_create", "vi_ctx_destroy", "vi_last_error", "vi_auto_levels",
+    "vi_footprint_bytes", "vi_upload", "vi_build_pyramid", "vi_init_nnf", "vi_onion_peel",
+    "vi_prepare", "vi_rescore", "vi_ann", "vi_reconstruct", "vi_iterate", "vi_next_level",
+    "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
+    "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
+    "vi_profile", "vi_get_stats",
+]
+
+
+class ViConfig(C.Structure):
+    _fields_ = [("lambda_", C.c_float), ("n_pm", C.c_int), ("rho", C.c_float),
+                ("levels", C.c_int), ("max_outer", C.c_int), ("stop", C.c_float),
+                ("weighted", C.c_int), ("use_texture", C.c_int), ("storage", C.c_int),
+                ("seed", C.c_uint64), ("clip", C.c_uint32)]
+
+
+class ViStats(C.Structure):
+    _fields_ = [("evals", C.c_ulonglong), ("step_evals", C.c_ulonglong),
+                ("step_launches", C.c_ulonglong), ("step_ms", C.c_double),
+                ("step_timed", C.c_ulonglong), ("outer", C.c_int * 16),
+                ("onion_layers", C.c_int), ("levels", C.c_int), ("launches", C.c_ulonglong)]
+
+
+class ViError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libvi.so (building it first only when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        _build.build()
+    lib = C.CDLL(path)
+    _declare(lib)
+    _lib = lib
+    return lib
+
+
+def _declare(L):
+    vp, i, f, d, ll = C.c_void_p, C.c_int, C.c_float, C.c_double, C.c_longlong
+    P = C.POINTER
+    L.vi_config_default.argtypes = [P(ViConfig)]
+    L.vi_config_default.restype = None
+    L.vi_ctx_create.argtypes = [P(ViConfig), vp, P(vp)]
+    L.vi_ctx_destroy.argtypes = [vp]
+    L.vi_ctx_destroy.restype = None
+    L.vi_last_error.argtypes = [vp]
+    L.vi_last_error.restype = C.c_char_p
+    L.vi_auto_levels.argtypes = [vp, i, i, i]
+    L.vi_footprint_bytes.argtypes = [P(ViConfig), i, i, i, ll]
+    L.vi_footprint_bytes.restype = C.c_size_t
+    L.vi_upload.argtypes = [vp, vp, vp, i, i, i, i]
+    for name in ("vi_build_pyramid", "vi_onion_peel", "vi_prepare", "vi_final", "vi_run"):
+        getattr(L, name).argtypes = [vp]
+    L.vi_init_nnf.argtypes = [vp, i]
+    L.vi_rescore.argtypes = [vp, i]
+    L.vi_ann.argtypes = [vp, i, i]
+    L.vi_reconstruct.argtypes = [vp, i, P(f)]
+    L.vi_iterate.argtypes = [vp, i, i, i, P(i), P(f)]
+    L.vi_next_level.argtypes = [vp, i]
+    L.vi_energy.argtypes = [vp, i, P(d), P(d)]
+    L.vi_level_info.argtypes = [vp, i, P(i), P(i), P(i), P(i), P(ll), P(ll), P(ll)]
+    L.vi_get_channels.argtypes = [vp, i, vp, i]
+    L.vi_set_channels.argtypes = [vp, i, vp, i]
+    L.vi_get_nnf.argtypes = [vp, i, vp, vp]
+    L.vi_set_nnf.argtypes = [vp, i, vp, vp]
+    L.vi_get_masks.argtypes = [vp, i, vp]
+    L.vi_patch_dist.argtypes = [vp, i, vp, i, vp]
+    L.vi_fetch_result.argtypes = [vp, vp, i]
+    L.vi_profile.argtypes = [vp, i]
+    L.vi_get_stats.argtypes = [vp, P(ViStats)]
+
+
+def default_config(**kw):
+    cfg = ViConfig()
+    load().vi_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, "lambda_" if k == "lam" else k, v)
+    return cfg
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "array must be C-contiguous"
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(type(a))
+
+
+class Context:
+    """One inpainting context (``vi_ctx``); methods mirror the C entry points."""
+
+    def __init__(self, cfg=None, stream=None, **kw):
+        self.lib = load()
+        if cfg is None:
+            cfg = default_config(**kw)
+        h = C.c_void_p()
+        st = self.lib.vi_ctx_create(C.byref(cfg), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != VI_OK:
+            raise ViError(st, "vi_ctx_create failed")
+        self.h = h
+        self.cfg = cfg
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vi_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st != VI_OK:
+            raise ViError(st, self.lib.vi_last_error(self.h).decode(errors="replace"))
+
+    # -- whole method and steps -------------------------------------------
+    def upload(self, rgb, mask):
+        if isinstance(rgb, np.ndarray):
+            rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+        if isinstance(mask, np.ndarray):
+            mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self._keep = (rgb, mask)
+        pr, dr = _ptr(rgb)
+        pm, dm = _ptr(mask)
+        assert dr == dm, "rgb and mask must both be host or both be device memory"
+        T, H, W = mask.shape[:3]
+        self._ck(self.lib.vi_upload(self.h, pr, pm, W, H, T, dr))
+
+    def build_pyramid(self):
+        self._ck(self.lib.vi_build_pyramid(self.h))
+
+    def init_nnf(self, level):
+        self._ck(self.lib.vi_init_nnf(self.h, level))
+
+    def onion_peel(self):
+        self._ck(self.lib.vi_onion_peel(self.h))
+
+    def prepare(self):
+        self._ck(self.lib.vi_prepare(self.h))
+
+    def rescore(self, level):
+        self._ck(self.lib.vi_rescore(self.h, level))
+
+    def ann(self, level, call=0):
+        self._ck(self.lib.vi_ann(self.h, level, call))
+
+    def reconstruct(self, level, want_e=True):
+        e = C.c_float(0.0)
+        self._ck(self.lib.vi_reconstruct(self.h, level, C.byref(e) if want_e else None))
+        return e.value if want_e else None
+
+    def iterate(self, level, n_outer=-1, first_call=0):
+        n = C.c_int(0)
+        e = C.c_float(0.0)
+        self._ck(self.lib.vi_iterate(self.h, level, n_outer, first_call, C.byref(n), C.byref(e)))
+        return n.value, e.value
+
+    def next_level(self, level):
+        self._ck(self.lib.vi_next_level(self.h, level))
+
+    def final(self):
+        self._ck(self.lib.vi_final(self.h))
+
+    def run(self):
+        self._ck(self.lib.vi_run(self.h))
+
+    def energy(self, level):
+        a, b = C.c_double(0.0), C.c_double(0.0)
+        self._ck(self.lib.vi_energy(self.h, level, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    # -- state access ---------------------------------------------------------
+    def level_info(self, level):
+        W, H, T, Cn = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        nh, nt, ns = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self._ck(self.lib.vi_level_info(self.h, level, C.byref(W), C.byref(H), C.byref(T),
+                                        C.byref(Cn), C.byref(nh), C.byref(nt), C.byref(ns)))
+        return dict(W=W.value, H=H.value, T=T.value, C=Cn.value, n_hole=nh.value,
+                    n_target=nt.value, n_source=ns.value)
+
+    def get_channels(self, level, out=None):
+        info = self.level_info(level)
+        if out is None:
+            out = np.empty((info["T"], info["H"], info["W"], info["C"]), np.float32)
+        p, dev = _ptr(out)
+        self._ck(self.lib.vi_get_channels(self.h, level, p, dev))
+        return out
+
+    def set_channels(self, level, x):
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float32)
+        p, dev = _ptr(x)
+        self._ck(self.lib.vi_set_channels(self.h, level, p, dev))
+
+    def get_nnf(self, level):
+        info = self.level_info(level)
+        phi = np.zeros((info["T"], info["H"], info["W"], 3), np.int32)
+        d2 = np.zeros((info["T"], info["H"], info["W"]), np.float32)
+        self._ck(self.lib.vi_get_nnf(self.h, level, phi.ctypes.data, d2.ctypes.data))
+        return phi, d2
+
+    def set_nnf(self, level, phi=None, d2=None):
+        pp = np.ascontiguousarray(phi, np.int32) if phi is not None else None
+        dd = np.ascontiguousarray(d2, np.float32) if d2 is not None else None
+        self._ck(self.lib.vi_set_nnf(self.h, level, pp.ctypes.data if pp is not None else None,
+                                     dd.ctypes.data if dd is not None else None))
+
+    def get_masks(self, level):
+        info = self.level_info(level)
+        code = np.zeros((info["T"], info["H"], info["W"]), np.uint8)
+        self._ck(self.lib.vi_get_masks(self.h, level, code.ctypes.data))
+        return code
+
+    def patch_dist(self, level, pairs):
+        pairs = np.ascontiguousarray(pairs, np.int32).reshape(-1, 6)
+        out = np.zeros(len(pairs), np.float32)
+        self._ck(self.lib.vi_patch_dist(self.h, level, pairs.ctypes.data, len(pairs),
+                                        out.ctypes.data))
+        return out
+
+    def fetch_result(self, out=None):
+        if out is None:
+            info = self.level_info(0)
+            out = np.empty((info["T"], info["H"], info["W"], 3), np.float32)
+        p, dev = _ptr(out)
+        self._ck(self.lib.vi_fetch_result(self.h, p, dev))
+        return out
+
+    def profile(self, enable=True):
+        self._ck(self.lib.vi_profile(self.h, 1 if enable else 0))
+
+    def stats(self):
+        s = ViStats()
+        self._ck(self.lib.vi_get_stats(self.h, C.byref(s)))
+        return dict(evals=s.evals, step_evals=s.step_evals, step_launches=s.step_launches,
+                    step_ms=s.step_ms, step_timed=s.step_timed, outer=list(s.outer),
+                    onion_layers=s.onion_layers, levels=s.levels, launches=s.launches)
+
+
+def auto_levels(mask):
+    mask = np.ascontiguousarray(mask, np.uint8)
+    T, H, W = mask.shape
+    return load().vi_auto_levels(mask.ctypes.data, W, H, T)
+
+
+def inpaint(rgb, mask, **cfg):
+    """Run the whole method on one clip and return the inpainted video."""
+    with Context(**cfg) as ctx:
+        ctx.upload(rgb, mask)
+        ctx.run()
+        return ctx.fetch_result()

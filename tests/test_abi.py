@@ -1,0 +1,79 @@
+"""The C ABI library: it builds, loads, and exports every entry point that
+include/vi.h declares; host-only calls behave. No kernel runs here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1503_05528_gb300 import build as B
+from paper_1503_05528_gb300 import vi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "vi.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vi_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return vi.load()
+
+
+def test_header_and_binding_agree():
+    assert _declared() == sorted(vi.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (vi_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [s for s in _declared() if s not in exported]
+    assert not missing, missing
+    for s in _declared():
+        assert hasattr(lib, s)
+
+
+def test_built_for_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", B.LIB], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_config_defaults_are_the_papers(lib):
+    cfg = vi.default_config()
+    assert cfg.lambda_ == 50.0 and cfg.n_pm == 10 and cfg.rho == 0.5
+    assert cfg.max_outer == 20 and abs(cfg.stop - 0.1 / 255) < 1e-9
+    assert cfg.weighted == 1 and cfg.use_texture == 1 and cfg.storage == 0
+
+
+def test_auto_levels_rule(lib):
+    # hole extent 8 px: fits under 9 at L = 1
+    m = np.zeros((4, 64, 64), np.uint8)
+    m[:, 10:18, 10:18] = 1
+    assert vi.auto_levels(m) == 1
+    # extent 60 px: 60 / 2^(L-1) <= 9 needs L = 4 (60/8 = 7.5)
+    m = np.zeros((4, 240, 320), np.uint8)
+    m[:, 50:110, 100:160] = 1
+    assert vi.auto_levels(m) == 4
+    # a small frame stops the pyramid at a coarsest side of 16 px
+    m = np.zeros((4, 40, 40), np.uint8)
+    m[:, 5:35, 5:35] = 1
+    assert vi.auto_levels(m) == 2
+
+
+def test_context_without_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = vi.default_config()
+    h = ctypes.c_void_p()
+    st = lib.vi_ctx_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert st == 7   # VI_ERR_NO_DEVICE
+    with pytest.raises(vi.ViError):
+        vi.Context()
