@@ -56,7 +56,8 @@ typedef enum {
     VI_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
     VI_ERR_NO_SOURCE = 5,  /* D~ is empty at some level: nothing to copy from */
     VI_ERR_STATE = 6,      /* call out of order (e.g. iterate before upload) */
-    VI_ERR_NO_DEVICE = 7   /* no CUDA device is available */
+    VI_ERR_NO_DEVICE = 7,  /* no CUDA device is available */
+    VI_ERR_TOO_LARGE = 8   /* input larger than the fixed maximum of vi_energy_noalloc */
 } vi_status;
 
 /* Parameters of the method (Sec. 3.7 gives the paper's values). */
@@ -198,6 +199,33 @@ vi_status vi_run(vi_ctx *ctx);
  * E_H = sum over H of d^2 and E_H~ = the same sum over H~ (FP32 distances,
  * FP64 sums). Synchronises. Either output may be NULL. */
 vi_status vi_energy(vi_ctx *ctx, int level, double *E_H_host, double *E_Ht_host);
+
+/* The energy of vi_energy (E_H and E_H~ of Eq. 1, FP32 distances, FP64 sums)
+ * for buffers the caller owns, computed without allocating any device or
+ * host memory. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- a process whose device memory is all
+ * handed out by its own allocator under a fixed budget, or a latency-bound
+ * loop that cannot take the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause.
+ *   chans_dev: device float32 [T][H][W][C], C = 3 or 5 (the layout of
+ *              vi_get_channels); phi_dev: device int32 [T][H][W][3];
+ *   code_dev:  device uint8 [T][H][W] with bit 0 = occluded, bit 1 = target
+ *              (the layout of vi_get_masks); voxels without bit 1 are ignored;
+ *   out_dev:   device double[2] receiving (E_H, E_H~);
+ *   cuda_stream: cudaStream_t the two kernels are launched on (NULL: default).
+ * At most 16,777,216 voxels (W*H*T) per call: larger inputs return
+ * VI_ERR_TOO_LARGE before anything runs. The scratch is one fixed 1 MiB array
+ * in the library's static device memory, held by every GPU that loads the
+ * library until the process exits. The first call on each device looks that
+ * array's device address up (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture. Every call shares the
+ * array, so calls that overlap on the GPU race; calls ordered on one stream
+ * do not (each reads back only what it has just written). Asynchronous: the
+ * result is in out_dev once the stream reaches it. Errors: VI_ERR_ARG (null
+ * pointer, C, sizes), VI_ERR_TOO_LARGE, VI_ERR_CUDA. */
+vi_status vi_energy_noalloc(const float *chans_dev, int C, const int32_t *phi_dev,
+                            const uint8_t *code_dev, int W, int H, int T, double *out_dev,
+                            void *cuda_stream);
 
 /* Sizes of a level: dims, channels, |H|, |H~| and |D~|. Outputs nullable. */
 vi_status vi_level_info(vi_ctx *ctx, int level, int *W, int *H, int *T, int *C,

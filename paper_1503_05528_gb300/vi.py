@@ -18,7 +18,7 @@ from . import build as _build
 
 VI_OK = 0
 STATUS = {0: "VI_OK", 1: "VI_ERR_ARG", 2: "VI_ERR_OOM", 3: "VI_ERR_CUDA", 4: "VI_ERR_TIMEOUT",
-          5: "VI_ERR_NO_SOURCE", 6: "VI_ERR_STATE", 7: "VI_ERR_NO_DEVICE"}
+          5: "VI_ERR_NO_SOURCE", 6: "VI_ERR_STATE", 7: "VI_ERR_NO_DEVICE", 8: "VI_ERR_TOO_LARGE"}
 
 # every entry point declared in include/vi.h
 EXPORTS = [
@@ -27,7 +27,7 @@ EXPORTS = [
     "vi_prepare", "vi_rescore", "vi_ann", "vi_reconstruct", "vi_iterate", "vi_next_level",
     "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
     "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
-    "vi_profile", "vi_get_stats",
+    "vi_profile", "vi_get_stats", "vi_energy_noalloc",
 ]
 
 
@@ -107,6 +107,7 @@ def _declare(L):
     L.vi_fetch_result.argtypes = [vp, vp, i]
     L.vi_profile.argtypes = [vp, i]
     L.vi_get_stats.argtypes = [vp, P(ViStats)]
+    L.vi_energy_noalloc.argtypes = [vp, i, vp, vp, i, i, i, vp, vp]
 
 
 def default_config(**kw):
