@@ -39,7 +39,8 @@ if ROOT not in sys.path:
 METRIC = "patch-distance evals/s (and inpainted voxels/s) vs HBM roofline"
 UNIT = "evals/s"
 WORKLOAD = "layered_320x240x60"
-BYTES_PER_EVAL_FP32_C5 = 125 * 5 * 4      # algorithmic gather of one source patch
+BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
+BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
 
 # dram bytes (read + write) per launch of the PatchMatch step kernel and the
 # evaluations of that launch, from one ncu capture (see profiles/); None when
@@ -223,7 +224,7 @@ def run_gpu(args):
     out_d = torch.empty_like(rgb_d)
     stream = torch.cuda.current_stream()
     ctx = vi.Context(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank,
-                     stream=stream.cuda_stream)
+                     stream=stream.cuda_stream, lanes_per_target=args.lanes)
     n_hole = int(clip.mask.sum())
 
     def step():
@@ -260,6 +261,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     evals = s1["evals"] - s0["evals"]
     step_evals = s1["step_evals"] - s0["step_evals"]
+    step_gathered = s1["step_gathered"] - s0["step_gathered"]
     step_ms = s1["step_ms"] - s0["step_ms"]
     step_launches = s1["step_timed"] - s0["step_timed"]
     launches = s1["launches"] - s0["launches"]
@@ -304,11 +306,16 @@ def run_gpu(args):
         return 0
 
     peak, peak_kind = _peaks()
-    achieved = step_evals * BYTES_PER_EVAL_FP32_C5 / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    # algorithmic bytes of the step kernel: the source voxels it has to gather
+    # (20 B each: 5 FP32 channels). A candidate equal to a shift already
+    # compared needs no gather, and a gather stops once the partial sum shows
+    # the candidate cannot win; both leave every decision unchanged.
+    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5
+    achieved = gathered_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     traffic = None
     if NCU_STEP_TRAFFIC and step_launches:
-        per_eval = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["evals"]
-        traffic = per_eval * step_evals / step_launches
+        per_voxel = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["gathered_voxels"]
+        traffic = per_voxel * step_gathered / step_launches
     line = {
         "metric": METRIC, "value": evals_tot / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -316,6 +323,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "levels": clip.levels, "channels": 5, "storage": "fp32",
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
+                   "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
         "inpainted_voxels_per_s": hole_tot * args.steps / (ms_max / 1e3),
         "evals_per_step": evals / args.steps,
@@ -323,9 +331,14 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "k_ann_step (PatchMatch propagation + random search)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": traffic, "bytes_per_eval": BYTES_PER_EVAL_FP32_C5,
+                     "traffic": traffic,
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels)",
+                     "gathered_bytes_per_launch": gathered_bytes / step_launches if step_launches else None,
                      "launches_timed": step_launches,
                      "evals_per_launch": step_evals / step_launches if step_launches else None,
+                     "evals_per_s_in_kernel": step_evals / (step_ms / 1e3) if step_ms > 0 else None,
+                     "full_eval_bytes": BYTES_PER_EVAL_FP32_C5,
+                     "gathered_bytes_per_eval": gathered_bytes / step_evals if step_evals else None,
                      "kernel_ms_share": step_ms / ms if ms > 0 else None},
         "e2e": {"value": e2e_evals_tot / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": int(clip.rgb.nbytes + clip.mask.nbytes),
@@ -349,6 +362,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="GPU lanes per target in the search kernels (0: chosen per level)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

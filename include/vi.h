@@ -74,6 +74,9 @@ typedef struct {
     int storage;         /* 0: FP32 channel storage (the only value accepted) */
     uint64_t seed;       /* Philox4x32-10 key (key words: low, high 32 bits) */
     uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
+    int lanes_per_target; /* GPU lanes sharing one target in the search kernels:
+                             0 = chosen per level from its size, or 1, 2, 4, 8;
+                             never changes a result, only the speed */
 } vi_config;
 
 /* Per-context counters. evals, step_*: since vi_ctx_create; outer and
@@ -81,6 +84,9 @@ typedef struct {
 typedef struct {
     unsigned long long evals;          /* patch-distance evaluations (Eq. 2 / 7b / 11) */
     unsigned long long step_evals;     /* those made inside the PatchMatch step kernel */
+    unsigned long long step_gathered;  /* source voxels the step kernel read: candidates
+                                          equal to a shift already compared need none,
+                                          and a gather stops once it cannot win */
     unsigned long long step_launches;  /* launches of the PatchMatch step kernel */
     double step_ms;                    /* device time of those launches (profiling on) */
     unsigned long long step_timed;     /* launches included in step_ms */

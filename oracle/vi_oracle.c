@@ -112,17 +112,22 @@ uint32_t vio_uniform_index(uint32_t w, uint32_t n)
  * always inside (sources are in D~). Eq. 2 divides by N = 125.
  * ---------------------------------------------------------------------- */
 
-/* FP32: each term (a - b)^2 is added with one fused multiply-add, channel by
- * channel, in the order above; the sum is then divided by N (or |N'_p|). */
+/* FP32, summed in a fixed order (Eq. 2 itself fixes none): the terms (a - b)^2
+ * of one row (fixed dt, dy; dx ascending, channels ascending) are added with
+ * one fused multiply-add each, starting from 0; the 5 row sums of a slice
+ * (fixed dt) are added in dy order; the 5 slice sums are added in dt order;
+ * the total is divided by N (or |N'_p|). Skipped voxels add nothing. */
 float vio_dist_f32(const float *x, int W, int H, int T, int C,
                    int px, int py, int pt, int sx, int sy, int st, const uint8_t *excl)
 {
     if (sx - R < 0 || sy - R < 0 || st - R < 0 || sx + R >= W || sy + R >= H || st + R >= T)
         return INFINITY;
-    float acc = 0.0f;
+    float total = 0.0f;
     int n = 0;
-    for (int dt = -R; dt <= R; ++dt)
-        for (int dy = -R; dy <= R; ++dy)
+    for (int dt = -R; dt <= R; ++dt) {
+        float slice = 0.0f;
+        for (int dy = -R; dy <= R; ++dy) {
+            float row = 0.0f;
             for (int dx = -R; dx <= R; ++dx) {
                 int rx = px + dx, ry = py + dy, rt = pt + dt;
                 if (!inside(rx, ry, rt, W, H, T))
@@ -133,16 +138,20 @@ float vio_dist_f32(const float *x, int W, int H, int T, int C,
                 size_t s = vidx(sx + dx, sy + dy, st + dt, W, H);
                 for (int c = 0; c < C; ++c) {
                     float df = x[r * (size_t)C + c] - x[s * (size_t)C + c];
-                    acc = fmaf(df, df, acc);
+                    row = fmaf(df, df, row);
                 }
                 ++n;
             }
+            slice = slice + row;
+        }
+        total = total + slice;
+    }
     if (excl) {
         if (n == 0)
             return INFINITY;
-        return acc / (float)n;
+        return total / (float)n;
     }
-    return acc / (float)NPATCH;
+    return total / (float)NPATCH;
 }
 
 /* FP64 evaluation of the same definition (plain summation), for the energy

@@ -86,7 +86,7 @@ struct vi_ctx {
     double *scal = nullptr;        // device scalars
     double *host_scal = nullptr;   // pinned
     int *host_counts = nullptr;    // pinned, 64 ints
-    unsigned long long *evals_dev = nullptr;  // [0] all, [1] step kernel
+    unsigned long long *evals_dev = nullptr;  // [0] rescore evals, [1] step evals, [2] step gathered voxels
 
     uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
     int *layer_list = nullptr, *ltgt_list = nullptr;
@@ -195,7 +195,9 @@ void free_state(vi_ctx *ctx)
 vi_status check_config(vi_ctx *ctx, const vi_config *c)
 {
     if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
-        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || c->storage != 0)
+        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || c->storage != 0 ||
+        !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
+          c->lanes_per_target == 4 || c->lanes_per_target == 8))
         return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
     // rho must be 2^-m, m >= 1
     int m = 0;
@@ -265,7 +267,8 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
 {
     Level &l = ctx->lv[level];
     const LevelView v = l.view();
-    launch_rescore(v, targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream);
+    launch_rescore(v, targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream,
+                   ctx->cfg.lanes_per_target);
     CK_LAUNCH();
     const int rmax = std::max(l.W, std::max(l.H, l.T));
     for (int k = 1; k <= ctx->cfg.n_pm; ++k) {
@@ -288,6 +291,8 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
         a.tag = tag;
         a.clip = ctx->cfg.clip;
         a.evals = ctx->evals_dev + 1;
+        a.gathered = ctx->evals_dev + 2;
+        a.lanes = ctx->cfg.lanes_per_target;
         TRY(step_launch(ctx, a));
     }
     if (ctx->cfg.n_pm & 1) {
@@ -370,6 +375,7 @@ void vi_config_default(vi_config *cfg)
     cfg->storage = 0;
     cfg->seed = 1503;
     cfg->clip = 0;
+    cfg->lanes_per_target = 0;
 }
 
 vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
@@ -406,13 +412,13 @@ vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
     }
     if (cudaMalloc((void **)&ctx->count_dev, 64 * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void **)&ctx->scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&ctx->evals_dev, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->evals_dev, 3 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->host_scal, 8 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->host_counts, 64 * sizeof(int)) != cudaSuccess) {
         vi_ctx_destroy(ctx);
         return VI_ERR_OOM;
     }
-    cudaMemsetAsync(ctx->evals_dev, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    cudaMemsetAsync(ctx->evals_dev, 0, 3 * sizeof(unsigned long long), ctx->stream);
     *out = ctx;
     return VI_OK;
 }
@@ -710,7 +716,7 @@ vi_status vi_rescore(vi_ctx *ctx, int level)
         return fail(ctx, VI_ERR_ARG, "vi_rescore: bad level or no pyramid");
     Level &l = ctx->lv[level];
     launch_rescore(l.view(), l.targets, l.nT, l.phi[0], l.d2[0], nullptr, ctx->c5, ctx->evals_dev,
-                   ctx->stream);
+                   ctx->stream, ctx->cfg.lanes_per_target);
     CK_LAUNCH();
     return VI_OK;
 }
@@ -1042,7 +1048,7 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
     if (!ctx || !out)
         return VI_ERR_ARG;
     std::memset(out, 0, sizeof(*out));
-    unsigned long long ev[2] = {0, 0};
+    unsigned long long ev[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(ev, ctx->evals_dev, sizeof(ev), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i < ctx->events_used; ++i) {
@@ -1054,6 +1060,7 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
     ctx->events_used = 0;
     out->evals = ev[0] + ev[1];
     out->step_evals = ev[1];
+    out->step_gathered = ev[2];
     out->step_launches = ctx->step_launches;
     out->step_ms = ctx->step_ms;
     out->step_timed = ctx->step_timed;

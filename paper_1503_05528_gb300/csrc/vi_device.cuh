@@ -74,13 +74,21 @@ __device__ __forceinline__ uint32_t uniform_index(uint32_t w, uint32_t n)
     return (uint32_t)(((unsigned long long)w * (unsigned long long)n) >> 32);
 }
 
+// ---------------------------------------------------------------------------
 // Squared patch distance between the 5x5x5 patch of target p = (px, py, pt)
-// and the patch of source s (linear index; its patch lies inside the video).
-// Terms are summed in the patch's fixed order (dt, dy, dx ascending, then
-// channels c0..c4), each (a - b)^2 added with one fused multiply-add, and the
-// sum divided by N = 125 (Eq. 2 / 7b). Target voxels outside the video add
-// nothing. With excl != nullptr, voxels r with excl[r] != 0 are left out too
-// and the sum is divided by their complement's count (Eq. 11), +inf if empty.
+// and the patch of source s (linear index; its patch lies inside the video),
+// Eq. 2 / 7b. Target voxels outside the video add nothing; the sum is divided
+// by N = 125. With excl != nullptr, voxels r with excl[r] != 0 are left out
+// too and the sum is divided by the count of voxels kept (Eq. 11), +inf if
+// none.
+//
+// Summation order (the oracle uses the same): the terms (a - b)^2 of one row
+// (fixed dt, dy; dx ascending, channels c0..c4) are accumulated by fused
+// multiply-adds starting from 0; the 5 row sums of a slice (fixed dt) are
+// added in dy order; the 5 slice sums are added in dt order. The five row
+// chains of a slice are independent, so a thread keeps 25 voxel loads and
+// five FMA chains in flight rather than one serial chain of 625 terms.
+// ---------------------------------------------------------------------------
 template <bool C5>
 __device__ __forceinline__ void acc_voxel(const LevelView &L, int r, int s, float &acc)
 {
@@ -97,42 +105,126 @@ __device__ __forceinline__ void acc_voxel(const LevelView &L, int r, int s, floa
     }
 }
 
+// Sum of one whole slice: ro, so = target / source voxel of offset (-2, -2).
+template <bool C5>
+__device__ __forceinline__ float slice_sum(const LevelView &L, int ro, int so)
+{
+    float r[5];
+#pragma unroll
+    for (int dy = 0; dy < 5; ++dy) {
+        r[dy] = 0.0f;
+#pragma unroll
+        for (int dx = 0; dx < 5; ++dx)
+            acc_voxel<C5>(L, ro + dy * L.W + dx, so + dy * L.W + dx, r[dy]);
+    }
+    float s = r[0];
+#pragma unroll
+    for (int dy = 1; dy < 5; ++dy)
+        s = __fadd_rn(s, r[dy]);
+    return s;
+}
+
 template <bool C5>
 __device__ __forceinline__ float patch_d2_interior(const LevelView &L, int p, int s)
 {
     const int W = L.W, HW = L.HW;
     const int off = 2 + 2 * W + 2 * HW;
     const int rb = p - off, sb = s - off;
-    float acc = 0.0f;
+    float total = 0.0f;
+#pragma unroll 1
+    for (int dt = 0; dt < 5; ++dt)
+        total = __fadd_rn(total, slice_sum<C5>(L, rb + dt * HW, sb + dt * HW));
+    return __fdiv_rn(total, 125.0f);
+}
+
+// The same distance for a candidate that only matters if it beats the current
+// best d (an interior target, full distance): after every slice the running
+// total is compared with thr = 125 * best rounded up, and the evaluation stops
+// as soon as the total reaches it, returning +inf. The terms are non-negative,
+// so the total only grows, and dividing by 125 preserves order: a stopped
+// candidate's full distance is >= best, so it would not have been accepted. A
+// completed evaluation returns exactly patch_d2_interior's value. `gathered`
+// counts the source voxels read.
+template <bool C5>
+__device__ __forceinline__ float patch_d2_interior_bounded(const LevelView &L, int p, int s, float best,
+                                                           unsigned &gathered)
+{
+    const int W = L.W, HW = L.HW;
+    const int off = 2 + 2 * W + 2 * HW;
+    const int rb = p - off, sb = s - off;
+    const float thr = __fmul_ru(best, 125.0f);
+    float total = 0.0f;
 #pragma unroll 1
     for (int dt = 0; dt < 5; ++dt) {
-#pragma unroll
-        for (int dy = 0; dy < 5; ++dy) {
-            const int ro = rb + dt * HW + dy * W;
-            const int so = sb + dt * HW + dy * W;
-#pragma unroll
-            for (int dx = 0; dx < 5; ++dx)
-                acc_voxel<C5>(L, ro + dx, so + dx, acc);
-        }
+        total = __fadd_rn(total, slice_sum<C5>(L, rb + dt * HW, sb + dt * HW));
+        gathered += 25;
+        if (total >= thr)
+            return __int_as_float(0x7f800000);
     }
-    return __fdiv_rn(acc, 125.0f);
+    return __fdiv_rn(total, 125.0f);
 }
 
 template <bool C5>
+__device__ __forceinline__ float slice_general(const LevelView &L, int px, int py, int pt, int s, int dt,
+                                               const uint8_t *excl, int &n);
+
+// Targets near the border (clipped patch) and the partial distance of Eq. 11.
+template <bool C5>
 __device__ float patch_d2_general(const LevelView &L, int px, int py, int pt, int s,
-                                  const uint8_t *excl)
+                                  const uint8_t *excl, unsigned *gathered = nullptr)
+{
+    float total = 0.0f;
+    int n = 0;
+#pragma unroll 1
+    for (int dt = -2; dt <= 2; ++dt) {
+        int sn;
+        total = __fadd_rn(total, slice_general<C5>(L, px, py, pt, s, dt, excl, sn));
+        n += sn;
+    }
+    if (gathered)
+        *gathered += (unsigned)n;
+    if (excl) {
+        if (n == 0)
+            return __int_as_float(0x7f800000);
+        return __fdiv_rn(total, (float)n);
+    }
+    return __fdiv_rn(total, 125.0f);
+}
+
+// acc_voxel for a voxel that may be skipped: both loads are issued from valid
+// addresses; a skipped voxel adds fma(0, 0, acc) = acc exactly.
+template <bool C5>
+__device__ __forceinline__ void acc_voxel_if(const LevelView &L, int r, int s, bool use, float &acc)
+{
+    const float4 a = __ldg(L.x4 + r);
+    const float4 b = __ldg(L.x4 + s);
+    float df;
+    df = use ? __fsub_rn(a.x, b.x) : 0.0f; acc = __fmaf_rn(df, df, acc);
+    df = use ? __fsub_rn(a.y, b.y) : 0.0f; acc = __fmaf_rn(df, df, acc);
+    df = use ? __fsub_rn(a.z, b.z) : 0.0f; acc = __fmaf_rn(df, df, acc);
+    df = use ? __fsub_rn(a.w, b.w) : 0.0f; acc = __fmaf_rn(df, df, acc);
+    if (C5) {
+        const float a1 = __ldg(L.x1 + r), b1 = __ldg(L.x1 + s);
+        df = use ? __fsub_rn(a1, b1) : 0.0f;
+        acc = __fmaf_rn(df, df, acc);
+    }
+}
+
+// One slice (fixed dt offset in [-2, 2]) of a clipped or partial distance:
+// the row sums over in-video, non-excluded target voxels, added in dy order;
+// n receives the number of voxels used.
+template <bool C5>
+__device__ __forceinline__ float slice_general(const LevelView &L, int px, int py, int pt, int s, int dt,
+                                               const uint8_t *excl, int &n)
 {
     const int W = L.W, HW = L.HW;
-    float acc = 0.0f;
-    int n = 0;
-    for (int dt = -2; dt <= 2; ++dt) {
-        const int rt = pt + dt;
-        if ((unsigned)rt >= (unsigned)L.T)
-            continue;
-        for (int dy = -2; dy <= 2; ++dy) {
-            const int ry = py + dy;
-            if ((unsigned)ry >= (unsigned)L.H)
-                continue;
+    const int rt = pt + dt;
+    float slice = 0.0f;
+    n = 0;
+    for (int dy = -2; dy <= 2; ++dy) {
+        const int ry = py + dy;
+        float row = 0.0f;
+        if ((unsigned)rt < (unsigned)L.T && (unsigned)ry < (unsigned)L.H) {
             for (int dx = -2; dx <= 2; ++dx) {
                 const int rx = px + dx;
                 if ((unsigned)rx >= (unsigned)W)
@@ -140,17 +232,110 @@ __device__ float patch_d2_general(const LevelView &L, int px, int py, int pt, in
                 const int r = rt * HW + ry * W + rx;
                 if (excl && excl[r])
                     continue;
-                acc_voxel<C5>(L, r, s + dt * HW + dy * W + dx, acc);
+                acc_voxel<C5>(L, r, s + dt * HW + dy * W + dx, row);
                 ++n;
             }
         }
+        slice = __fadd_rn(slice, row);
     }
-    if (excl) {
+    return slice;
+}
+
+// The same slice, fully unrolled and predicated, so that its 25 voxel loads
+// are independent (a skipped target voxel reads the source voxel instead and
+// contributes nothing). Used for the partial distance, where any voxel may
+// be excluded.
+template <bool C5>
+__device__ __forceinline__ float slice_masked(const LevelView &L, int px, int py, int pt, int s, int dt,
+                                              const uint8_t *excl, int &n)
+{
+    const int W = L.W, HW = L.HW;
+    const int rt = pt + dt;
+    const bool t_ok = (unsigned)rt < (unsigned)L.T;
+    float slice = 0.0f;
+    n = 0;
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy) {
+        const int ry = py + dy;
+        const bool y_ok = t_ok && (unsigned)ry < (unsigned)L.H;
+        float row = 0.0f;
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx) {
+            const int rx = px + dx;
+            const int sv = s + dt * HW + dy * W + dx;
+            bool use = y_ok && (unsigned)rx < (unsigned)W;
+            const int r = use ? rt * HW + ry * W + rx : sv;
+            if (excl)
+                use = use && !excl[r];
+            acc_voxel_if<C5>(L, r, sv, use, row);
+            n += use ? 1 : 0;
+        }
+        slice = __fadd_rn(slice, row);
+    }
+    return slice;
+}
+
+// The distance computed by a group of G lanes (G = 1, 2, 4 or 8 consecutive
+// lanes of a warp; gmask is the group's lane mask, sub the lane's rank in it).
+// Lane sub gathers the slices dt = sub, sub + G, ...; the group adds the slice
+// sums in dt order with shuffles, so every lane holds the same total, in the
+// same order as patch_d2_interior / patch_d2_general: the value is bit-
+// identical for every G. Slices are gathered in rounds of G; after each round
+// the running total is compared with 125 * best rounded up (the full-distance
+// case only) and the evaluation stops as soon as it is reached, returning +inf
+// (the total only grows, so the candidate could not win). best = +inf gives
+// the unbounded distance. `gathered` counts the source voxels this lane read.
+// PARTIAL selects the distance of Eq. 11 (excl = H', every voxel tested).
+// Otherwise excl is ignored; a target whose patch stays inside the frame
+// (x and y at least 2 from the border) takes the unrolled slice_sum for each
+// slice inside the video and adds 0 for a slice outside it (the same terms,
+// in the same order, as slice_general).
+template <bool C5, int G, bool PARTIAL>
+__device__ __forceinline__ float group_d2(const LevelView &L, int p, int px, int py, int pt, int s,
+                                          const uint8_t *excl, float best, int sub, unsigned gmask,
+                                          unsigned &gathered)
+{
+    const int HW = L.HW;
+    const int off = 2 + 2 * L.W + 2 * HW;
+    const bool frame_inside = px >= 2 && px < L.W - 2 && py >= 2 && py < L.H - 2;
+    const float thr = __fmul_ru(best, 125.0f);
+    float total = 0.0f;
+    int n = 0;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 5; r0 += G) {
+        const int dt = r0 + sub;
+        float mine = 0.0f;
+        int my_n = 0;
+        if (dt < 5) {
+            if (PARTIAL) {
+                mine = slice_masked<C5>(L, px, py, pt, s, dt - 2, excl, my_n);
+            } else if (frame_inside) {
+                if ((unsigned)(pt + dt - 2) < (unsigned)L.T) {
+                    mine = slice_sum<C5>(L, p - off + dt * HW, s - off + dt * HW);
+                    my_n = 25;
+                }
+            } else {
+                mine = slice_general<C5>(L, px, py, pt, s, dt - 2, nullptr, my_n);
+            }
+            gathered += (unsigned)my_n;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (r0 + j < 5) {
+                total = __fadd_rn(total, G == 1 ? mine : __shfl_sync(gmask, mine, j, G));
+                if (PARTIAL)
+                    n += G == 1 ? my_n : __shfl_sync(gmask, my_n, j, G);
+            }
+        }
+        if (!PARTIAL && total >= thr)
+            return __int_as_float(0x7f800000);
+    }
+    if (PARTIAL) {
         if (n == 0)
             return __int_as_float(0x7f800000);
-        return __fdiv_rn(acc, (float)n);
+        return __fdiv_rn(total, (float)n);
     }
-    return __fdiv_rn(acc, 125.0f);
+    return __fdiv_rn(total, 125.0f);
 }
 
 template <bool C5>

@@ -55,12 +55,15 @@ struct AnnArgs {
     int rmax;
     int rho_log2;          // rho = 2^-rho_log2
     uint32_t key0, key1, tag, clip;
-    unsigned long long *evals;
+    unsigned long long *evals;     // candidate evaluations (valid candidates)
+    unsigned long long *gathered;  // source voxels actually read
+    int lanes;                     // lanes per target (1, 2, 4, 8); 0: by target count
 };
 void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st);
 // d_out[p] = distance of target p to p + phi[p] (in place allowed).
 void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
-                    const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st);
+                    const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st,
+                    int lanes = 0);
 void launch_copy_targets(const int *targets, int nT, const Shift *phi_src, const float *d_src,
                          Shift *phi_dst, float *d_dst, cudaStream_t st);
 void launch_init_nnf(LevelView L, const int *targets, int nT, const int *sources, int nS,

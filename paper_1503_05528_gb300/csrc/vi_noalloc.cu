@@ -30,35 +30,38 @@ static constexpr long long VI_NOALLOC_MAX_VOXELS = (long long)VI_NOALLOC_MAX_BLO
 // Per-block (E_H, E_H~) partial sums of the last call.
 static __device__ __align__(256) double g_energy_scratch[2 * VI_NOALLOC_MAX_BLOCKS];
 
-// Squared patch distance on the [V][C] layout of the ABI, terms summed in the
-// patch order (dt, dy, dx ascending, then channels), one fused multiply-add
-// per term, divided by N = 125 (Eq. 2 / Eq. 7b).
+// Squared patch distance on the [V][C] layout of the ABI (Eq. 2 / Eq. 7b), in
+// the library's summation order: per row (fixed dt, dy) fused multiply-adds
+// over dx and channels from 0, row sums added in dy order, slice sums in dt
+// order, divided by N = 125.
 __device__ float d2_abi_layout(const float *__restrict__ x, int C, int W, int H, int T, int px, int py,
                                int pt, int sx, int sy, int st)
 {
-    float acc = 0.0f;
+    float total = 0.0f;
     for (int dt = -2; dt <= 2; ++dt) {
         const int rt = pt + dt;
-        if ((unsigned)rt >= (unsigned)T)
-            continue;
+        float slice = 0.0f;
         for (int dy = -2; dy <= 2; ++dy) {
             const int ry = py + dy;
-            if ((unsigned)ry >= (unsigned)H)
-                continue;
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int rx = px + dx;
-                if ((unsigned)rx >= (unsigned)W)
-                    continue;
-                const long long r = ((long long)rt * H + ry) * W + rx;
-                const long long s = ((long long)(st + dt) * H + (sy + dy)) * W + (sx + dx);
-                for (int c = 0; c < C; ++c) {
-                    const float df = __fsub_rn(x[r * C + c], x[s * C + c]);
-                    acc = __fmaf_rn(df, df, acc);
+            float row = 0.0f;
+            if ((unsigned)rt < (unsigned)T && (unsigned)ry < (unsigned)H) {
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int rx = px + dx;
+                    if ((unsigned)rx >= (unsigned)W)
+                        continue;
+                    const long long r = ((long long)rt * H + ry) * W + rx;
+                    const long long s = ((long long)(st + dt) * H + (sy + dy)) * W + (sx + dx);
+                    for (int c = 0; c < C; ++c) {
+                        const float df = __fsub_rn(x[r * C + c], x[s * C + c]);
+                        row = __fmaf_rn(df, df, row);
+                    }
                 }
             }
+            slice = __fadd_rn(slice, row);
         }
+        total = __fadd_rn(total, slice);
     }
-    return __fdiv_rn(acc, 125.0f);
+    return __fdiv_rn(total, 125.0f);
 }
 
 // One thread per voxel; targets (code bit 1) add d^2(W_p, W_{p+phi(p)}) to

@@ -28,11 +28,81 @@ __device__ __forceinline__ int source_of(const LevelView &L, int px, int py, int
     return (L.code[s] & CODE_SOURCE) ? s : -1;
 }
 
-template <bool C5>
+__device__ __forceinline__ unsigned long long shift_key(int dx, int dy, int dt)
+{
+    return ((unsigned long long)(unsigned short)dx) | ((unsigned long long)(unsigned short)dy << 16) |
+           ((unsigned long long)(unsigned short)dt << 32);
+}
+
+// Shifts rejected so far in one iteration (at most 3 need remembering).
+struct Rejected {
+    unsigned long long k0 = ~0ull, k1 = ~0ull, k2 = ~0ull;
+    __device__ __forceinline__ bool has(unsigned long long k) const { return k == k0 || k == k1 || k == k2; }
+    __device__ __forceinline__ void add(unsigned long long k)
+    {
+        k2 = k1;
+        k1 = k0;
+        k0 = k;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Lane groups. A coarse level has too few targets to fill 152 SMs with one
+// thread each, and one thread's candidates are a chain of dependent memory
+// round trips. So G consecutive lanes (G = 1, 2, 4, 8; chosen from the target
+// count) share a target: they make the same decisions on the same data and
+// split each distance's five slices between them (group_d2). PARTIAL selects
+// the partial distance of Eq. 11 (onion peel).
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ unsigned group_mask()
+{
+    return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+}
+
+// One candidate of Algorithm 1 for target p: counted as an evaluation when it
+// lands in D~ (the oracle counts the same). A candidate equal to the current
+// best shift, or to one already rejected in this iteration, has that shift's
+// distance, which cannot be strictly smaller than the current best, so it is
+// resolved without a gather. Otherwise the G lanes of the group gather its
+// distance, bounded by the current best; the decision is the same bit for bit
+// as with a full evaluation.
+template <bool C5, int G, bool PARTIAL>
+__device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px, int py, int pt, int s,
+                                                int cdx, int cdy, int cdt, Shift &cur, float &d,
+                                                Rejected &rej, unsigned &evals, unsigned &gathered, int sub,
+                                                unsigned gmask)
+{
+    if (s < 0)
+        return;
+    ++evals;
+    const unsigned long long key = shift_key(cdx, cdy, cdt);
+    if (key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key))
+        return;
+    const float dd = group_d2<C5, G, PARTIAL>(a.L, p, px, py, pt, s, a.excl, d, sub, gmask, gathered);
+    if (dd < d) {
+        d = dd;
+        cur.dx = (short)cdx;
+        cur.dy = (short)cdy;
+        cur.dt = (short)cdt;
+    } else {
+        rej.add(key);
+    }
+}
+
+// One PatchMatch iteration k for every target: propagation from the three
+// neighbours (Algorithm 1; sign by the parity of k), then the random search
+// of Eq. 3 around the propagated shift. Reads phi_in / d_in (the state when
+// iteration k began), writes phi_out / d_out. The three neighbours' shifts and
+// their sources' set codes are loaded together before any distance.
+template <bool C5, int G, bool PARTIAL>
 __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned evals = 0;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / G;
+    const int sub = gt & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    unsigned evals = 0, gathered = 0;
     if (i < a.nT) {
         const LevelView &L = a.L;
         const int p = a.targets[i];
@@ -42,28 +112,23 @@ __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
         float d = a.d_in[p];
         const int sg = (a.k & 1) ? 1 : -1;   // odd k: +1 neighbours; even k: -1
 
-        // propagation: candidates phi(p + sg e_x), phi(p + sg e_y), phi(p + sg e_t)
-#pragma unroll 1
-        for (int ax = 0; ax < 3; ++ax) {
-            const int rx = px + (ax == 0 ? sg : 0);
-            const int ry = py + (ax == 1 ? sg : 0);
-            const int rt = pt + (ax == 2 ? sg : 0);
-            if (!inside(L, rx, ry, rt))
-                continue;
-            const int r = rt * L.HW + ry * L.W + rx;
-            if (!(a.tmask[r] & a.tbit))
-                continue;
-            const Shift c = a.phi_in[r];
-            const int s = source_of(L, px, py, pt, c.dx, c.dy, c.dt);
-            if (s < 0)
-                continue;
-            const float dd = patch_d2<C5>(L, p, px, py, pt, s, a.excl);
-            ++evals;
-            if (dd < d) {
-                d = dd;
-                cur = c;
-            }
-        }
+        // propagation candidates phi(p + sg e_x), phi(p + sg e_y), phi(p + sg e_t)
+        const bool in0 = inside(L, px + sg, py, pt), in1 = inside(L, px, py + sg, pt),
+                   in2 = inside(L, px, py, pt + sg);
+        const int r0 = in0 ? p + sg : p, r1 = in1 ? p + sg * L.W : p, r2 = in2 ? p + sg * L.HW : p;
+        const bool t0 = in0 && (a.tmask[r0] & a.tbit), t1 = in1 && (a.tmask[r1] & a.tbit),
+                   t2 = in2 && (a.tmask[r2] & a.tbit);
+        const Shift c0 = a.phi_in[r0], c1 = a.phi_in[r1], c2 = a.phi_in[r2];
+        const int s0 = t0 ? source_of(L, px, py, pt, c0.dx, c0.dy, c0.dt) : -1;
+        const int s1 = t1 ? source_of(L, px, py, pt, c1.dx, c1.dy, c1.dt) : -1;
+        const int s2 = t2 ? source_of(L, px, py, pt, c2.dx, c2.dy, c2.dt) : -1;
+        Rejected rej;
+        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s0, c0.dx, c0.dy, c0.dt, cur, d, rej, evals,
+                                        gathered, sub, gmask);
+        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s1, c1.dx, c1.dy, c1.dt, cur, d, rej, evals,
+                                        gathered, sub, gmask);
+        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s2, c2.dx, c2.dy, c2.dt, cur, d, rej, evals,
+                                        gathered, sub, gmask);
 
         // random search (Eq. 3)
         const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)a.k, a.clip, 0u),
@@ -72,21 +137,45 @@ __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
         const int cdx = cur.dx + random_offset(w.x, a.rmax, shift);
         const int cdy = cur.dy + random_offset(w.y, a.rmax, shift);
         const int cdt = cur.dt + random_offset(w.z, a.rmax, shift);
-        const int s = source_of(L, px, py, pt, cdx, cdy, cdt);
-        if (s >= 0) {
-            const float dd = patch_d2<C5>(L, p, px, py, pt, s, a.excl);
-            ++evals;
-            if (dd < d) {
-                d = dd;
-                cur.dx = (short)cdx;
-                cur.dy = (short)cdy;
-                cur.dt = (short)cdt;
-            }
+        const int s3 = source_of(L, px, py, pt, cdx, cdy, cdt);
+        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s3, cdx, cdy, cdt, cur, d, rej, evals, gathered,
+                                        sub, gmask);
+        if (sub == 0) {
+            a.phi_out[p] = cur;
+            a.d_out[p] = d;
         }
-        a.phi_out[p] = cur;
-        a.d_out[p] = d;
     }
-    count_evals(a.evals, evals);
+    count_evals(a.evals, sub == 0 ? evals : 0u);
+    count_evals(a.gathered, gathered);
+}
+
+// Lanes per target: the smallest G in {1, 2, 4, 8} that gives the level at
+// least 512 threads per SM. Measured on the 320x240x60 workload (one launch,
+// microseconds, G = 1 / 2 / 4 / 8): 445k targets 280 / 301 / 447 / 681,
+// 126k targets 101 / 108 / 147 / 207, 40k targets 79 / 51 / 60 / 82, 15k
+// targets 78 / 46 / 37 / 34: more lanes pay only while the targets alone
+// leave the SMs idle. The partial distance (onion peel, coarsest level, few
+// targets) always uses G = 8.
+static int pick_group(int nT)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    const long long want = (long long)sms * 512;
+    int G = 1;
+    while (G < 8 && (long long)nT * G < want)
+        G *= 2;
+    return G;
+}
+
+template <bool C5, int G, bool PARTIAL>
+static void launch_ann_step_g(const AnnArgs &a, cudaStream_t st)
+{
+    k_ann_step<C5, G, PARTIAL><<<blocks_for((long long)a.nT * G, 256), 256, 0, st>>>(a);
 }
 
 void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
@@ -94,19 +183,35 @@ void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
     if (a.nT <= 0)
         return;
     VI_COUNT_LAUNCH();
-    if (c5)
-        k_ann_step<true><<<blocks_for(a.nT, 256), 256, 0, st>>>(a);
-    else
-        k_ann_step<false><<<blocks_for(a.nT, 256), 256, 0, st>>>(a);
+    if (a.excl) {
+        if (c5)
+            launch_ann_step_g<true, 8, true>(a, st);
+        else
+            launch_ann_step_g<false, 8, true>(a, st);
+        return;
+    }
+    switch ((a.lanes > 0 ? a.lanes : pick_group(a.nT)) * 2 + (c5 ? 1 : 0)) {
+    case 2: launch_ann_step_g<false, 1, false>(a, st); break;
+    case 3: launch_ann_step_g<true, 1, false>(a, st); break;
+    case 4: launch_ann_step_g<false, 2, false>(a, st); break;
+    case 5: launch_ann_step_g<true, 2, false>(a, st); break;
+    case 8: launch_ann_step_g<false, 4, false>(a, st); break;
+    case 9: launch_ann_step_g<true, 4, false>(a, st); break;
+    case 16: launch_ann_step_g<false, 8, false>(a, st); break;
+    default: launch_ann_step_g<true, 8, false>(a, st); break;
+    }
 }
 
-template <bool C5>
+template <bool C5, int G, bool PARTIAL>
 __global__ void __launch_bounds__(256) k_rescore(LevelView L, const int *__restrict__ targets, int nT,
                                                  const Shift *__restrict__ phi, float *__restrict__ d_out,
                                                  const uint8_t *excl, unsigned long long *evals_ctr)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned evals = 0;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / G;
+    const int sub = gt & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    unsigned evals = 0, gathered = 0;
     if (i < nT) {
         const int p = targets[i];
         int px, py, pt;
@@ -115,24 +220,46 @@ __global__ void __launch_bounds__(256) k_rescore(LevelView L, const int *__restr
         const int s = source_of(L, px, py, pt, c.dx, c.dy, c.dt);
         float d = __int_as_float(0x7f800000);
         if (s >= 0) {
-            d = patch_d2<C5>(L, p, px, py, pt, s, excl);
+            d = group_d2<C5, G, PARTIAL>(L, p, px, py, pt, s, excl, d, sub, gmask, gathered);
             ++evals;
         }
-        d_out[p] = d;
+        if (sub == 0)
+            d_out[p] = d;
     }
-    count_evals(evals_ctr, evals);
+    count_evals(evals_ctr, sub == 0 ? evals : 0u);
+}
+
+template <bool C5, int G, bool PARTIAL>
+static void launch_rescore_g(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
+                             const uint8_t *excl, unsigned long long *evals, cudaStream_t st)
+{
+    k_rescore<C5, G, PARTIAL><<<blocks_for((long long)nT * G, 256), 256, 0, st>>>(L, targets, nT, phi,
+                                                                                  d_out, excl, evals);
 }
 
 void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
-                    const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st)
+                    const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st, int lanes)
 {
     if (nT <= 0)
         return;
     VI_COUNT_LAUNCH();
-    if (c5)
-        k_rescore<true><<<blocks_for(nT, 256), 256, 0, st>>>(L, targets, nT, phi, d_out, excl, evals);
-    else
-        k_rescore<false><<<blocks_for(nT, 256), 256, 0, st>>>(L, targets, nT, phi, d_out, excl, evals);
+    if (excl) {
+        if (c5)
+            launch_rescore_g<true, 8, true>(L, targets, nT, phi, d_out, excl, evals, st);
+        else
+            launch_rescore_g<false, 8, true>(L, targets, nT, phi, d_out, excl, evals, st);
+        return;
+    }
+    switch ((lanes > 0 ? lanes : pick_group(nT)) * 2 + (c5 ? 1 : 0)) {
+    case 2: launch_rescore_g<false, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 3: launch_rescore_g<true, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 4: launch_rescore_g<false, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 5: launch_rescore_g<true, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 8: launch_rescore_g<false, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 9: launch_rescore_g<true, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 16: launch_rescore_g<false, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    default: launch_rescore_g<true, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    }
 }
 
 __global__ void k_copy_targets(const int *__restrict__ targets, int nT, const Shift *__restrict__ ps,

@@ -35,11 +35,12 @@ class ViConfig(C.Structure):
     _fields_ = [("lambda_", C.c_float), ("n_pm", C.c_int), ("rho", C.c_float),
                 ("levels", C.c_int), ("max_outer", C.c_int), ("stop", C.c_float),
                 ("weighted", C.c_int), ("use_texture", C.c_int), ("storage", C.c_int),
-                ("seed", C.c_uint64), ("clip", C.c_uint32)]
+                ("seed", C.c_uint64), ("clip", C.c_uint32), ("lanes_per_target", C.c_int)]
 
 
 class ViStats(C.Structure):
     _fields_ = [("evals", C.c_ulonglong), ("step_evals", C.c_ulonglong),
+                ("step_gathered", C.c_ulonglong),
                 ("step_launches", C.c_ulonglong), ("step_ms", C.c_double),
                 ("step_timed", C.c_ulonglong), ("outer", C.c_int * 16),
                 ("onion_layers", C.c_int), ("levels", C.c_int), ("launches", C.c_ulonglong)]
@@ -283,7 +284,8 @@ class Context:
     def stats(self):
         s = ViStats()
         self._ck(self.lib.vi_get_stats(self.h, C.byref(s)))
-        return dict(evals=s.evals, step_evals=s.step_evals, step_launches=s.step_launches,
+        return dict(evals=s.evals, step_evals=s.step_evals, step_gathered=s.step_gathered,
+                    step_launches=s.step_launches,
                     step_ms=s.step_ms, step_timed=s.step_timed, outer=list(s.outer),
                     onion_layers=s.onion_layers, levels=s.levels, launches=s.launches)
 

@@ -122,10 +122,35 @@ def test_ann_bit_exact(case, n_pm, call):
             x, phi, d2 = _state(lv, level, 31)
             ctx.set_channels(level, x)
             ctx.set_nnf(level, phi, d2)
+            e0 = ctx.stats()["evals"]
             ctx.ann(level, call)
+            g_evals = ctx.stats()["evals"] - e0
             gphi, gd2 = ctx.get_nnf(level)
-            O.ann(x, lv.htilde, lv.dtilde, phi, d2, n_pm=n_pm, schedule="JAC", key=(31, 0),
-                  tag_base=O.tag(O.PURPOSE_SEARCH, level, call))
+            o_evals = O.ann(x, lv.htilde, lv.dtilde, phi, d2, n_pm=n_pm, schedule="JAC", key=(31, 0),
+                            tag_base=O.tag(O.PURPOSE_SEARCH, level, call))
+            m = lv.htilde == 1
+            assert (gphi[m] == phi[m]).all()
+            assert (gd2[m].view(np.uint32) == d2[m].view(np.uint32)).all()
+            # the same candidates were compared (valid candidates of Algorithm 1)
+            assert g_evals == o_evals
+
+
+@pytest.mark.parametrize("case", ["layered_tex", "odd_sizes", "tiny_rgb"])
+def test_ann_five_iterations_bit_exact(case):
+    spec = CASES[case]
+    clip = spec["clip"]()
+    pyr = O.build_pyramid(clip.rgb, clip.mask, spec["levels"], spec["tex"])
+    with vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=37, n_pm=5) as ctx:
+        ctx.upload(clip.rgb, clip.mask)
+        ctx.build_pyramid()
+        for level, lv in enumerate(pyr):
+            x, phi, d2 = _state(lv, level, 37)
+            ctx.set_channels(level, x)
+            ctx.set_nnf(level, phi, d2)
+            ctx.ann(level, 2)
+            gphi, gd2 = ctx.get_nnf(level)
+            O.ann(x, lv.htilde, lv.dtilde, phi, d2, n_pm=5, schedule="JAC", key=(37, 0),
+                  tag_base=O.tag(O.PURPOSE_SEARCH, level, 2))
             m = lv.htilde == 1
             assert (gphi[m] == phi[m]).all()
             assert (gd2[m].view(np.uint32) == d2[m].view(np.uint32)).all()
