@@ -12,10 +12,12 @@ Output: one JSON line (rank 0). `value` is patch-distance evaluations per
 second over the whole job (all ranks), inputs resident in device memory when
 the timed region starts. `e2e` is the same metric through the same calls with
 host buffers (host->device upload and device->host fetch inside the timed
-region). `roofline` is the PatchMatch step kernel's algorithmic gather bytes
-(125 voxels x C channels x 4 bytes per evaluation) over its CUDA-event time,
+region). `roofline` is the PatchMatch step kernel's gathered source bytes
+(20 B per source voxel read; a full evaluation is 125 voxels = 2,500 B, and
+exact pruning skips or shortens most of them) over its CUDA-event time,
 against the measured HBM copy bandwidth. `cpu_baseline` times the CPU oracle
 (sequential PatchMatch, one thread) on a bounded sample of the same workload.
+--workload layered_1280x720x100 selects the HD clip (5 levels).
 
 Multi-GPU (torchrun): replicas only -- each rank inpaints its own clip; no
 collective on the data path; barrier + max-over-ranks timing.
@@ -42,10 +44,24 @@ WORKLOAD = "layered_320x240x60"
 BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
 BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
 
-# dram bytes (read + write) per launch of the PatchMatch step kernel and the
-# evaluations of that launch, from one ncu capture (see profiles/); None when
-# the kernel changed since the capture.
+# dram bytes (read + write) of one launch of the PatchMatch step kernel and the
+# source voxels that launch gathered, from one ncu capture (see profiles/);
+# None when the kernel changed since the capture.
 NCU_STEP_TRAFFIC = None
+
+
+def combine_ranks(values, dist=None, device="cpu"):
+    """(max over ranks, sum over ranks) of a list of floats. With one rank
+    (dist None or not initialised) both are the values themselves."""
+    import torch
+    if dist is None or not dist.is_initialized():
+        return list(values), list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
 
 
 def _peaks():
@@ -115,11 +131,19 @@ def _dist():
     return world, rank, local
 
 
-def make_clip(rank):
+WORKLOADS = {
+    # name: (W, H, T, sprites, sprite px, hole fraction, levels, seed offset, dynamic texture)
+    "layered_320x240x60": (320, 240, 60, 3, (20, 50), 0.08, 4, 2, False),
+    "layered_1280x720x100": (1280, 720, 100, 6, (40, 160), 0.05, 5, 3, True),
+}
+
+
+def make_clip(rank, workload=WORKLOAD):
     from paper_1503_05528_gb300 import synth
+    W, H, T, ns, sp, frac, L, off, dyn = WORKLOADS[workload]
     # weak scaling: every rank inpaints its own clip of the same size
-    return synth.layered_clip(320, 240, 60, 3, (20, 50), 0.08, 4, synth.BASE_SEED + 2 + rank,
-                              name=WORKLOAD)
+    return synth.layered_clip(W, H, T, ns, sp, frac, L, synth.BASE_SEED + off + rank,
+                              dynamic_texture=dyn, name=workload)
 
 
 # ---------------------------------------------------------------------------
@@ -170,7 +194,7 @@ def cpu_baseline(clip, seconds):
         frames += 2
     return {"value": evals / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"sequential ANN search (rescore + 10 PatchMatch iterations) over the "
-                      f"level-0 targets of {frames} frames of {WORKLOAD}: {evals} evaluations "
+                      f"level-0 targets of {frames} frames of {clip.name}: {evals} evaluations "
                       f"in {el:.1f} s, one thread"}
 
 
@@ -178,7 +202,7 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    clip = make_clip(0)
+    clip = make_clip(0, args.workload)
     smp = OracleSample(clip)
     frames = 2
     for _ in range(args.warmup):
@@ -193,10 +217,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{frames} frames per step"},
+            "config": {"workload": args.workload, "sample": f"{frames} frames per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: sequential ANN search over the level-0 "
-                                       f"targets of {frames} frames of {WORKLOAD}, one thread"},
+                                       f"targets of {frames} frames of {args.workload}, one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -218,7 +242,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vi.load(build_if_missing=True)
-    clip = make_clip(rank)
+    clip = make_clip(rank, args.workload)
     rgb_d = torch.from_numpy(clip.rgb).cuda()
     mask_d = torch.from_numpy(clip.mask).cuda()
     out_d = torch.empty_like(rgb_d)
@@ -287,18 +311,9 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t
     e2e_evals = ctx.stats()["evals"] - se["evals"]
 
-    vals = torch.tensor([ms, float(evals), float(n_hole), e2e_s, float(e2e_evals)], dtype=torch.float64,
-                        device="cuda")
-    if dist:
-        mx = vals.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = vals.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_max, evals_tot, hole_tot = mx[0].item(), sm[1].item(), sm[2].item()
-        e2e_max, e2e_evals_tot = mx[3].item(), sm[4].item()
-    else:
-        ms_max, evals_tot, hole_tot = ms, float(evals), float(n_hole)
-        e2e_max, e2e_evals_tot = e2e_s, float(e2e_evals)
+    mx, sm = combine_ranks([ms, float(evals), float(n_hole), e2e_s, float(e2e_evals)], dist, "cuda")
+    ms_max, evals_tot, hole_tot = mx[0], sm[1], sm[2]
+    e2e_max, e2e_evals_tot = mx[3], sm[4]
     ctx.close()
     if rank != 0:
         if dist:
@@ -321,7 +336,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "levels": clip.levels, "channels": 5, "storage": "fp32",
+        "config": {"workload": args.workload, "levels": clip.levels, "channels": 5, "storage": "fp32",
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
                    "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
@@ -362,6 +377,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--lanes", type=int, default=0,
                     help="GPU lanes per target in the search kernels (0: chosen per level)")
     args = ap.parse_args()
