@@ -267,6 +267,60 @@ vi_status vi_profile(vi_ctx *ctx, int enable);
 /* The context's counters (synchronises to read event times). */
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many clips, one launch per step.
+ *
+ * A batch runs the same method (Algorithm 4 without realignment) on many
+ * clips of different sizes at once. Each clip keeps its own pyramid, levels,
+ * seed and stopping rule; a round (vi_batch_step) runs one search and
+ * reconstruction iteration (vi_ann + vi_reconstruct) for every clip still
+ * iterating, whatever its level, in single launches that cover the targets
+ * and occluded voxels of all of them, then applies each clip's stopping rule,
+ * level transition and final step. Clips can be added and removed between
+ * rounds (continuous batching). Each clip's result is bit-identical to
+ * vi_run on that clip alone with the same vi_config. All work is ordered on
+ * the batch's stream; a batch is used by one thread at a time.
+ * ------------------------------------------------------------------------- */
+typedef struct vi_batch vi_batch;
+
+/* Creates an empty batch. cfg: defaults for its clips (use_texture and n_pm
+ * are fixed for the whole batch); cuda_stream: NULL for an own stream. */
+vi_status vi_batch_create(const vi_config *cfg, void *cuda_stream, vi_batch **out);
+void vi_batch_destroy(vi_batch *b);
+const char *vi_batch_last_error(const vi_batch *b);
+
+/* Adds a clip (copied, as vi_upload) and prepares it (vi_prepare: pyramid,
+ * initialisation, onion peel) on the batch's stream; job_cfg (nullable: the
+ * batch's cfg) sets its seed, clip tag, levels and stopping parameters.
+ * *id_out receives the clip's id. */
+vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, const uint8_t *mask,
+                       int W, int H, int T, int ptr_is_device, int *id_out);
+
+/* One round for every iterating clip (synchronises once). *n_active (nullable)
+ * receives the number of clips still iterating afterwards. */
+vi_status vi_batch_step(vi_batch *b, int *n_active);
+
+/* Rounds until no clip is iterating. */
+vi_status vi_batch_run(vi_batch *b);
+
+/* *done: 1 finished, 0 iterating, -1 failed; *level: its current level. */
+vi_status vi_batch_poll(vi_batch *b, int id, int *done, int *level);
+
+/* The inpainted video of a finished clip (as vi_fetch_result). */
+vi_status vi_batch_fetch(vi_batch *b, int id, float *rgb_out, int ptr_is_device);
+
+/* Releases a clip's device state. */
+vi_status vi_batch_remove(vi_batch *b, int id);
+
+/* A clip's counters (as vi_get_stats). */
+vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out);
+
+/* Batch counters: patch-distance evaluations (batch launches plus the clips'
+ * own launches), source voxels gathered by the batch step launches, rounds.
+ * Synchronises. Outputs nullable. */
+vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned long long *gathered,
+                             unsigned long long *rounds);
+
 #ifdef __cplusplus
 }
 #endif

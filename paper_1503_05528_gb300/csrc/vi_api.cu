@@ -14,94 +14,18 @@
 #include <utility>
 #include <vector>
 
-#include "vi.h"
-#include "vi_launch.h"
+#include "vi_ctx.h"
 
 using namespace vi;
 
 std::atomic<unsigned long long> vi::g_launch_count{0};
 
-namespace {
-
-// Philox tag word: purpose (4 bits) | level (4) | call (16) | k (8).
-enum : uint32_t { PURPOSE_INIT = 1, PURPOSE_SEARCH = 2, PURPOSE_UPSAMPLE = 3, PURPOSE_ONION = 4 };
-
-uint32_t make_tag(uint32_t purpose, int level, int call)
+vi_status vi::ctx_fail(vi_ctx *ctx, vi_status st, const std::string &msg)
 {
-    return ((purpose & 0xFu) << 28) | (((uint32_t)level & 0xFu) << 24) | (((uint32_t)call & 0xFFFFu) << 8);
+    if (ctx)
+        ctx->err = msg;
+    return st;
 }
-
-struct Level {
-    int W = 0, H = 0, T = 0;
-    int V = 0;
-    float4 *x4 = nullptr;
-    float *x1 = nullptr;
-    uint8_t *code = nullptr;
-    Shift *phi[2] = {nullptr, nullptr};
-    float *d2[2] = {nullptr, nullptr};
-    int *targets = nullptr, *holes = nullptr, *sources = nullptr;
-    int nT = 0, nH = 0, nS = 0;
-
-    LevelView view() const
-    {
-        LevelView v;
-        v.W = W;
-        v.H = H;
-        v.T = T;
-        v.HW = W * H;
-        v.V = V;
-        v.x4 = x4;
-        v.x1 = x1;
-        v.code = code;
-        return v;
-    }
-};
-
-}  // namespace
-
-struct vi_ctx {
-    vi_config cfg{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::string err;
-    bool c5 = true;
-    int rho_log2 = 1;
-
-    int W = 0, H = 0, T = 0;
-    int V0 = 0;
-    int L = 0;
-    float *rgb = nullptr;
-    uint8_t *mask = nullptr;
-    float *out_rgb = nullptr;      // staging of vi_fetch_result to host memory
-    float2 *T0 = nullptr;
-    std::vector<Level> lv;
-
-    uint8_t *tmpA = nullptr, *tmpB = nullptr;
-    int *block_counts = nullptr;
-    int *count_dev = nullptr;      // 64 ints
-    float *partials = nullptr;
-    int partials_cap = 0;
-    double *partials2 = nullptr;
-    int partials2_cap = 0;
-    double *scal = nullptr;        // device scalars
-    double *host_scal = nullptr;   // pinned
-    int *host_counts = nullptr;    // pinned, 64 ints
-    unsigned long long *evals_dev = nullptr;  // [0] rescore evals, [1] step evals, [2] step gathered voxels
-
-    uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
-    int *layer_list = nullptr, *ltgt_list = nullptr;
-
-    bool uploaded = false, built = false;
-    unsigned long long step_launches = 0;
-    int outer[16] = {0};
-    int onion_layers = 0;
-
-    bool profiling = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-    size_t events_used = 0;
-    double step_ms = 0.0;
-    unsigned long long step_timed = 0;
-};
 
 namespace {
 
@@ -305,7 +229,7 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
 vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
 {
     Level &l = ctx->lv[level];
-    TRY(ensure_partials(ctx, vote_blocks(std::max(l.nH, 1))));
+    TRY(ensure_partials(ctx, std::max(l.nH, 1)));
     VoteArgs a;
     a.L = l.view();
     a.list = l.holes;
@@ -320,11 +244,17 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
     launch_vote(a, ctx->c5, ctx->stream);
     CK_LAUNCH();
     if (change_dev) {
-        launch_sum_partials(ctx->partials, vote_blocks(std::max(l.nH, 1)), change_dev, ctx->stream);
+        launch_sum_partials(ctx->partials, l.nH, change_dev, ctx->stream);
         CK_LAUNCH();
     }
     return VI_OK;
 }
+
+}  // namespace
+
+vi_status vi::ctx_ensure_partials(vi_ctx *ctx, int n) { return ensure_partials(ctx, n); }
+
+namespace {
 
 int host_auto_levels(const uint8_t *mask, int W, int H, int T)
 {
@@ -614,7 +544,7 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         max_list = std::max(max_list, lv.nH);
         max_t = std::max(max_t, lv.nT);
     }
-    TRY(ensure_partials(ctx, vote_blocks(max_list)));
+    TRY(ensure_partials(ctx, max_list));
     TRY(ensure_partials2(ctx, energy_blocks(max_t)));
     ctx->built = true;
     return VI_OK;
@@ -654,7 +584,7 @@ vi_status vi_onion_peel(vi_ctx *ctx)
         TRY(dalloc(ctx, &ctx->layer_list, V * sizeof(int)));
         TRY(dalloc(ctx, &ctx->ltgt_list, V * sizeof(int)));
     }
-    TRY(ensure_partials(ctx, vote_blocks(l.V)));
+    TRY(ensure_partials(ctx, l.V));
     launch_extract_bit(l.code, CODE_HOLE, ctx->hp, l.V, st);
     CK_LAUNCH();
     launch_count(ctx->hp, l.V, ctx->count_dev + 60, st);

@@ -1,0 +1,103 @@
+// vi_ctx.h -- the context structure behind the vi_ctx handle of the C ABI,
+// shared by the single-clip runtime (vi_api.cu) and the batch runtime
+// (vi_batch.cu). Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vi.h"
+#include "vi_launch.h"
+
+namespace vi {
+
+// Philox tag word: purpose (4 bits) | level (4) | call (16) | k (8).
+enum : uint32_t { PURPOSE_INIT = 1, PURPOSE_SEARCH = 2, PURPOSE_UPSAMPLE = 3, PURPOSE_ONION = 4 };
+
+inline uint32_t make_tag(uint32_t purpose, int level, int call)
+{
+    return ((purpose & 0xFu) << 28) | (((uint32_t)level & 0xFu) << 24) | (((uint32_t)call & 0xFFFFu) << 8);
+}
+
+// Device buffers of one pyramid level.
+struct Level {
+    int W = 0, H = 0, T = 0;
+    int V = 0;
+    float4 *x4 = nullptr;
+    float *x1 = nullptr;
+    uint8_t *code = nullptr;
+    Shift *phi[2] = {nullptr, nullptr};
+    float *d2[2] = {nullptr, nullptr};
+    int *targets = nullptr, *holes = nullptr, *sources = nullptr;
+    int nT = 0, nH = 0, nS = 0;
+
+    LevelView view() const
+    {
+        LevelView v;
+        v.W = W;
+        v.H = H;
+        v.T = T;
+        v.HW = W * H;
+        v.V = V;
+        v.x4 = x4;
+        v.x1 = x1;
+        v.code = code;
+        return v;
+    }
+};
+
+}  // namespace vi
+
+struct vi_ctx {
+    vi_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    bool c5 = true;
+    int rho_log2 = 1;
+
+    int W = 0, H = 0, T = 0;
+    int V0 = 0;
+    int L = 0;
+    float *rgb = nullptr;
+    uint8_t *mask = nullptr;
+    float *out_rgb = nullptr;      // staging of vi_fetch_result to host memory
+    float2 *T0 = nullptr;
+    std::vector<vi::Level> lv;
+
+    uint8_t *tmpA = nullptr, *tmpB = nullptr;
+    int *block_counts = nullptr;
+    int *count_dev = nullptr;      // 64 ints
+    float *partials = nullptr;     // per-voxel (vote) or per-block reduction scratch
+    int partials_cap = 0;
+    double *partials2 = nullptr;
+    int partials2_cap = 0;
+    double *scal = nullptr;        // device scalars
+    double *host_scal = nullptr;   // pinned
+    int *host_counts = nullptr;    // pinned, 64 ints
+    unsigned long long *evals_dev = nullptr;  // [0] rescore evals, [1] step evals, [2] step gathered voxels
+
+    uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
+    int *layer_list = nullptr, *ltgt_list = nullptr;
+
+    bool uploaded = false, built = false;
+    unsigned long long step_launches = 0;
+    int outer[16] = {0};
+    int onion_layers = 0;
+
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    double step_ms = 0.0;
+    unsigned long long step_timed = 0;
+};
+
+namespace vi {
+// Records a failure on a context (or nothing for a null context).
+vi_status ctx_fail(vi_ctx *ctx, vi_status st, const std::string &msg);
+// Grows ctx->partials to hold at least n floats.
+vi_status ctx_ensure_partials(vi_ctx *ctx, int n);
+}  // namespace vi

@@ -349,6 +349,21 @@ __device__ __forceinline__ float patch_d2(const LevelView &L, int p, int px, int
     return patch_d2_general<C5>(L, px, py, pt, s, excl);
 }
 
+// Index of the segment holding global index i: prefix[c] <= i < prefix[c+1]
+// (prefix has n + 1 ascending entries; batches of clips).
+__device__ __forceinline__ int find_segment(const int *__restrict__ prefix, int n, int i)
+{
+    int lo = 0, hi = n;   // invariant: prefix[lo] <= i < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

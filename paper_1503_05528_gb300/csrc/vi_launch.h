@@ -93,12 +93,36 @@ int vote_blocks(int n);
 void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st);
 // out[0] = sum of partials[0..n) in a fixed order.
 void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st);
+// out[i] = sum of vals[starts[i] .. starts[i+1]) in the same fixed order
+// (starts in device memory, nseg + 1 entries).
+void launch_segment_sums(const float *vals, const int *starts, int nseg, double *out, cudaStream_t st);
 void launch_final(LevelView L, const int *holes, int nH, const Shift *phi, const float *d2,
                   bool c5, cudaStream_t st);
 int energy_blocks(int n);
 void launch_energy(LevelView L, const int *targets, int nT, const Shift *phi, bool c5,
                    double *partials2, cudaStream_t st);
 void launch_sum_partials2(const double *partials2, int n, double *out2, cudaStream_t st);
+// ---- batches of clips (one launch for the current level of every clip) -----
+// odd: arguments of the odd PatchMatch iterations (read buffer 0, write 1);
+// even: the even ones (read 1, write 0); vote: the clip's reconstruction,
+// whose partials point at the clip's slice of the batch's per-voxel array;
+// d0: buffer 0 of the distances (written by the batch rescore).
+struct BatchClip {
+    AnnArgs odd;
+    AnnArgs even;
+    VoteArgs vote;
+    float *d0;
+};
+// clips[c] owns targets [tprefix[c], tprefix[c+1]) / holes [hprefix[c],
+// hprefix[c+1]); prefixes in device memory (n + 1 entries); totals on the host.
+void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+                           bool c5, unsigned long long *evals, unsigned long long *gathered, int lanes,
+                           cudaStream_t st);
+void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
+                          unsigned long long *evals, int lanes, cudaStream_t st);
+void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int total_holes, bool c5,
+                       cudaStream_t st);
+
 // Onion peel sets on the coarsest level (Algorithm 3).
 void launch_onion_layer(LevelView L, const uint8_t *hp, uint8_t *layer, cudaStream_t st);
 void launch_onion_targets(LevelView L, const uint8_t *hp, const uint8_t *layer, uint8_t *ltgt,

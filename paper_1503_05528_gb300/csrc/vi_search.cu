@@ -95,22 +95,20 @@ __device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px,
 // of Eq. 3 around the propagated shift. Reads phi_in / d_in (the state when
 // iteration k began), writes phi_out / d_out. The three neighbours' shifts and
 // their sources' set codes are loaded together before any distance.
+// The step for target i of the clip described by a (iteration k), by the G
+// lanes of one group.
 template <bool C5, int G, bool PARTIAL>
-__global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
+__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub, unsigned gmask,
+                                        unsigned &evals, unsigned &gathered)
 {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / G;
-    const int sub = gt & (G - 1);
-    const unsigned gmask = group_mask<G>();
-    unsigned evals = 0, gathered = 0;
-    if (i < a.nT) {
+    {
         const LevelView &L = a.L;
         const int p = a.targets[i];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);
         Shift cur = a.phi_in[p];
         float d = a.d_in[p];
-        const int sg = (a.k & 1) ? 1 : -1;   // odd k: +1 neighbours; even k: -1
+        const int sg = (k & 1) ? 1 : -1;   // odd k: +1 neighbours; even k: -1
 
         // propagation candidates phi(p + sg e_x), phi(p + sg e_y), phi(p + sg e_t)
         const bool in0 = inside(L, px + sg, py, pt), in1 = inside(L, px, py + sg, pt),
@@ -131,9 +129,9 @@ __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
                                         gathered, sub, gmask);
 
         // random search (Eq. 3)
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)a.k, a.clip, 0u),
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip, 0u),
                                       a.key0, a.key1);
-        const int shift = a.rho_log2 * a.k + 24;
+        const int shift = a.rho_log2 * k + 24;
         const int cdx = cur.dx + random_offset(w.x, a.rmax, shift);
         const int cdy = cur.dy + random_offset(w.y, a.rmax, shift);
         const int cdt = cur.dt + random_offset(w.z, a.rmax, shift);
@@ -145,8 +143,145 @@ __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
             a.d_out[p] = d;
         }
     }
+}
+
+template <bool C5, int G, bool PARTIAL>
+__global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
+{
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / G;
+    const int sub = gt & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    unsigned evals = 0, gathered = 0;
+    if (i < a.nT)
+        ann_one<C5, G, PARTIAL>(a, i, a.k, sub, gmask, evals, gathered);
     count_evals(a.evals, sub == 0 ? evals : 0u);
     count_evals(a.gathered, gathered);
+}
+
+static int pick_group(int nT);
+
+// Batch form: the targets of n clips in one persistent launch. Clip c owns
+// the global target indices [prefix[c], prefix[c+1]) and is described by
+// descs[c]; every clip runs iteration k. A grid-stride loop over groups keeps
+// the grid at the resident size whatever the batch holds.
+template <bool C5, int G>
+__global__ void __launch_bounds__(256) k_ann_step_batch(const BatchClip *__restrict__ clips,
+                                                        const int *__restrict__ prefix, int n, int k,
+                                                        unsigned long long *evals_ctr,
+                                                        unsigned long long *gathered_ctr)
+{
+    const int total = __ldg(prefix + n);
+    const int sub = (blockIdx.x * blockDim.x + threadIdx.x) & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    const int stride = gridDim.x * blockDim.x / G;
+    unsigned evals = 0, gathered = 0;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
+        const int c = find_segment(prefix, n, g);
+        const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
+        ann_one<C5, G, false>(a, g - __ldg(prefix + c), k, sub, gmask, evals, gathered);
+    }
+    count_evals(evals_ctr, sub == 0 ? evals : 0u);
+    count_evals(gathered_ctr, gathered);
+}
+
+// Grid of a persistent batch launch: one wave of 256-thread blocks, or fewer
+// when the work is smaller.
+static int persistent_grid(long long threads)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    const long long cap = (long long)sms * 8;   // 8 blocks of 256 threads per SM
+    const long long need = (threads + 255) / 256;
+    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+template <bool C5, int G>
+static void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, int total, int k,
+                                    unsigned long long *evals, unsigned long long *gathered, cudaStream_t st)
+{
+    k_ann_step_batch<C5, G><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, k, evals,
+                                                                                  gathered);
+}
+
+void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+                           bool c5, unsigned long long *evals, unsigned long long *gathered, int lanes,
+                           cudaStream_t st)
+{
+    if (total_targets <= 0 || n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    switch ((lanes > 0 ? lanes : pick_group(total_targets)) * 2 + (c5 ? 1 : 0)) {
+    case 2: launch_ann_step_batch_g<false, 1>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 3: launch_ann_step_batch_g<true, 1>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 4: launch_ann_step_batch_g<false, 2>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 5: launch_ann_step_batch_g<true, 2>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 8: launch_ann_step_batch_g<false, 4>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 9: launch_ann_step_batch_g<true, 4>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    case 16: launch_ann_step_batch_g<false, 8>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    default: launch_ann_step_batch_g<true, 8>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
+    }
+}
+
+// Distances of the current shifts (buffer 0) for every target of a batch.
+template <bool C5, int G>
+__global__ void __launch_bounds__(256) k_rescore_batch(const BatchClip *__restrict__ clips,
+                                                       const int *__restrict__ prefix, int n,
+                                                       unsigned long long *evals_ctr)
+{
+    const int total = __ldg(prefix + n);
+    const int sub = (blockIdx.x * blockDim.x + threadIdx.x) & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    const int stride = gridDim.x * blockDim.x / G;
+    unsigned evals = 0, gathered = 0;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
+        const int c = find_segment(prefix, n, g);
+        const AnnArgs &a = clips[c].odd;
+        const LevelView &L = a.L;
+        const int p = a.targets[g - __ldg(prefix + c)];
+        int px, py, pt;
+        decode(p, L.W, L.HW, px, py, pt);
+        const Shift f = a.phi_in[p];
+        const int s = source_of(L, px, py, pt, f.dx, f.dy, f.dt);
+        float d = __int_as_float(0x7f800000);
+        if (s >= 0) {
+            d = group_d2<C5, G, false>(L, p, px, py, pt, s, nullptr, d, sub, gmask, gathered);
+            ++evals;
+        }
+        if (sub == 0)
+            clips[c].d0[p] = d;
+    }
+    count_evals(evals_ctr, sub == 0 ? evals : 0u);
+}
+
+template <bool C5, int G>
+static void launch_rescore_batch_g(const BatchClip *clips, const int *tprefix, int n, int total,
+                                   unsigned long long *evals, cudaStream_t st)
+{
+    k_rescore_batch<C5, G><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, evals);
+}
+
+void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
+                          unsigned long long *evals, int lanes, cudaStream_t st)
+{
+    if (total_targets <= 0 || n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    switch ((lanes > 0 ? lanes : pick_group(total_targets)) * 2 + (c5 ? 1 : 0)) {
+    case 2: launch_rescore_batch_g<false, 1>(clips, tprefix, n, total_targets, evals, st); break;
+    case 3: launch_rescore_batch_g<true, 1>(clips, tprefix, n, total_targets, evals, st); break;
+    case 4: launch_rescore_batch_g<false, 2>(clips, tprefix, n, total_targets, evals, st); break;
+    case 5: launch_rescore_batch_g<true, 2>(clips, tprefix, n, total_targets, evals, st); break;
+    case 8: launch_rescore_batch_g<false, 4>(clips, tprefix, n, total_targets, evals, st); break;
+    case 9: launch_rescore_batch_g<true, 4>(clips, tprefix, n, total_targets, evals, st); break;
+    case 16: launch_rescore_batch_g<false, 8>(clips, tprefix, n, total_targets, evals, st); break;
+    default: launch_rescore_batch_g<true, 8>(clips, tprefix, n, total_targets, evals, st); break;
+    }
 }
 
 // Lanes per target: the smallest G in {1, 2, 4, 8} that gives the level at

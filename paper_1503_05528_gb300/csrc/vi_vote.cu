@@ -25,17 +25,13 @@ int vote_blocks(int n) { return blocks_for(n, VOTE_WARPS); }
 //     non-negative d2 with warp-wide counts;
 //  3. s_q = exp(-d2(q) / (2 sigma_p^2)) (limit 1/0 for sigma_p = 0; 1 when
 //     unweighted); each lane accumulates s_q u(p + phi(q)) over all channels;
-//  4. warp sums; lane 0 writes u(p) and adds |u_new - u_old| (RGB) to the
-//     block's change.
+//  4. warp sums; lane 0 writes u(p) and stores |u_new - u_old| summed over
+//     R, G, B in the voxel's slot of partials.
 template <bool C5>
-__global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
+__device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
 {
-    __shared__ float block_change[VOTE_WARPS];
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int item = blockIdx.x * VOTE_WARPS + wid;
     float change = 0.0f;
-    if (item < a.n) {
+    {
         const LevelView &L = a.L;
         const int p = a.list[item];
         int px, py, pt;
@@ -127,16 +123,49 @@ __global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
                     a.hp[p] = 0;
             }
         }
+        if (lane == 0)
+            a.partials[item] = change;   // one value per voxel, summed in a fixed order
     }
-    if (lane == 0)
-        block_change[wid] = change;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f;
-        for (int w = 0; w < VOTE_WARPS; ++w)
-            s += block_change[w];
-        a.partials[blockIdx.x] = s;
+}
+
+template <bool C5>
+__global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
+{
+    const int item = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5);
+    if (item < a.n)
+        vote_one<C5>(a, item, threadIdx.x & 31);
+}
+
+// Batch form: warp g of the launch grid-strides over the occluded voxels of
+// all clips; clip c owns [prefix[c], prefix[c+1]).
+template <bool C5>
+__global__ void __launch_bounds__(VOTE_BLOCK) k_vote_batch(const BatchClip *__restrict__ clips,
+                                                           const int *__restrict__ prefix, int n)
+{
+    const int total = __ldg(prefix + n);
+    const int nwarps = gridDim.x * VOTE_WARPS;
+    for (int g = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5); g < total; g += nwarps) {
+        const int c = find_segment(prefix, n, g);
+        vote_one<C5>(clips[c].vote, g - __ldg(prefix + c), threadIdx.x & 31);
     }
+}
+
+void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int total_holes, bool c5,
+                       cudaStream_t st)
+{
+    if (total_holes <= 0 || n <= 0)
+        return;
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = vote_blocks(total_holes);
+    if (grid > sms * 8)
+        grid = sms * 8;
+    VI_COUNT_LAUNCH();
+    if (c5)
+        k_vote_batch<true><<<grid, VOTE_BLOCK, 0, st>>>(clips, hprefix, n);
+    else
+        k_vote_batch<false><<<grid, VOTE_BLOCK, 0, st>>>(clips, hprefix, n);
 }
 
 void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st)
@@ -150,14 +179,16 @@ void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st)
         k_vote<false><<<vote_blocks(a.n), VOTE_BLOCK, 0, st>>>(a);
 }
 
-// Deterministic sum of per-block partials: each thread a strided slice, then
-// a fixed-order tree in shared memory.
-__global__ void k_sum_partials(const float *__restrict__ partials, int n, double *out)
+// Deterministic sum of n values by one block of 256 threads: thread j adds
+// elements j, j + 256, ... in FP64, then a fixed-order tree in shared
+// memory. The result depends only on the values, not on where they sit, so a
+// clip's sum is the same alone and inside a batch.
+__device__ double block_sum_range(const float *__restrict__ v, int n)
 {
     __shared__ double s[256];
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += 256)
-        acc += (double)partials[i];
+        acc += (double)v[i];
     s[threadIdx.x] = acc;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -165,14 +196,42 @@ __global__ void k_sum_partials(const float *__restrict__ partials, int n, double
             s[threadIdx.x] += s[threadIdx.x + o];
         __syncthreads();
     }
+    const double r = s[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_sum_partials(const float *__restrict__ partials, int n, double *out)
+{
+    const double r = block_sum_range(partials, n);
     if (threadIdx.x == 0)
-        out[0] = s[0];
+        out[0] = r;
 }
 
 void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st)
 {
     VI_COUNT_LAUNCH();
     k_sum_partials<<<1, 256, 0, st>>>(partials, n, out);
+}
+
+// One block per segment [starts[i], starts[i+1]) of vals.
+__global__ void k_segment_sums(const float *__restrict__ vals, const int *__restrict__ starts, int nseg,
+                               double *out)
+{
+    const int i = blockIdx.x;
+    if (i >= nseg)
+        return;
+    const double r = block_sum_range(vals + starts[i], starts[i + 1] - starts[i]);
+    if (threadIdx.x == 0)
+        out[i] = r;
+}
+
+void launch_segment_sums(const float *vals, const int *starts, int nseg, double *out, cudaStream_t st)
+{
+    if (nseg <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    k_segment_sums<<<nseg, 256, 0, st>>>(vals, starts, nseg, out);
 }
 
 // Eq. 6: the occluded voxel p copies u(p + phi(q*)), q* = argmin d2(q) over

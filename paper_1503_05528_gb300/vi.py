@@ -28,6 +28,9 @@ EXPORTS = [
     "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
     "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
     "vi_profile", "vi_get_stats", "vi_energy_noalloc",
+    "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
+    "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
+    "vi_batch_get_stats",
 ]
 
 
@@ -109,6 +112,20 @@ def _declare(L):
     L.vi_profile.argtypes = [vp, i]
     L.vi_get_stats.argtypes = [vp, P(ViStats)]
     L.vi_energy_noalloc.argtypes = [vp, i, vp, vp, i, i, i, vp, vp]
+    ull = C.c_ulonglong
+    L.vi_batch_create.argtypes = [P(ViConfig), vp, P(vp)]
+    L.vi_batch_destroy.argtypes = [vp]
+    L.vi_batch_destroy.restype = None
+    L.vi_batch_last_error.argtypes = [vp]
+    L.vi_batch_last_error.restype = C.c_char_p
+    L.vi_batch_add.argtypes = [vp, P(ViConfig), vp, vp, i, i, i, i, P(i)]
+    L.vi_batch_step.argtypes = [vp, P(i)]
+    L.vi_batch_run.argtypes = [vp]
+    L.vi_batch_poll.argtypes = [vp, i, P(i), P(i)]
+    L.vi_batch_fetch.argtypes = [vp, i, vp, i]
+    L.vi_batch_remove.argtypes = [vp, i]
+    L.vi_batch_clip_stats.argtypes = [vp, i, P(ViStats)]
+    L.vi_batch_get_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
 
 
 def default_config(**kw):
@@ -288,6 +305,103 @@ class Context:
                     step_launches=s.step_launches,
                     step_ms=s.step_ms, step_timed=s.step_timed, outer=list(s.outer),
                     onion_layers=s.onion_layers, levels=s.levels, launches=s.launches)
+
+
+def _stats_dict(s):
+    return dict(evals=s.evals, step_evals=s.step_evals, step_gathered=s.step_gathered,
+                step_launches=s.step_launches, step_ms=s.step_ms, step_timed=s.step_timed,
+                outer=list(s.outer), onion_layers=s.onion_layers, levels=s.levels,
+                launches=s.launches)
+
+
+class Batch:
+    """A batch of clips (``vi_batch``): one launch per step for all of them."""
+
+    def __init__(self, cfg=None, stream=None, **kw):
+        self.lib = load()
+        if cfg is None:
+            cfg = default_config(**kw)
+        self.cfg = cfg
+        self.defaults = dict(kw)
+        h = C.c_void_p()
+        st = self.lib.vi_batch_create(C.byref(cfg), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != VI_OK:
+            raise ViError(st, "vi_batch_create failed")
+        self.h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _ck(self, st):
+        if st != VI_OK:
+            raise ViError(st, self.lib.vi_batch_last_error(self.h).decode(errors="replace"))
+
+    def add(self, rgb, mask, **job):
+        """Adds and prepares a clip; job overrides the batch's config fields
+        (seed, clip, levels, ...). Returns the clip id."""
+        cfg = default_config(**{**self.defaults, **job})
+        if isinstance(rgb, np.ndarray):
+            rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+        if isinstance(mask, np.ndarray):
+            mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        pr, dr = _ptr(rgb)
+        pm, dm = _ptr(mask)
+        assert dr == dm
+        T, H, W = mask.shape[:3]
+        cid = C.c_int(-1)
+        self._ck(self.lib.vi_batch_add(self.h, C.byref(cfg), pr, pm, W, H, T, dr, C.byref(cid)))
+        self._keep[cid.value] = (rgb, mask, (T, H, W))
+        return cid.value
+
+    def step(self):
+        n = C.c_int(0)
+        self._ck(self.lib.vi_batch_step(self.h, C.byref(n)))
+        return n.value
+
+    def run(self):
+        self._ck(self.lib.vi_batch_run(self.h))
+
+    def poll(self, cid):
+        done, level = C.c_int(0), C.c_int(0)
+        self._ck(self.lib.vi_batch_poll(self.h, cid, C.byref(done), C.byref(level)))
+        return done.value, level.value
+
+    def fetch(self, cid, out=None):
+        if out is None:
+            T, H, W = self._keep[cid][2]
+            out = np.empty((T, H, W, 3), np.float32)
+        p, dev = _ptr(out)
+        self._ck(self.lib.vi_batch_fetch(self.h, cid, p, dev))
+        return out
+
+    def remove(self, cid):
+        self._ck(self.lib.vi_batch_remove(self.h, cid))
+        self._keep.pop(cid, None)
+
+    def clip_stats(self, cid):
+        s = ViStats()
+        self._ck(self.lib.vi_batch_clip_stats(self.h, cid, C.byref(s)))
+        return _stats_dict(s)
+
+    def stats(self):
+        e, g, r = C.c_ulonglong(0), C.c_ulonglong(0), C.c_ulonglong(0)
+        self._ck(self.lib.vi_batch_get_stats(self.h, C.byref(e), C.byref(g), C.byref(r)))
+        return dict(evals=e.value, gathered=g.value, rounds=r.value)
 
 
 def auto_levels(mask):

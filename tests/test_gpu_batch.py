@@ -1,0 +1,82 @@
+"""Batches of uneven clips (vi_batch_*): every clip's inpainted video, shift
+map and iteration counts are bit-identical to the same clip run alone with
+vi_run, whether the batch is filled up front or clips join and leave while
+others are iterating (continuous batching)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1503_05528_gb300 import synth, vi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    vi.load(build_if_missing=True)
+
+
+# uneven clips: (W, H, T, levels, hole fraction, seed)
+SPECS = [(72, 56, 14, 2, 0.08, 1601), (96, 64, 10, 2, 0.05, 1602), (48, 40, 12, 1, 0.10, 1603),
+         (120, 80, 16, 3, 0.06, 1604), (64, 64, 8, 1, 0.08, 1605), (88, 48, 20, 2, 0.12, 1606)]
+
+
+def _clip(spec):
+    W, H, T, L, frac, seed = spec
+    return synth.layered_clip(W, H, T, 2, (10, 20), frac, L, seed, name=f"c{seed}")
+
+
+def _alone(clip, seed, tag):
+    with vi.Context(levels=clip.levels, seed=seed, clip=tag) as ctx:
+        ctx.upload(clip.rgb, clip.mask)
+        ctx.run()
+        out = ctx.fetch_result()
+        phi, _ = ctx.get_nnf(0)
+        st = ctx.stats()
+    return out, phi, st["outer"][:clip.levels]
+
+
+def test_batch_equals_alone():
+    clips = [_clip(s) for s in SPECS]
+    with vi.Batch() as b:
+        ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=100 + i, clip=i) for i, c in enumerate(clips)]
+        b.run()
+        for i, (cid, c) in enumerate(zip(ids, clips)):
+            assert b.poll(cid) == (1, 0)
+            got = b.fetch(cid)
+            want, _, outer = _alone(c, 100 + i, i)
+            assert (got.view(np.uint32) == want.view(np.uint32)).all(), i
+            assert b.clip_stats(cid)["outer"][:c.levels] == outer
+        s = b.stats()
+        assert s["rounds"] >= 1 and s["evals"] > 0
+
+
+def test_continuous_batching_join_and_leave():
+    clips = [_clip(s) for s in SPECS[:4]]
+    with vi.Batch() as b:
+        first = [b.add(c.rgb, c.mask, levels=c.levels, seed=200 + i, clip=i) for i, c in enumerate(clips[:2])]
+        b.step()
+        b.step()
+        late = b.add(clips[2].rgb, clips[2].mask, levels=clips[2].levels, seed=202, clip=2)
+        gone = b.add(clips[3].rgb, clips[3].mask, levels=clips[3].levels, seed=203, clip=3)
+        b.step()
+        b.remove(gone)                       # leaves while iterating
+        n = 1
+        while n:
+            n = b.step()
+        for i, cid in enumerate(first + [late]):
+            want, _, _ = _alone(clips[i], 200 + i, i)
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
+        with pytest.raises(vi.ViError):
+            b.poll(gone)
+
+
+def test_batch_rejects_mismatched_channels():
+    with vi.Batch(use_texture=1) as b:
+        c = _clip(SPECS[2])
+        with pytest.raises(vi.ViError):
+            b.add(c.rgb, c.mask, use_texture=0)
