@@ -315,11 +315,18 @@ vi_status vi_batch_remove(vi_batch *b, int id);
 /* A clip's counters (as vi_get_stats). */
 vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out);
 
-/* Batch counters: patch-distance evaluations (batch launches plus the clips'
- * own launches), source voxels gathered by the batch step launches, rounds.
+/* Batch counters: patch-distance evaluations (batch launches plus the own
+ * launches of every clip added so far, removed ones included), source voxels
+ * gathered by the batch step launches, rounds.
  * Synchronises. Outputs nullable. */
 vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned long long *gathered,
                              unsigned long long *rounds);
+
+/* Device-time profiling of the batch PatchMatch step launches (events on the
+ * batch's stream around each launch), and its totals since creation: summed
+ * milliseconds and the evaluations those launches made. Synchronises. */
+vi_status vi_batch_profile(vi_batch *b, int enable);
+vi_status vi_batch_step_time(vi_batch *b, double *step_ms, unsigned long long *step_evals);
 
 #ifdef __cplusplus
 }

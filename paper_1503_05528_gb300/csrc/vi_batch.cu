@@ -57,6 +57,12 @@ struct vi_batch {
     long long change_cap = 0;
     unsigned long long *counters = nullptr;          // evals, step evals, gathered
     unsigned long long rounds = 0;
+    unsigned long long removed_evals = 0;            // own evaluations of removed clips
+
+    bool profiling = false;                          // events around the step launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+    double step_ms = 0.0;
 };
 
 namespace {
@@ -201,6 +207,10 @@ void vi_batch_destroy(vi_batch *b)
     if (b->h_e) cudaFreeHost(b->h_e);
     if (b->d_change) cudaFree(b->d_change);
     if (b->counters) cudaFree(b->counters);
+    for (auto &e : b->events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
     if (b->own_stream && b->stream)
         cudaStreamDestroy(b->stream);
     delete b;
@@ -315,9 +325,25 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
         const int *tpre = b->d_prefix, *hpre = b->d_prefix + b->cap + 1;
         const int lanes = b->cfg.lanes_per_target;
         launch_rescore_batch(b->d_clips, tpre, n, (int)tot_t, c5, b->counters, lanes, st);
-        for (int k = 1; k <= b->cfg.n_pm; ++k)
+        for (int k = 1; k <= b->cfg.n_pm; ++k) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (b->profiling) {
+                if (b->events_used == b->events.size()) {
+                    cudaEvent_t x, y;
+                    BCK(cudaEventCreate(&x));
+                    BCK(cudaEventCreate(&y));
+                    b->events.emplace_back(x, y);
+                }
+                e0 = b->events[b->events_used].first;
+                e1 = b->events[b->events_used].second;
+                ++b->events_used;
+                BCK(cudaEventRecord(e0, st));
+            }
             launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, k, c5, b->counters + 1, b->counters + 2,
                                   lanes, st);
+            if (b->profiling)
+                BCK(cudaEventRecord(e1, st));
+        }
         if (b->cfg.n_pm & 1)
             for (int i = 0; i < n; ++i) {
                 Level &l = act[i]->ctx->lv[act[i]->level];
@@ -398,6 +424,9 @@ vi_status vi_batch_remove(vi_batch *b, int id)
         return VI_ERR_ARG;
     for (size_t i = 0; i < b->clips.size(); ++i)
         if (b->clips[i].id == id) {
+            vi_stats s;
+            if (vi_get_stats(b->clips[i].ctx, &s) == VI_OK)
+                b->removed_evals += s.evals;
             vi_ctx_destroy(b->clips[i].ctx);
             b->clips.erase(b->clips.begin() + (long)i);
             return VI_OK;
@@ -415,6 +444,34 @@ vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out)
     return vi_get_stats(c->ctx, out);
 }
 
+vi_status vi_batch_profile(vi_batch *b, int enable)
+{
+    if (!b)
+        return VI_ERR_ARG;
+    b->profiling = enable != 0;
+    return VI_OK;
+}
+
+vi_status vi_batch_step_time(vi_batch *b, double *step_ms, unsigned long long *step_evals)
+{
+    if (!b)
+        return VI_ERR_ARG;
+    unsigned long long h[3] = {0, 0, 0};
+    BCK(cudaMemcpyAsync(h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->events_used; ++i) {
+        float ms = 0.0f;
+        BCK(cudaEventElapsedTime(&ms, b->events[i].first, b->events[i].second));
+        b->step_ms += ms;
+    }
+    b->events_used = 0;
+    if (step_ms)
+        *step_ms = b->step_ms;
+    if (step_evals)
+        *step_evals = h[1];
+    return VI_OK;
+}
+
 vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned long long *gathered,
                              unsigned long long *rounds)
 {
@@ -423,7 +480,7 @@ vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned lo
     unsigned long long h[3] = {0, 0, 0};
     BCK(cudaMemcpyAsync(h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
-    unsigned long long ev = h[0] + h[1];
+    unsigned long long ev = h[0] + h[1] + b->removed_evals;
     for (Entry &c : b->clips) {
         vi_stats s;
         if (vi_get_stats(c.ctx, &s) == VI_OK)

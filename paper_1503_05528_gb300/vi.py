@@ -30,7 +30,7 @@ EXPORTS = [
     "vi_profile", "vi_get_stats", "vi_energy_noalloc",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
-    "vi_batch_get_stats",
+    "vi_batch_get_stats", "vi_batch_profile", "vi_batch_step_time",
 ]
 
 
@@ -126,6 +126,8 @@ def _declare(L):
     L.vi_batch_remove.argtypes = [vp, i]
     L.vi_batch_clip_stats.argtypes = [vp, i, P(ViStats)]
     L.vi_batch_get_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
+    L.vi_batch_profile.argtypes = [vp, i]
+    L.vi_batch_step_time.argtypes = [vp, P(d), P(ull)]
 
 
 def default_config(**kw):
@@ -401,7 +403,13 @@ class Batch:
     def stats(self):
         e, g, r = C.c_ulonglong(0), C.c_ulonglong(0), C.c_ulonglong(0)
         self._ck(self.lib.vi_batch_get_stats(self.h, C.byref(e), C.byref(g), C.byref(r)))
-        return dict(evals=e.value, gathered=g.value, rounds=r.value)
+        ms, se = C.c_double(0.0), C.c_ulonglong(0)
+        self._ck(self.lib.vi_batch_step_time(self.h, C.byref(ms), C.byref(se)))
+        return dict(evals=e.value, gathered=g.value, rounds=r.value, step_ms=ms.value,
+                    step_evals=se.value)
+
+    def profile(self, enable=True):
+        self._ck(self.lib.vi_batch_profile(self.h, 1 if enable else 0))
 
 
 def auto_levels(mask):
