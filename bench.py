@@ -202,7 +202,8 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    clip = make_clip(0, args.workload)
+    workload = args.workload if args.workload in WORKLOADS else WORKLOAD
+    clip = make_clip(0, workload)
     smp = OracleSample(clip)
     frames = 2
     for _ in range(args.warmup):
@@ -217,10 +218,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": f"{frames} frames per step"},
+            "config": {"workload": workload, "sample": f"{frames} frames per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: sequential ANN search over the level-0 "
-                                       f"targets of {frames} frames of {args.workload}, one thread"},
+                                       f"targets of {frames} frames of {workload}, one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -498,6 +499,158 @@ def run_batch(args):
     return 0
 
 
+SERVE_WORKLOAD = "serve_poisson4"
+
+
+def make_serve_pool(rank, n_pool):
+    """Distinct clips for the serving workload: layered-motion clips (integer
+    camera drift, textured sprites, moving elliptical occlusion tube) with
+    sizes W ~ logU[320, 1280], H ~ logU[240, 720], frames ~ logU[30, 120] and
+    3-10% occlusion; levels by the rule of Sec. 3.6."""
+    from paper_1503_05528_gb300 import synth
+    return [synth.fast_layered_clip(W, H, T, frac, synth.BASE_SEED + 5000 + 1000 * rank + i,
+                                    name=f"serve_{i}")
+            for i, (W, H, T, frac) in enumerate(synth.serve_sizes(n_pool))]
+
+
+def run_serve(args):
+    """A Poisson stream of inpainting requests (mean 4 per second, seeded)
+    through the continuous-batching server: admission by an HBM budget,
+    clips joining and leaving the running batch between rounds, host buffers
+    in and out. Latency = completion - arrival (queueing, upload, preparation,
+    iterations, fetch). The plain path serves the same arrivals one request
+    at a time through vi_run (FCFS single server; its latencies follow from
+    each request's measured service time by the Lindley recursion)."""
+    import numpy as np
+    import torch
+
+    from paper_1503_05528_gb300 import vi
+    from paper_1503_05528_gb300.serve import CudaBackend, Server, poisson_arrivals, run_load
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vi.load(build_if_missing=True)
+    pool = make_serve_pool(rank, args.serve_pool)
+    n = args.requests
+    reqs = [(pool[i % len(pool)].rgb, pool[i % len(pool)].mask, {"seed": 7000 + i, "clip": i})
+            for i in range(n)]
+    arrivals = poisson_arrivals(n, args.rate, seed=1503 + rank)
+    hole = [int(pool[i % len(pool)].mask.sum()) for i in range(n)]
+    vox = [int(pool[i % len(pool)].mask.size) for i in range(n)]
+    stream = torch.cuda.current_stream()
+    budget = int(args.hbm_budget_gb * (1 << 30))
+    backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1)
+
+    # warm-up: a few requests back to back
+    warm = Server(backend, budget, max_slots=args.slots)
+    for i in range(args.warmup):
+        c = pool[i % len(pool)]
+        warm.submit(c.rgb, c.mask, seed=1, clip=i)
+    while warm.step():
+        pass
+
+    backend.batch.profile(True)
+    s0 = backend.batch.stats()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    srv = Server(backend, budget, max_slots=args.slots)
+    wall, srv = run_load(srv, reqs, arrivals)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    s1 = backend.batch.stats()
+    backend.batch.profile(False)
+    lat = np.array([srv.done[t].latency for t in range(n)])
+    failed = sum(1 for r in srv.done.values() if r.info.get("failed"))
+    evals = s1["evals"] - s0["evals"]
+    step_ms = s1["step_ms"] - s0["step_ms"]
+    gathered = s1["gathered"] - s0["gathered"]
+    rounds = s1["rounds"] - s0["rounds"]
+    served = {t: srv.done[t].result for t in range(min(n, len(pool)))}
+    backend.close()
+
+    # plain path: each request alone through vi_run, back to back
+    service, single_evals = [], 0
+    torch.cuda.synchronize()
+    for i, (rgb, mask, job) in enumerate(reqs):
+        t = time.perf_counter()
+        with vi.Context(levels=0, use_texture=1, stream=stream.cuda_stream, **job) as ctx:
+            ctx.upload(rgb, mask)
+            ctx.run()
+            out = ctx.fetch_result()
+            single_evals += ctx.stats()["evals"]
+        service.append(time.perf_counter() - t)
+        if i in served:
+            assert (out.view(np.uint32) == served[i].view(np.uint32)).all(), \
+                f"request {i}: served result differs from vi_run alone"
+    free, lat1 = 0.0, []
+    for a, s in zip(arrivals, service):
+        free = max(free, a) + s
+        lat1.append(free - a)
+    lat1 = np.array(lat1)
+    plain_wall = free
+
+    mx, sm = combine_ranks([wall, float(evals), float(sum(hole)), plain_wall, float(single_evals)],
+                           dist, "cuda")
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    achieved = gathered * BYTES_PER_VOXEL_FP32_C5 / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    pct = lambda x, q: float(np.percentile(x, q, method="inverted_cdf"))  # noqa: E731
+    line = {
+        "metric": METRIC, "value": sm[1] / mx[0], "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * mx[0],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "requests": n, "rate_per_s": args.rate,
+                   "distinct_clips": len(pool), "voxels_mean": float(np.mean(vox)),
+                   "hole_voxels": int(sum(hole)), "hbm_budget_gb": args.hbm_budget_gb,
+                   "max_slots": args.slots, "levels": "rule of Sec. 3.6 per clip", "channels": 5,
+                   "storage": "fp32", "parallelism": f"replicas x{world}",
+                   "step": "the whole arrival stream, host buffers in and out",
+                   "l2": "inputs larger than L2: every request uploads and rebuilds its state"},
+        "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(lat.max()),
+                      "mean": float(lat.mean())},
+        "inpainted_voxels_per_s": sm[2] / mx[0],
+        "requests_per_s": n * world / mx[0],
+        "failed": failed, "max_concurrent": srv.max_concurrent, "rounds": rounds,
+        "plain_fp32_path": {"value": sm[4] / mx[3], "unit": UNIT,
+                            "latency_s": {"p50": pct(lat1, 50), "p99": pct(lat1, 99),
+                                          "max": float(lat1.max())},
+                            "inpainted_voxels_per_s": sm[2] / mx[3],
+                            "busy_s": float(sum(service)),
+                            "note": "same arrivals, one request at a time through vi_run"},
+        "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                     "traffic": None, "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels)",
+                     "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None},
+        "e2e": {"value": sm[1] / mx[0], "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(v * 13 for v in vox)),
+                "d2h_bytes_per_step": int(sum(v * 12 for v in vox))},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,7 +659,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVE_WORKLOAD])
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=4.0, help="serving: mean arrivals per second")
+    ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
+    ap.add_argument("--hbm-budget-gb", type=float, default=96.0, help="serving: admission budget")
+    ap.add_argument("--slots", type=int, default=32, help="serving: most requests in the batch")
     ap.add_argument("--lanes", type=int, default=0,
                     help="GPU lanes per target in the search kernels (0: chosen per level)")
     args = ap.parse_args()
@@ -514,6 +673,8 @@ def main():
         return run_reference(args)
     if args.workload == BATCH_WORKLOAD:
         return run_batch(args)
+    if args.workload == SERVE_WORKLOAD:
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -224,6 +224,49 @@ def small_layered(W=72, H=56, T=14, levels=2, seed=BASE_SEED + 11, hole_frac=0.0
                         dynamic_texture=dynamic_texture, name=f"layered_{W}x{H}x{T}")
 
 
+def fast_layered_clip(W, H, T, hole_frac, seed, n_sprites=2, name=None):
+    """A cheaper layered clip for load tests: a two-octave smooth-noise
+    background under an integer camera drift (whole-pixel shifts, no
+    resampling), textured rectangles on integer linear paths, and the moving
+    elliptical occlusion tube of layered_clip. Pyramid levels by the rule of
+    Sec. 3.6 (levels = 0)."""
+    rng = np.random.default_rng(seed)
+    bg = (0.4 * smooth_noise(rng, H, W, 2.0) + 0.6 * smooth_noise(rng, H, W, 8.0)).astype(np.float32)
+    mn, mx = bg.min(), bg.max()
+    bg = (0.1 + 0.8 * (bg - mn) / (mx - mn)).astype(np.float32)
+    vx, vy = int(rng.integers(-1, 2)), int(rng.integers(-1, 2))
+    sprites = []
+    for _ in range(n_sprites):
+        sw, sh = int(rng.integers(W // 12 + 4, W // 5 + 5)), int(rng.integers(H // 12 + 4, H // 5 + 5))
+        tex = smooth_noise(rng, sh, sw, 1.5, lo=0.05, hi=0.95).astype(np.float32)
+        x0, y0 = int(rng.integers(0, W - sw)), int(rng.integers(0, H - sh))
+        sprites.append((tex, x0, y0, int(rng.integers(-3, 4)), int(rng.integers(-2, 3))))
+    out = np.empty((T, H, W, 3), np.float32)
+    for t in range(T):
+        out[t] = np.roll(bg, (vy * t, vx * t), axis=(0, 1))
+        for tex, x0, y0, sx, sy in sprites:
+            sh, sw = tex.shape[:2]
+            x = (x0 + sx * t) % (W - sw)
+            y = (y0 + sy * t) % (H - sh)
+            out[t, y:y + sh, x:x + sw] = tex
+    mask = _ellipse_tube(W, H, T, hole_frac, rng)
+    return Clip(name or f"fast_{W}x{H}x{T}", out, mask, levels=0, use_texture=True,
+                meta={"seed": seed, "hole_frac": hole_frac})
+
+
+def serve_sizes(n=200, seed=BASE_SEED + 5):
+    """Request sizes of the serving workload: W ~ logU[320, 1280], H ~
+    logU[240, 720], frames ~ logU[30, 120] (even), hole fraction ~ U[3%, 10%]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        W = int(round(math.exp(rng.uniform(math.log(320), math.log(1280))) / 2)) * 2
+        H = int(round(math.exp(rng.uniform(math.log(240), math.log(720))) / 2)) * 2
+        T = int(round(math.exp(rng.uniform(math.log(30), math.log(120))) / 2)) * 2
+        out.append((W, H, T, float(rng.uniform(0.03, 0.10))))
+    return out
+
+
 def batch_sizes(n=48, seed=BASE_SEED + 4):
     """Clip sizes for the batched workload: W ~ logU[160,640], H ~ logU[120,480],
     frames ~ logU[20,80], independently drawn and rounded to even sizes, plus a
