@@ -43,6 +43,7 @@ UNIT = "evals/s"
 WORKLOAD = "layered_320x240x60"
 BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
 BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
+BYTES_PER_VOXEL_FP16_C5 = 5 * 2           # the same voxel from the FP16 copy
 
 # dram bytes (read + write) of one launch of the PatchMatch step kernel and the
 # source voxels that launch gathered, from one ncu capture (see profiles/);
@@ -248,8 +249,9 @@ def run_gpu(args):
     mask_d = torch.from_numpy(clip.mask).cuda()
     out_d = torch.empty_like(rgb_d)
     stream = torch.cuda.current_stream()
+    storage = 1 if args.storage == "fp16" else 0
     ctx = vi.Context(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank,
-                     stream=stream.cuda_stream, lanes_per_target=args.lanes)
+                     stream=stream.cuda_stream, lanes_per_target=args.lanes, storage=storage)
     n_hole = int(clip.mask.sum())
 
     def step():
@@ -287,6 +289,9 @@ def run_gpu(args):
     evals = s1["evals"] - s0["evals"]
     step_evals = s1["step_evals"] - s0["step_evals"]
     step_gathered = s1["step_gathered"] - s0["step_gathered"]
+    step_gathered_h = s1["step_gathered_h"] - s0["step_gathered_h"]
+    screened = s1["screened"] - s0["screened"]
+    passed = s1["screen_passed"] - s0["screen_passed"]
     step_ms = s1["step_ms"] - s0["step_ms"]
     step_launches = s1["step_timed"] - s0["step_timed"]
     launches = s1["launches"] - s0["launches"]
@@ -323,10 +328,11 @@ def run_gpu(args):
 
     peak, peak_kind = _peaks()
     # algorithmic bytes of the step kernel: the source voxels it has to gather
-    # (20 B each: 5 FP32 channels). A candidate equal to a shift already
-    # compared needs no gather, and a gather stops once the partial sum shows
-    # the candidate cannot win; both leave every decision unchanged.
-    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5
+    # (20 B each: 5 FP32 channels; 10 B from the FP16 copy when screening). A
+    # candidate equal to a shift already compared needs no gather, and a gather
+    # stops once the partial sum shows the candidate cannot win; both leave
+    # every decision unchanged.
+    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5 + step_gathered_h * BYTES_PER_VOXEL_FP16_C5
     achieved = gathered_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     traffic = None
     if NCU_STEP_TRAFFIC and step_launches:
@@ -337,18 +343,22 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "levels": clip.levels, "channels": 5, "storage": "fp32",
+        "config": {"workload": args.workload, "levels": clip.levels, "channels": 5, "storage": args.storage,
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
                    "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
         "inpainted_voxels_per_s": hole_tot * args.steps / (ms_max / 1e3),
         "evals_per_step": evals / args.steps,
         "outer_iterations_per_level": outer[:clip.levels],
+        "screening": ({"screened": screened, "passed": passed,
+                       "pass_rate": passed / screened if screened else None,
+                       "fp16_voxels": step_gathered_h, "fp32_voxels": step_gathered}
+                      if storage else None),
         "roofline": {"bound": "hbm", "kernel": "k_ann_step (PatchMatch propagation + random search)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels)",
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
                      "gathered_bytes_per_launch": gathered_bytes / step_launches if step_launches else None,
                      "launches_timed": step_launches,
                      "evals_per_launch": step_evals / step_launches if step_launches else None,
@@ -406,7 +416,8 @@ def run_batch(args):
     n_hole = sum(int(c.mask.sum()) for c in clips)
     n_vox = sum(int(c.mask.size) for c in clips)
     stream = torch.cuda.current_stream()
-    b = vi.Batch(stream=stream.cuda_stream, levels=0, lanes_per_target=args.lanes)
+    storage = 1 if args.storage == "fp16" else 0
+    b = vi.Batch(stream=stream.cuda_stream, levels=0, lanes_per_target=args.lanes, storage=storage)
 
     def step():
         ids = [b.add(r, m, levels=0, seed=1503 + i, clip=i) for i, (r, m) in enumerate(dev)]
@@ -446,6 +457,9 @@ def run_batch(args):
     evals = s1["evals"] - s0["evals"]
     step_ms = s1["step_ms"] - s0["step_ms"]
     gathered = s1["gathered"] - s0["gathered"]
+    gathered_h = s1["gathered_h"] - s0["gathered_h"]
+    screened = s1["screened"] - s0["screened"]
+    passed = s1["screen_passed"] - s0["screen_passed"]
     rounds = (s1["rounds"] - s0["rounds"]) / args.steps
 
     # the same clips one after another through the single-clip path
@@ -454,7 +468,7 @@ def run_batch(args):
     single_evals = 0
     for i, (r, m) in enumerate(dev):
         with vi.Context(levels=0, seed=1503 + i, clip=i, stream=stream.cuda_stream,
-                        lanes_per_target=args.lanes) as ctx:
+                        lanes_per_target=args.lanes, storage=storage) as ctx:
             ctx.upload(r, m)
             ctx.run()
             ctx.fetch_result(outs[i])
@@ -469,19 +483,22 @@ def run_batch(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    achieved = gathered * BYTES_PER_VOXEL_FP32_C5 / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16_C5
+    achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     line = {
         "metric": METRIC, "value": sm[1] / (mx[0] / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx[0] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "clips": len(clips), "voxels": n_vox, "hole_voxels": n_hole,
-                   "levels": "rule of Sec. 3.6 per clip", "channels": 5, "storage": "fp32",
+                   "levels": "rule of Sec. 3.6 per clip", "channels": 5, "storage": args.storage,
                    "parallelism": f"replicas x{world}", "lanes_per_target": args.lanes or "auto",
                    "rounds_per_step": rounds,
                    "l2": "inputs larger than L2: about 10 GB of clip state rebuilt every step"},
         "inpainted_voxels_per_s": sm[2] * args.steps / (mx[0] / 1e3),
         "evals_per_step": evals / args.steps,
+        "screening": ({"screened": screened, "passed": passed,
+                       "pass_rate": passed / screened if screened else None} if storage else None),
         "single_clip_path": {"value": sm[4] / mx[3], "unit": UNIT,
                              "inpainted_voxels_per_s": sm[2] / mx[3], "seconds": mx[3],
                              "note": "the same 48 clips one after another through vi_run; "
@@ -489,7 +506,8 @@ def run_batch(args):
         "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": None, "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels)",
+                     "traffic": None,
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
                      "kernel_ms_share": step_ms / ms if ms > 0 else None},
         "clocks": clocks,
     }
@@ -543,7 +561,8 @@ def run_serve(args):
     vox = [int(pool[i % len(pool)].mask.size) for i in range(n)]
     stream = torch.cuda.current_stream()
     budget = int(args.hbm_budget_gb * (1 << 30))
-    backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1)
+    storage = 1 if args.storage == "fp16" else 0
+    backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1, storage=storage)
 
     # warm-up: a few requests back to back
     warm = Server(backend, budget, max_slots=args.slots)
@@ -578,6 +597,7 @@ def run_serve(args):
     evals = s1["evals"] - s0["evals"]
     step_ms = s1["step_ms"] - s0["step_ms"]
     gathered = s1["gathered"] - s0["gathered"]
+    gathered_h = s1["gathered_h"] - s0["gathered_h"]
     rounds = s1["rounds"] - s0["rounds"]
     served = {t: srv.done[t].result for t in range(min(n, len(pool)))}
     backend.close()
@@ -610,7 +630,8 @@ def run_serve(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    achieved = gathered * BYTES_PER_VOXEL_FP32_C5 / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16_C5
+    achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     pct = lambda x, q: float(np.percentile(x, q, method="inverted_cdf"))  # noqa: E731
     line = {
         "metric": METRIC, "value": sm[1] / mx[0], "unit": UNIT, "n_gpus": world,
@@ -621,7 +642,7 @@ def run_serve(args):
                    "distinct_clips": len(pool), "voxels_mean": float(np.mean(vox)),
                    "hole_voxels": int(sum(hole)), "hbm_budget_gb": args.hbm_budget_gb,
                    "max_slots": args.slots, "levels": "rule of Sec. 3.6 per clip", "channels": 5,
-                   "storage": "fp32", "parallelism": f"replicas x{world}",
+                   "storage": args.storage, "parallelism": f"replicas x{world}",
                    "step": "the whole arrival stream, host buffers in and out",
                    "l2": "inputs larger than L2: every request uploads and rebuilds its state"},
         "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(lat.max()),
@@ -638,7 +659,8 @@ def run_serve(args):
         "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": None, "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels)",
+                     "traffic": None,
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
                      "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None},
         "e2e": {"value": sm[1] / mx[0], "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v * 13 for v in vox)),
@@ -666,6 +688,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0, help="serving: admission budget")
     ap.add_argument("--slots", type=int, default=32, help="serving: most requests in the batch")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                    help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
     ap.add_argument("--lanes", type=int, default=0,
                     help="GPU lanes per target in the search kernels (0: chosen per level)")
     args = ap.parse_args()

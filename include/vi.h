@@ -71,7 +71,14 @@ typedef struct {
                             channel and voxel of H between iterations (0.1/255) */
     int weighted;        /* 1: weights of Eq. 5; 0: the unweighted mean (s = 1) */
     int use_texture;     /* 1: C = 5 channels (Sec. 3.3); 0: RGB only (C = 3) */
-    int storage;         /* 0: FP32 channel storage (the only value accepted) */
+    int storage;         /* 0: FP32 channels. 1: FP32 channels plus an FP16 copy;
+                            the PatchMatch step screens each candidate on the
+                            FP16 copy with a rigorous error bound and computes
+                            the FP32 distance only when the candidate could
+                            beat the current best, so results are identical to
+                            storage 0 (the paper fixes no storage precision;
+                            this is a speed option). The partial distance of
+                            the initialisation (Eq. 11) always reads FP32. */
     uint64_t seed;       /* Philox4x32-10 key (key words: low, high 32 bits) */
     uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
     int lanes_per_target; /* GPU lanes sharing one target in the search kernels:
@@ -87,6 +94,10 @@ typedef struct {
     unsigned long long step_gathered;  /* source voxels the step kernel read: candidates
                                           equal to a shift already compared need none,
                                           and a gather stops once it cannot win */
+    unsigned long long step_gathered_h; /* FP16 source voxels the step kernel read
+                                          (storage 1: candidate screening) */
+    unsigned long long screened;       /* candidates screened on the FP16 copy */
+    unsigned long long screen_passed;  /* of those, evaluated in FP32 */
     unsigned long long step_launches;  /* launches of the PatchMatch step kernel */
     double step_ms;                    /* device time of those launches (profiling on) */
     unsigned long long step_timed;     /* launches included in step_ms */
@@ -321,6 +332,12 @@ vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out);
  * Synchronises. Outputs nullable. */
 vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned long long *gathered,
                              unsigned long long *rounds);
+
+/* FP16 screening counters of the batch step launches (storage 1): FP16
+ * source voxels gathered, candidates screened, candidates passed on to the
+ * FP32 distance. All zero with storage 0. Synchronises. Outputs nullable. */
+vi_status vi_batch_screen_stats(vi_batch *b, unsigned long long *gathered_h, unsigned long long *screened,
+                                unsigned long long *passed);
 
 /* Device-time profiling of the batch PatchMatch step launches (events on the
  * batch's stream around each launch), and its totals since creation: summed

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvi.so")
-SOURCES = ["vi_pyramid.cu", "vi_search.cu", "vi_vote.cu", "vi_api.cu", "vi_batch.cu", "vi_noalloc.cu"]
+SOURCES = ["vi_pyramid.cu", "vi_search.cu", "vi_search_h.cu", "vi_vote.cu", "vi_api.cu", "vi_batch.cu",
+           "vi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

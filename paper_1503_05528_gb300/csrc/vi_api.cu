@@ -89,6 +89,9 @@ void free_state(vi_ctx *ctx)
         dfree(l.x4);
         dfree(l.x1);
         dfree(l.code);
+        dfree(l.h4);
+        dfree(l.h1);
+        dfree(l.hmax);
         dfree(l.phi[0]);
         dfree(l.phi[1]);
         dfree(l.d2[0]);
@@ -119,7 +122,7 @@ void free_state(vi_ctx *ctx)
 vi_status check_config(vi_ctx *ctx, const vi_config *c)
 {
     if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
-        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || c->storage != 0 ||
+        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
           c->lanes_per_target == 4 || c->lanes_per_target == 8))
         return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
@@ -216,6 +219,7 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
         a.clip = ctx->cfg.clip;
         a.evals = ctx->evals_dev + 1;
         a.gathered = ctx->evals_dev + 2;
+        a.screen = ctx->evals_dev + 3;
         a.lanes = ctx->cfg.lanes_per_target;
         TRY(step_launch(ctx, a));
     }
@@ -342,13 +346,13 @@ vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
     }
     if (cudaMalloc((void **)&ctx->count_dev, 64 * sizeof(int)) != cudaSuccess ||
         cudaMalloc((void **)&ctx->scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&ctx->evals_dev, 3 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->evals_dev, 6 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->host_scal, 8 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&ctx->host_counts, 64 * sizeof(int)) != cudaSuccess) {
         vi_ctx_destroy(ctx);
         return VI_ERR_OOM;
     }
-    cudaMemsetAsync(ctx->evals_dev, 0, 3 * sizeof(unsigned long long), ctx->stream);
+    cudaMemsetAsync(ctx->evals_dev, 0, 6 * sizeof(unsigned long long), ctx->stream);
     *out = ctx;
     return VI_OK;
 }
@@ -392,8 +396,11 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
     int w = W, h = H;
     for (int l = 0; l < L; ++l) {
         const size_t V = (size_t)w * h * T;
-        // x4, x1, code, 2 shift + 2 distance buffers, three lists (upper bound)
+        // x4, x1, code, 2 shift + 2 distance buffers, three lists (upper bound),
+        // FP16 copies
         total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 12);
+        if (cfg && cfg->storage == 1)
+            total += V * (8 + (c5 ? 2 : 0)) + 256;
         w = (w + 1) / 2;
         h = (h + 1) / 2;
     }
@@ -451,6 +458,12 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
         if (ctx->c5)
             TRY(dalloc(ctx, &lv.x1, V * sizeof(float)));
         TRY(dalloc(ctx, &lv.code, V));
+        if (ctx->cfg.storage == 1) {
+            TRY(dalloc(ctx, &lv.h4, V * sizeof(uint2)));
+            if (ctx->c5)
+                TRY(dalloc(ctx, &lv.h1, V * sizeof(unsigned short)));
+            TRY(dalloc(ctx, &lv.hmax, 8 * sizeof(unsigned)));
+        }
         for (int b = 0; b < 2; ++b) {
             TRY(dalloc(ctx, &lv.phi[b], V * sizeof(Shift)));
             TRY(dalloc(ctx, &lv.d2[b], V * sizeof(float)));
@@ -510,6 +523,12 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         launch_downsample(ctx->lv[l - 1].view(), ctx->lv[l].view(), l, ctx->T0, W, H, s, ctx->c5, st);
         CK_LAUNCH();
         launch_codes(ctx->lv[l].view(), ctx->tmpA, ctx->tmpB, st);
+        CK_LAUNCH();
+    }
+    // FP16 storage: the copies of every level and their magnitude bounds
+    for (int l = 0; l < ctx->L && ctx->cfg.storage == 1; ++l) {
+        CK(cudaMemsetAsync(ctx->lv[l].hmax, 0, 8 * sizeof(unsigned), st));
+        launch_shadow_all(ctx->lv[l].view(), ctx->c5, st);
         CK_LAUNCH();
     }
     // list sizes (one synchronisation), then the lists
@@ -825,6 +844,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
     const size_t bytes = (size_t)l.V * C * sizeof(float);
     if (ptr_is_device) {
         launch_set_channels(l.view(), in, C, ctx->stream);
+        launch_shadow_all(l.view(), ctx->c5, ctx->stream);
         CK_LAUNCH();
         return VI_OK;
     }
@@ -833,6 +853,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
     cudaError_t e = cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) {
         launch_set_channels(l.view(), tmp, C, ctx->stream);
+        launch_shadow_all(l.view(), ctx->c5, ctx->stream);
         e = cudaStreamSynchronize(ctx->stream);
     }
     cudaFree(tmp);
@@ -978,7 +999,7 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
     if (!ctx || !out)
         return VI_ERR_ARG;
     std::memset(out, 0, sizeof(*out));
-    unsigned long long ev[3] = {0, 0, 0};
+    unsigned long long ev[6] = {0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(ev, ctx->evals_dev, sizeof(ev), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (size_t i = 0; i < ctx->events_used; ++i) {
@@ -991,6 +1012,9 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
     out->evals = ev[0] + ev[1];
     out->step_evals = ev[1];
     out->step_gathered = ev[2];
+    out->step_gathered_h = ev[3];
+    out->screened = ev[4];
+    out->screen_passed = ev[5];
     out->step_launches = ctx->step_launches;
     out->step_ms = ctx->step_ms;
     out->step_timed = ctx->step_timed;

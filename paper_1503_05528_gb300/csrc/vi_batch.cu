@@ -55,7 +55,9 @@ struct vi_batch {
     double *d_e = nullptr, *h_e = nullptr;
     float *d_change = nullptr;
     long long change_cap = 0;
-    unsigned long long *counters = nullptr;          // evals, step evals, gathered
+    // rescore evals, step evals, FP32 voxels gathered, FP16 voxels gathered,
+    // screened, passed
+    unsigned long long *counters = nullptr;
     unsigned long long rounds = 0;
     unsigned long long removed_evals = 0;            // own evaluations of removed clips
 
@@ -182,11 +184,11 @@ vi_status vi_batch_create(const vi_config *cfg, void *cuda_stream, vi_batch **ou
         }
         b->own_stream = true;
     }
-    if (cudaMalloc((void **)&b->counters, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc((void **)&b->counters, 6 * sizeof(unsigned long long)) != cudaSuccess) {
         vi_batch_destroy(b);
         return VI_ERR_OOM;
     }
-    cudaMemsetAsync(b->counters, 0, 3 * sizeof(unsigned long long), b->stream);
+    cudaMemsetAsync(b->counters, 0, 6 * sizeof(unsigned long long), b->stream);
     *out = b;
     return VI_OK;
 }
@@ -224,8 +226,8 @@ vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, 
     if (!b || !id_out)
         return VI_ERR_ARG;
     vi_config cfg = job_cfg ? *job_cfg : b->cfg;
-    if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm)
-        return bfail(b, VI_ERR_ARG, "vi_batch_add: use_texture and n_pm must match the batch");
+    if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm || cfg.storage != b->cfg.storage)
+        return bfail(b, VI_ERR_ARG, "vi_batch_add: use_texture, n_pm and storage must match the batch");
     vi_ctx *ctx = nullptr;
     vi_status s = vi_ctx_create(&cfg, b->stream, &ctx);
     if (s != VI_OK)
@@ -339,7 +341,7 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
                 ++b->events_used;
                 BCK(cudaEventRecord(e0, st));
             }
-            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, k, c5, b->counters + 1, b->counters + 2,
+            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, k, c5, b->cfg.storage == 1, b->counters + 1,
                                   lanes, st);
             if (b->profiling)
                 BCK(cudaEventRecord(e1, st));
@@ -492,6 +494,23 @@ vi_status vi_batch_get_stats(vi_batch *b, unsigned long long *evals, unsigned lo
         *gathered = h[2];
     if (rounds)
         *rounds = b->rounds;
+    return VI_OK;
+}
+
+vi_status vi_batch_screen_stats(vi_batch *b, unsigned long long *gathered_h, unsigned long long *screened,
+                                unsigned long long *passed)
+{
+    if (!b)
+        return VI_ERR_ARG;
+    unsigned long long h[6] = {0, 0, 0, 0, 0, 0};
+    BCK(cudaMemcpyAsync(h, b->counters, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (gathered_h)
+        *gathered_h = h[3];
+    if (screened)
+        *screened = h[4];
+    if (passed)
+        *passed = h[5];
     return VI_OK;
 }
 

@@ -29,6 +29,9 @@ struct Level {
     float4 *x4 = nullptr;
     float *x1 = nullptr;
     uint8_t *code = nullptr;
+    uint2 *h4 = nullptr;              // FP16 storage: copies of x4 / x1, |x| bounds
+    unsigned short *h1 = nullptr;
+    unsigned *hmax = nullptr;
     Shift *phi[2] = {nullptr, nullptr};
     float *d2[2] = {nullptr, nullptr};
     int *targets = nullptr, *holes = nullptr, *sources = nullptr;
@@ -45,6 +48,9 @@ struct Level {
         v.x4 = x4;
         v.x1 = x1;
         v.code = code;
+        v.h4 = h4;
+        v.h1 = h1;
+        v.hmax = hmax;
         return v;
     }
 };
@@ -78,7 +84,9 @@ struct vi_ctx {
     double *scal = nullptr;        // device scalars
     double *host_scal = nullptr;   // pinned
     int *host_counts = nullptr;    // pinned, 64 ints
-    unsigned long long *evals_dev = nullptr;  // [0] rescore evals, [1] step evals, [2] step gathered voxels
+    // [0] rescore evals, [1] step evals, [2] FP32 voxels gathered by the step,
+    // [3] FP16 voxels gathered, [4] candidates screened, [5] screened and passed
+    unsigned long long *evals_dev = nullptr;
 
     uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
     int *layer_list = nullptr, *ltgt_list = nullptr;

@@ -3,6 +3,7 @@
 // distance of Eq. 2 / Eq. 7b / Eq. 11.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,7 +18,10 @@ struct __align__(8) Shift {
 };
 
 // One pyramid level as the kernels see it. Channels c0..c3 live in x4 (c3 = 0
-// when C = 3), channel c4 in x1 (C = 5 only).
+// when C = 3), channel c4 in x1 (C = 5 only). With FP16 storage, h4 / h1 hold
+// the same channels rounded to FP16 (four halves per uint2, one per ushort)
+// and hmax[c] bounds |x_c| over every value the level has held (float bits,
+// raised with atomicMax); h4 == nullptr means FP32 storage only.
 struct LevelView {
     int W, H, T;
     int HW;          // W * H
@@ -25,6 +29,9 @@ struct LevelView {
     float4 *x4;
     float *x1;
     uint8_t *code;
+    uint2 *h4;
+    unsigned short *h1;
+    unsigned *hmax;
 };
 
 __device__ __forceinline__ void decode(int p, int W, int HW, int &x, int &y, int &t)
@@ -89,24 +96,42 @@ __device__ __forceinline__ uint32_t uniform_index(uint32_t w, uint32_t n)
 // chains of a slice are independent, so a thread keeps 25 voxel loads and
 // five FMA chains in flight rather than one serial chain of 625 terms.
 // ---------------------------------------------------------------------------
-template <bool C5>
+__device__ __forceinline__ float half_lo(unsigned u) { return __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu))); }
+__device__ __forceinline__ float half_hi(unsigned u) { return __half2float(__ushort_as_half((unsigned short)(u >> 16))); }
+
+// Adds the terms of voxel pair (r, s) to acc: from the FP32 channels, or with
+// H from their FP16 copies (converted exactly to FP32).
+template <bool C5, bool H = false>
 __device__ __forceinline__ void acc_voxel(const LevelView &L, int r, int s, float &acc)
 {
-    const float4 a = __ldg(L.x4 + r);
-    const float4 b = __ldg(L.x4 + s);
+    float a0, a1, a2, a3, b0, b1, b2, b3;
+    if (H) {
+        const uint2 ua = __ldg(L.h4 + r), ub = __ldg(L.h4 + s);
+        a0 = half_lo(ua.x); a1 = half_hi(ua.x); a2 = half_lo(ua.y); a3 = half_hi(ua.y);
+        b0 = half_lo(ub.x); b1 = half_hi(ub.x); b2 = half_lo(ub.y); b3 = half_hi(ub.y);
+    } else {
+        const float4 a = __ldg(L.x4 + r);
+        const float4 b = __ldg(L.x4 + s);
+        a0 = a.x; a1 = a.y; a2 = a.z; a3 = a.w;
+        b0 = b.x; b1 = b.y; b2 = b.z; b3 = b.w;
+    }
     float df;
-    df = __fsub_rn(a.x, b.x); acc = __fmaf_rn(df, df, acc);
-    df = __fsub_rn(a.y, b.y); acc = __fmaf_rn(df, df, acc);
-    df = __fsub_rn(a.z, b.z); acc = __fmaf_rn(df, df, acc);
-    df = __fsub_rn(a.w, b.w); acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(a0, b0); acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(a1, b1); acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(a2, b2); acc = __fmaf_rn(df, df, acc);
+    df = __fsub_rn(a3, b3); acc = __fmaf_rn(df, df, acc);
     if (C5) {
-        df = __fsub_rn(__ldg(L.x1 + r), __ldg(L.x1 + s));
+        if (H)
+            df = __fsub_rn(__half2float(__ushort_as_half(__ldg(L.h1 + r))),
+                           __half2float(__ushort_as_half(__ldg(L.h1 + s))));
+        else
+            df = __fsub_rn(__ldg(L.x1 + r), __ldg(L.x1 + s));
         acc = __fmaf_rn(df, df, acc);
     }
 }
 
 // Sum of one whole slice: ro, so = target / source voxel of offset (-2, -2).
-template <bool C5>
+template <bool C5, bool H = false>
 __device__ __forceinline__ float slice_sum(const LevelView &L, int ro, int so)
 {
     float r[5];
@@ -115,7 +140,7 @@ __device__ __forceinline__ float slice_sum(const LevelView &L, int ro, int so)
         r[dy] = 0.0f;
 #pragma unroll
         for (int dx = 0; dx < 5; ++dx)
-            acc_voxel<C5>(L, ro + dy * L.W + dx, so + dy * L.W + dx, r[dy]);
+            acc_voxel<C5, H>(L, ro + dy * L.W + dx, so + dy * L.W + dx, r[dy]);
     }
     float s = r[0];
 #pragma unroll
@@ -164,7 +189,7 @@ __device__ __forceinline__ float patch_d2_interior_bounded(const LevelView &L, i
     return __fdiv_rn(total, 125.0f);
 }
 
-template <bool C5>
+template <bool C5, bool H = false>
 __device__ __forceinline__ float slice_general(const LevelView &L, int px, int py, int pt, int s, int dt,
                                                const uint8_t *excl, int &n);
 
@@ -213,7 +238,7 @@ __device__ __forceinline__ void acc_voxel_if(const LevelView &L, int r, int s, b
 // One slice (fixed dt offset in [-2, 2]) of a clipped or partial distance:
 // the row sums over in-video, non-excluded target voxels, added in dy order;
 // n receives the number of voxels used.
-template <bool C5>
+template <bool C5, bool H>
 __device__ __forceinline__ float slice_general(const LevelView &L, int px, int py, int pt, int s, int dt,
                                                const uint8_t *excl, int &n)
 {
@@ -232,7 +257,7 @@ __device__ __forceinline__ float slice_general(const LevelView &L, int px, int p
                 const int r = rt * HW + ry * W + rx;
                 if (excl && excl[r])
                     continue;
-                acc_voxel<C5>(L, r, s + dt * HW + dy * W + dx, row);
+                acc_voxel<C5, H>(L, r, s + dt * HW + dy * W + dx, row);
                 ++n;
             }
         }
@@ -336,6 +361,127 @@ __device__ __forceinline__ float group_d2(const LevelView &L, int p, int px, int
         return __fdiv_rn(total, (float)n);
     }
     return __fdiv_rn(total, 125.0f);
+}
+
+// FP16 copy of voxel v's channels (FP16 storage: L.h4 != nullptr), and
+// hmax raised to cover the values written. hmax holds |x| as float bits, so
+// unsigned comparison orders it (a NaN compares above +inf and disables the
+// screening below).
+__device__ __forceinline__ unsigned pack_half2(float lo, float hi)
+{
+    return (unsigned)__half_as_ushort(__float2half_rn(lo)) |
+           ((unsigned)__half_as_ushort(__float2half_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+__device__ __forceinline__ void raise_hmax(unsigned *hmax, int c, unsigned m)
+{
+    if (m > __ldcg(hmax + c))
+        atomicMax(hmax + c, m);
+}
+
+template <bool C5>
+__device__ __forceinline__ void shadow_store(const LevelView &L, int v, float4 a, float b)
+{
+    L.h4[v] = make_uint2(pack_half2(a.x, a.y), pack_half2(a.z, a.w));
+    if (C5)
+        L.h1[v] = __half_as_ushort(__float2half_rn(b));
+}
+
+// shadow_store for one voxel written by a single thread, hmax raised at once.
+template <bool C5>
+__device__ __forceinline__ void shadow_store_raise(const LevelView &L, int v, float4 a, float b)
+{
+    shadow_store<C5>(L, v, a, b);
+    raise_hmax(L.hmax, 0, abs_bits(a.x));
+    raise_hmax(L.hmax, 1, abs_bits(a.y));
+    raise_hmax(L.hmax, 2, abs_bits(a.z));
+    raise_hmax(L.hmax, 3, abs_bits(a.w));
+    if (C5)
+        raise_hmax(L.hmax, 4, abs_bits(b));
+}
+
+// ---------------------------------------------------------------------------
+// FP16 screening (storage = 1). A candidate's FP32 distance is only computed
+// when its distance over the FP16 copies does not already prove that it
+// cannot beat the current best; the FP32 comparison then decides, so the
+// shift maps are the same bit for bit as with FP32 storage.
+//
+// The proof. Over the k voxels summed so far let x be the vector of FP32
+// differences in channels c0..c3 and x' that of the FP16 copies' differences,
+// S = |x|^2, S' = |x'|^2. Rounding to FP16 moves a value v with |v| <= M_c by
+// at most 2^-11 |v| + 2^-25, so every entry of e = x' - x is at most
+// delta_c = 2^-10 M_c + 2^-24 in channel c, and |e| <= sqrt(k * D) with
+// D = sum_c delta_c^2. By the triangle inequality sqrt(S) >= sqrt(S') -
+// sqrt(k D), and the full sum S_full (all voxels, all channels: the terms are
+// non-negative) is at least S. The FP32 path
+// accepts only when fl(fl(S_full) / 125) < best; its summation (at most 37
+// roundings of non-negative terms) is within a factor 1 - 2^-18 of S_full, so
+// S_full >= 125 best (1 + 2^-16) rules acceptance out. The bound is evaluated
+// with directed rounding (the computed S' shrunk by 2^-17 for its own
+// rounding, square roots and the subtraction rounded down, the right-hand
+// side rounded up), so every approximation errs towards passing. An M_c that
+// is not finite or exceeds the FP16 range makes D infinite or NaN and every
+// candidate passes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float screen_d2bound(const LevelView &L)
+{
+    float D = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float m = __uint_as_float(__ldg(L.hmax + c));
+        const float dl = (m <= 65504.0f) ? __fadd_ru(__fmul_ru(m, 0x1p-10f), 0x1p-24f)
+                                          : __int_as_float(0x7f800000);
+        D = __fadd_ru(D, __fmul_ru(dl, dl));
+    }
+    return D;
+}
+
+// True when the candidate must be rescored in FP32 (see above); D from
+// screen_d2bound over channels c0..c3. The screen reads only the four
+// channels of h4 (one 8-byte load per voxel): leaving channel c4 out can only
+// lower S, so the bound stays valid, and a candidate costs half the load
+// instructions of the FP32 distance. Slices are summed in rounds of G as in
+// group_d2 and the test runs after every round; every lane of the group
+// holds the same totals and takes the same decision. `gathered` counts the
+// FP16 source voxels read.
+template <bool C5, int G>
+__device__ __forceinline__ bool group_screen(const LevelView &L, int p, int px, int py, int pt, int s,
+                                             float best, float D, int sub, unsigned gmask, unsigned &gathered)
+{
+    const int HW = L.HW;
+    const int off = 2 + 2 * L.W + 2 * HW;
+    const bool frame_inside = px >= 2 && px < L.W - 2 && py >= 2 && py < L.H - 2;
+    const float rhs = __fsqrt_ru(__fmul_ru(best, 125.0019073486328125f));   // 125 (1 + 2^-16)
+    float total = 0.0f;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 5; r0 += G) {
+        const int dt = r0 + sub;
+        float mine = 0.0f;
+        if (dt < 5) {
+            int my_n = 0;
+            if (frame_inside) {
+                if ((unsigned)(pt + dt - 2) < (unsigned)L.T) {
+                    mine = slice_sum<false, true>(L, p - off + dt * HW, s - off + dt * HW);
+                    my_n = 25;
+                }
+            } else {
+                mine = slice_general<false, true>(L, px, py, pt, s, dt - 2, nullptr, my_n);
+            }
+            gathered += (unsigned)my_n;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (r0 + j < 5)
+                total = __fadd_rn(total, G == 1 ? mine : __shfl_sync(gmask, mine, j, G));
+        const int k = 25 * (r0 + G < 5 ? r0 + G : 5);   // voxels summed so far, at most
+        const float lower = __fsub_rd(__fsqrt_rd(__fmul_rd(total, 0.999992370605468750f)),   // 1 - 2^-17
+                                      __fsqrt_ru(__fmul_ru((float)k, D)));
+        if (lower >= rhs)
+            return false;
+    }
+    return true;
 }
 
 template <bool C5>

@@ -56,10 +56,14 @@ struct AnnArgs {
     int rho_log2;          // rho = 2^-rho_log2
     uint32_t key0, key1, tag, clip;
     unsigned long long *evals;     // candidate evaluations (valid candidates)
-    unsigned long long *gathered;  // source voxels actually read
+    unsigned long long *gathered;  // FP32 source voxels actually read
+    unsigned long long *screen;    // FP16 storage: FP16 voxels read, screened, passed (3 counters)
     int lanes;                     // lanes per target (1, 2, 4, 8); 0: by target count
 };
+// FP16 screening when a.L.h4 is set (full distance only; the partial
+// distance of Eq. 11 always runs on the FP32 channels).
 void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st);
+void launch_ann_step_f16(const AnnArgs &a, bool c5, cudaStream_t st);
 // d_out[p] = distance of target p to p + phi[p] (in place allowed).
 void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
                     const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st,
@@ -115,9 +119,11 @@ struct BatchClip {
 };
 // clips[c] owns targets [tprefix[c], tprefix[c+1]) / holes [hprefix[c],
 // hprefix[c+1]); prefixes in device memory (n + 1 entries); totals on the host.
+// ctr: evaluations, FP32 voxels read, FP16 voxels read, screened, passed.
 void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
-                           bool c5, unsigned long long *evals, unsigned long long *gathered, int lanes,
-                           cudaStream_t st);
+                           bool c5, bool f16, unsigned long long *ctr, int lanes, cudaStream_t st);
+void launch_ann_step_batch_f16(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+                               bool c5, unsigned long long *ctr, int lanes, cudaStream_t st);
 void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
                           unsigned long long *evals, int lanes, cudaStream_t st);
 void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int total_holes, bool c5,
@@ -132,6 +138,8 @@ void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st);
 void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st);
 void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st);
 void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st);
+// FP16 copies of every voxel of a level (no-op for FP32 storage).
+void launch_shadow_all(LevelView L, bool c5, cudaStream_t st);
 
 }  // namespace vi
 

@@ -1,231 +1,32 @@
-// vi_search.cu -- the spatio-temporal PatchMatch of Sec. 3.1 (Algorithm 1) as
-// a parallel (Jacobi) sweep, its shift-map initialisation and the level
-// transition of Sec. 3.6.
-//
-// One thread per target voxel. Targets are raster ordered, so a warp covers a
-// run of neighbouring voxels along x; with the piecewise-constant shift maps
-// PatchMatch relies on, their candidate source patches are neighbours too, and
-// the 5x5x5 gathers of a warp coalesce into contiguous rows.
-#include "vi_launch.h"
+// vi_search.cu -- the spatio-temporal PatchMatch of Sec. 3.1 (Algorithm 1):
+// the FP32-storage step kernels (vi_ann.cuh), the distance rescoring of the
+// current shifts, the shift-map initialisation and the level transition of
+// Sec. 3.6.
+#include "vi_ann.cuh"
 
 namespace vi {
 
-static inline int blocks_for(long long n, int block)
+void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
 {
-    long long g = (n + block - 1) / block;
-    return (int)(g < 1 ? 1 : g);
-}
-
-// Candidate source for target (px, py, pt) under shift (dx, dy, dt): its
-// linear index when inside the video and in D~, else -1.
-__device__ __forceinline__ int source_of(const LevelView &L, int px, int py, int pt, int dx, int dy,
-                                         int dt)
-{
-    const int sx = px + dx, sy = py + dy, st = pt + dt;
-    if (!inside(L, sx, sy, st))
-        return -1;
-    const int s = st * L.HW + sy * L.W + sx;
-    return (L.code[s] & CODE_SOURCE) ? s : -1;
-}
-
-__device__ __forceinline__ unsigned long long shift_key(int dx, int dy, int dt)
-{
-    return ((unsigned long long)(unsigned short)dx) | ((unsigned long long)(unsigned short)dy << 16) |
-           ((unsigned long long)(unsigned short)dt << 32);
-}
-
-// Shifts rejected so far in one iteration (at most 3 need remembering).
-struct Rejected {
-    unsigned long long k0 = ~0ull, k1 = ~0ull, k2 = ~0ull;
-    __device__ __forceinline__ bool has(unsigned long long k) const { return k == k0 || k == k1 || k == k2; }
-    __device__ __forceinline__ void add(unsigned long long k)
-    {
-        k2 = k1;
-        k1 = k0;
-        k0 = k;
-    }
-};
-
-// ---------------------------------------------------------------------------
-// Lane groups. A coarse level has too few targets to fill 152 SMs with one
-// thread each, and one thread's candidates are a chain of dependent memory
-// round trips. So G consecutive lanes (G = 1, 2, 4, 8; chosen from the target
-// count) share a target: they make the same decisions on the same data and
-// split each distance's five slices between them (group_d2). PARTIAL selects
-// the partial distance of Eq. 11 (onion peel).
-// ---------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ unsigned group_mask()
-{
-    return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-}
-
-// One candidate of Algorithm 1 for target p: counted as an evaluation when it
-// lands in D~ (the oracle counts the same). A candidate equal to the current
-// best shift, or to one already rejected in this iteration, has that shift's
-// distance, which cannot be strictly smaller than the current best, so it is
-// resolved without a gather. Otherwise the G lanes of the group gather its
-// distance, bounded by the current best; the decision is the same bit for bit
-// as with a full evaluation.
-template <bool C5, int G, bool PARTIAL>
-__device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px, int py, int pt, int s,
-                                                int cdx, int cdy, int cdt, Shift &cur, float &d,
-                                                Rejected &rej, unsigned &evals, unsigned &gathered, int sub,
-                                                unsigned gmask)
-{
-    if (s < 0)
+    if (a.nT <= 0)
         return;
-    ++evals;
-    const unsigned long long key = shift_key(cdx, cdy, cdt);
-    if (key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key))
-        return;
-    const float dd = group_d2<C5, G, PARTIAL>(a.L, p, px, py, pt, s, a.excl, d, sub, gmask, gathered);
-    if (dd < d) {
-        d = dd;
-        cur.dx = (short)cdx;
-        cur.dy = (short)cdy;
-        cur.dt = (short)cdt;
-    } else {
-        rej.add(key);
-    }
-}
-
-// One PatchMatch iteration k for every target: propagation from the three
-// neighbours (Algorithm 1; sign by the parity of k), then the random search
-// of Eq. 3 around the propagated shift. Reads phi_in / d_in (the state when
-// iteration k began), writes phi_out / d_out. The three neighbours' shifts and
-// their sources' set codes are loaded together before any distance.
-// The step for target i of the clip described by a (iteration k), by the G
-// lanes of one group.
-template <bool C5, int G, bool PARTIAL>
-__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub, unsigned gmask,
-                                        unsigned &evals, unsigned &gathered)
-{
-    {
-        const LevelView &L = a.L;
-        const int p = a.targets[i];
-        int px, py, pt;
-        decode(p, L.W, L.HW, px, py, pt);
-        Shift cur = a.phi_in[p];
-        float d = a.d_in[p];
-        const int sg = (k & 1) ? 1 : -1;   // odd k: +1 neighbours; even k: -1
-
-        // propagation candidates phi(p + sg e_x), phi(p + sg e_y), phi(p + sg e_t)
-        const bool in0 = inside(L, px + sg, py, pt), in1 = inside(L, px, py + sg, pt),
-                   in2 = inside(L, px, py, pt + sg);
-        const int r0 = in0 ? p + sg : p, r1 = in1 ? p + sg * L.W : p, r2 = in2 ? p + sg * L.HW : p;
-        const bool t0 = in0 && (a.tmask[r0] & a.tbit), t1 = in1 && (a.tmask[r1] & a.tbit),
-                   t2 = in2 && (a.tmask[r2] & a.tbit);
-        const Shift c0 = a.phi_in[r0], c1 = a.phi_in[r1], c2 = a.phi_in[r2];
-        const int s0 = t0 ? source_of(L, px, py, pt, c0.dx, c0.dy, c0.dt) : -1;
-        const int s1 = t1 ? source_of(L, px, py, pt, c1.dx, c1.dy, c1.dt) : -1;
-        const int s2 = t2 ? source_of(L, px, py, pt, c2.dx, c2.dy, c2.dt) : -1;
-        Rejected rej;
-        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s0, c0.dx, c0.dy, c0.dt, cur, d, rej, evals,
-                                        gathered, sub, gmask);
-        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s1, c1.dx, c1.dy, c1.dt, cur, d, rej, evals,
-                                        gathered, sub, gmask);
-        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s2, c2.dx, c2.dy, c2.dt, cur, d, rej, evals,
-                                        gathered, sub, gmask);
-
-        // random search (Eq. 3)
-        const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip, 0u),
-                                      a.key0, a.key1);
-        const int shift = a.rho_log2 * k + 24;
-        const int cdx = cur.dx + random_offset(w.x, a.rmax, shift);
-        const int cdy = cur.dy + random_offset(w.y, a.rmax, shift);
-        const int cdt = cur.dt + random_offset(w.z, a.rmax, shift);
-        const int s3 = source_of(L, px, py, pt, cdx, cdy, cdt);
-        try_candidate_g<C5, G, PARTIAL>(a, p, px, py, pt, s3, cdx, cdy, cdt, cur, d, rej, evals, gathered,
-                                        sub, gmask);
-        if (sub == 0) {
-            a.phi_out[p] = cur;
-            a.d_out[p] = d;
-        }
-    }
-}
-
-template <bool C5, int G, bool PARTIAL>
-__global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
-{
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = gt / G;
-    const int sub = gt & (G - 1);
-    const unsigned gmask = group_mask<G>();
-    unsigned evals = 0, gathered = 0;
-    if (i < a.nT)
-        ann_one<C5, G, PARTIAL>(a, i, a.k, sub, gmask, evals, gathered);
-    count_evals(a.evals, sub == 0 ? evals : 0u);
-    count_evals(a.gathered, gathered);
-}
-
-static int pick_group(int nT);
-
-// Batch form: the targets of n clips in one persistent launch. Clip c owns
-// the global target indices [prefix[c], prefix[c+1]) and is described by
-// descs[c]; every clip runs iteration k. A grid-stride loop over groups keeps
-// the grid at the resident size whatever the batch holds.
-template <bool C5, int G>
-__global__ void __launch_bounds__(256) k_ann_step_batch(const BatchClip *__restrict__ clips,
-                                                        const int *__restrict__ prefix, int n, int k,
-                                                        unsigned long long *evals_ctr,
-                                                        unsigned long long *gathered_ctr)
-{
-    const int total = __ldg(prefix + n);
-    const int sub = (blockIdx.x * blockDim.x + threadIdx.x) & (G - 1);
-    const unsigned gmask = group_mask<G>();
-    const int stride = gridDim.x * blockDim.x / G;
-    unsigned evals = 0, gathered = 0;
-    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
-        const int c = find_segment(prefix, n, g);
-        const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
-        ann_one<C5, G, false>(a, g - __ldg(prefix + c), k, sub, gmask, evals, gathered);
-    }
-    count_evals(evals_ctr, sub == 0 ? evals : 0u);
-    count_evals(gathered_ctr, gathered);
-}
-
-// Grid of a persistent batch launch: one wave of 256-thread blocks, or fewer
-// when the work is smaller.
-static int persistent_grid(long long threads)
-{
-    static int sms = 0;
-    if (sms <= 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-    }
-    const long long cap = (long long)sms * 8;   // 8 blocks of 256 threads per SM
-    const long long need = (threads + 255) / 256;
-    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
-}
-
-template <bool C5, int G>
-static void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, int total, int k,
-                                    unsigned long long *evals, unsigned long long *gathered, cudaStream_t st)
-{
-    k_ann_step_batch<C5, G><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, k, evals,
-                                                                                  gathered);
+    VI_COUNT_LAUNCH();
+    if (a.L.h4 && !a.excl)
+        launch_ann_step_f16(a, c5, st);
+    else
+        launch_ann_step_impl<false>(a, c5, st);
 }
 
 void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
-                           bool c5, unsigned long long *evals, unsigned long long *gathered, int lanes,
-                           cudaStream_t st)
+                           bool c5, bool f16, unsigned long long *ctr, int lanes, cudaStream_t st)
 {
     if (total_targets <= 0 || n <= 0)
         return;
     VI_COUNT_LAUNCH();
-    switch ((lanes > 0 ? lanes : pick_group(total_targets)) * 2 + (c5 ? 1 : 0)) {
-    case 2: launch_ann_step_batch_g<false, 1>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 3: launch_ann_step_batch_g<true, 1>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 4: launch_ann_step_batch_g<false, 2>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 5: launch_ann_step_batch_g<true, 2>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 8: launch_ann_step_batch_g<false, 4>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 9: launch_ann_step_batch_g<true, 4>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    case 16: launch_ann_step_batch_g<false, 8>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    default: launch_ann_step_batch_g<true, 8>(clips, tprefix, n, total_targets, k, evals, gathered, st); break;
-    }
+    if (f16)
+        launch_ann_step_batch_f16(clips, tprefix, n, total_targets, k, c5, ctr, lanes, st);
+    else
+        launch_ann_step_batch_impl<false>(clips, tprefix, n, total_targets, k, c5, ctr, lanes, st);
 }
 
 // Distances of the current shifts (buffer 0) for every target of a batch.
@@ -281,59 +82,6 @@ void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int
     case 9: launch_rescore_batch_g<true, 4>(clips, tprefix, n, total_targets, evals, st); break;
     case 16: launch_rescore_batch_g<false, 8>(clips, tprefix, n, total_targets, evals, st); break;
     default: launch_rescore_batch_g<true, 8>(clips, tprefix, n, total_targets, evals, st); break;
-    }
-}
-
-// Lanes per target: the smallest G in {1, 2, 4, 8} that gives the level at
-// least 512 threads per SM. Measured on the 320x240x60 workload (one launch,
-// microseconds, G = 1 / 2 / 4 / 8): 445k targets 280 / 301 / 447 / 681,
-// 126k targets 101 / 108 / 147 / 207, 40k targets 79 / 51 / 60 / 82, 15k
-// targets 78 / 46 / 37 / 34: more lanes pay only while the targets alone
-// leave the SMs idle. The partial distance (onion peel, coarsest level, few
-// targets) always uses G = 8.
-static int pick_group(int nT)
-{
-    static int sms = 0;
-    if (sms <= 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-    }
-    const long long want = (long long)sms * 512;
-    int G = 1;
-    while (G < 8 && (long long)nT * G < want)
-        G *= 2;
-    return G;
-}
-
-template <bool C5, int G, bool PARTIAL>
-static void launch_ann_step_g(const AnnArgs &a, cudaStream_t st)
-{
-    k_ann_step<C5, G, PARTIAL><<<blocks_for((long long)a.nT * G, 256), 256, 0, st>>>(a);
-}
-
-void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
-{
-    if (a.nT <= 0)
-        return;
-    VI_COUNT_LAUNCH();
-    if (a.excl) {
-        if (c5)
-            launch_ann_step_g<true, 8, true>(a, st);
-        else
-            launch_ann_step_g<false, 8, true>(a, st);
-        return;
-    }
-    switch ((a.lanes > 0 ? a.lanes : pick_group(a.nT)) * 2 + (c5 ? 1 : 0)) {
-    case 2: launch_ann_step_g<false, 1, false>(a, st); break;
-    case 3: launch_ann_step_g<true, 1, false>(a, st); break;
-    case 4: launch_ann_step_g<false, 2, false>(a, st); break;
-    case 5: launch_ann_step_g<true, 2, false>(a, st); break;
-    case 8: launch_ann_step_g<false, 4, false>(a, st); break;
-    case 9: launch_ann_step_g<true, 4, false>(a, st); break;
-    case 16: launch_ann_step_g<false, 8, false>(a, st); break;
-    default: launch_ann_step_g<true, 8, false>(a, st); break;
     }
 }
 
@@ -503,9 +251,17 @@ __global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restri
     int px, py, pt;
     decode(p, F.W, F.HW, px, py, pt);
     const int q = pt * C.HW + (py >> 1) * C.W + (px >> 1);
-    F.x4[p] = C.x4[q];
+    const float4 a = C.x4[q];
+    const float b = c5 ? C.x1[q] : 0.0f;
+    F.x4[p] = a;
     if (c5)
-        F.x1[p] = C.x1[q];
+        F.x1[p] = b;
+    if (F.h4) {
+        if (c5)
+            shadow_store_raise<true>(F, p, a, b);
+        else
+            shadow_store_raise<false>(F, p, a, b);
+    }
 }
 
 void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH, bool c5,

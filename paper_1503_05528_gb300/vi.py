@@ -30,7 +30,7 @@ EXPORTS = [
     "vi_profile", "vi_get_stats", "vi_energy_noalloc",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
-    "vi_batch_get_stats", "vi_batch_profile", "vi_batch_step_time",
+    "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
 ]
 
 
@@ -43,7 +43,8 @@ class ViConfig(C.Structure):
 
 class ViStats(C.Structure):
     _fields_ = [("evals", C.c_ulonglong), ("step_evals", C.c_ulonglong),
-                ("step_gathered", C.c_ulonglong),
+                ("step_gathered", C.c_ulonglong), ("step_gathered_h", C.c_ulonglong),
+                ("screened", C.c_ulonglong), ("screen_passed", C.c_ulonglong),
                 ("step_launches", C.c_ulonglong), ("step_ms", C.c_double),
                 ("step_timed", C.c_ulonglong), ("outer", C.c_int * 16),
                 ("onion_layers", C.c_int), ("levels", C.c_int), ("launches", C.c_ulonglong)]
@@ -126,6 +127,7 @@ def _declare(L):
     L.vi_batch_remove.argtypes = [vp, i]
     L.vi_batch_clip_stats.argtypes = [vp, i, P(ViStats)]
     L.vi_batch_get_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
+    L.vi_batch_screen_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
     L.vi_batch_profile.argtypes = [vp, i]
     L.vi_batch_step_time.argtypes = [vp, P(d), P(ull)]
 
@@ -303,14 +305,12 @@ class Context:
     def stats(self):
         s = ViStats()
         self._ck(self.lib.vi_get_stats(self.h, C.byref(s)))
-        return dict(evals=s.evals, step_evals=s.step_evals, step_gathered=s.step_gathered,
-                    step_launches=s.step_launches,
-                    step_ms=s.step_ms, step_timed=s.step_timed, outer=list(s.outer),
-                    onion_layers=s.onion_layers, levels=s.levels, launches=s.launches)
+        return _stats_dict(s)
 
 
 def _stats_dict(s):
     return dict(evals=s.evals, step_evals=s.step_evals, step_gathered=s.step_gathered,
+                step_gathered_h=s.step_gathered_h, screened=s.screened, screen_passed=s.screen_passed,
                 step_launches=s.step_launches, step_ms=s.step_ms, step_timed=s.step_timed,
                 outer=list(s.outer), onion_layers=s.onion_layers, levels=s.levels,
                 launches=s.launches)
@@ -405,8 +405,10 @@ class Batch:
         self._ck(self.lib.vi_batch_get_stats(self.h, C.byref(e), C.byref(g), C.byref(r)))
         ms, se = C.c_double(0.0), C.c_ulonglong(0)
         self._ck(self.lib.vi_batch_step_time(self.h, C.byref(ms), C.byref(se)))
+        gh, sc, sp = C.c_ulonglong(0), C.c_ulonglong(0), C.c_ulonglong(0)
+        self._ck(self.lib.vi_batch_screen_stats(self.h, C.byref(gh), C.byref(sc), C.byref(sp)))
         return dict(evals=e.value, gathered=g.value, rounds=r.value, step_ms=ms.value,
-                    step_evals=se.value)
+                    step_evals=se.value, gathered_h=gh.value, screened=sc.value, screen_passed=sp.value)
 
     def profile(self, enable=True):
         self._ck(self.lib.vi_batch_profile(self.h, 1 if enable else 0))
