@@ -43,12 +43,15 @@ UNIT = "evals/s"
 WORKLOAD = "layered_320x240x60"
 BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
 BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
-BYTES_PER_VOXEL_FP16_C5 = 5 * 2           # the same voxel from the FP16 copy
+BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the FP16 copy
 
-# dram bytes (read + write) of one launch of the PatchMatch step kernel and the
-# source voxels that launch gathered, from one ncu capture (see profiles/);
-# None when the kernel changed since the capture.
-NCU_STEP_TRAFFIC = None
+# DRAM bytes (read + write) per launch of the PatchMatch step kernel, averaged
+# over the 330 step launches of one inpainting of the default workload with
+# FP32 storage, and the source voxels those launches gathered per launch, from
+# one ncu capture (profiles/k_ann_step_layered_320x240x60.md). Applies to that
+# workload and storage only; set to None when the kernel changes.
+NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
+                    "bytes": 9.016e6, "gathered_voxels": 6499884}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
@@ -328,14 +331,15 @@ def run_gpu(args):
 
     peak, peak_kind = _peaks()
     # algorithmic bytes of the step kernel: the source voxels it has to gather
-    # (20 B each: 5 FP32 channels; 10 B from the FP16 copy when screening). A
+    # (20 B each: 5 FP32 channels; 8 B from the FP16 copy when screening). A
     # candidate equal to a shift already compared needs no gather, and a gather
     # stops once the partial sum shows the candidate cannot win; both leave
     # every decision unchanged.
-    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5 + step_gathered_h * BYTES_PER_VOXEL_FP16_C5
+    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5 + step_gathered_h * BYTES_PER_VOXEL_FP16
     achieved = gathered_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     traffic = None
-    if NCU_STEP_TRAFFIC and step_launches:
+    if (NCU_STEP_TRAFFIC and step_launches and NCU_STEP_TRAFFIC["workload"] == args.workload
+            and NCU_STEP_TRAFFIC["storage"] == args.storage):
         per_voxel = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["gathered_voxels"]
         traffic = per_voxel * step_gathered / step_launches
     line = {
@@ -358,7 +362,7 @@ def run_gpu(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
                      "gathered_bytes_per_launch": gathered_bytes / step_launches if step_launches else None,
                      "launches_timed": step_launches,
                      "evals_per_launch": step_evals / step_launches if step_launches else None,
@@ -483,7 +487,7 @@ def run_batch(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16_C5
+    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16
     achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     line = {
         "metric": METRIC, "value": sm[1] / (mx[0] / 1e3), "unit": UNIT, "n_gpus": world,
@@ -507,7 +511,7 @@ def run_batch(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": None,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
                      "kernel_ms_share": step_ms / ms if ms > 0 else None},
         "clocks": clocks,
     }
@@ -630,7 +634,7 @@ def run_serve(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16_C5
+    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16
     achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     pct = lambda x, q: float(np.percentile(x, q, method="inverted_cdf"))  # noqa: E731
     line = {
@@ -660,7 +664,7 @@ def run_serve(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": None,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 10 B (FP16 copy)",
+                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
                      "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None},
         "e2e": {"value": sm[1] / mx[0], "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v * 13 for v in vox)),

@@ -71,14 +71,14 @@ typedef struct {
                             channel and voxel of H between iterations (0.1/255) */
     int weighted;        /* 1: weights of Eq. 5; 0: the unweighted mean (s = 1) */
     int use_texture;     /* 1: C = 5 channels (Sec. 3.3); 0: RGB only (C = 3) */
-    int storage;         /* 0: FP32 channels. 1: FP32 channels plus an FP16 copy;
-                            the PatchMatch step screens each candidate on the
-                            FP16 copy with a rigorous error bound and computes
-                            the FP32 distance only when the candidate could
-                            beat the current best, so results are identical to
+    int storage;         /* 0: FP32 channels. 1: FP32 channels plus an FP16 copy
+                            of channels c0..c3 (8 B per voxel); the PatchMatch
+                            step screens each random-search candidate on that
+                            copy with a rigorous error bound and computes the
+                            FP32 distance only when the candidate could beat
+                            the current best, so results are identical to
                             storage 0 (the paper fixes no storage precision;
-                            this is a speed option). The partial distance of
-                            the initialisation (Eq. 11) always reads FP32. */
+                            this is a speed option for clips larger than L2). */
     uint64_t seed;       /* Philox4x32-10 key (key words: low, high 32 bits) */
     uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
     int lanes_per_target; /* GPU lanes sharing one target in the search kernels:
@@ -94,8 +94,8 @@ typedef struct {
     unsigned long long step_gathered;  /* source voxels the step kernel read: candidates
                                           equal to a shift already compared need none,
                                           and a gather stops once it cannot win */
-    unsigned long long step_gathered_h; /* FP16 source voxels the step kernel read
-                                          (storage 1: candidate screening) */
+    unsigned long long step_gathered_h; /* FP16 source voxels (8 B) the step kernel
+                                          read (storage 1: candidate screening) */
     unsigned long long screened;       /* candidates screened on the FP16 copy */
     unsigned long long screen_passed;  /* of those, evaluated in FP32 */
     unsigned long long step_launches;  /* launches of the PatchMatch step kernel */

@@ -90,7 +90,6 @@ void free_state(vi_ctx *ctx)
         dfree(l.x1);
         dfree(l.code);
         dfree(l.h4);
-        dfree(l.h1);
         dfree(l.hmax);
         dfree(l.phi[0]);
         dfree(l.phi[1]);
@@ -400,7 +399,7 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
         // FP16 copies
         total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 12);
         if (cfg && cfg->storage == 1)
-            total += V * (8 + (c5 ? 2 : 0)) + 256;
+            total += V * 8 + 256;
         w = (w + 1) / 2;
         h = (h + 1) / 2;
     }
@@ -460,8 +459,6 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
         TRY(dalloc(ctx, &lv.code, V));
         if (ctx->cfg.storage == 1) {
             TRY(dalloc(ctx, &lv.h4, V * sizeof(uint2)));
-            if (ctx->c5)
-                TRY(dalloc(ctx, &lv.h1, V * sizeof(unsigned short)));
             TRY(dalloc(ctx, &lv.hmax, 8 * sizeof(unsigned)));
         }
         for (int b = 0; b < 2; ++b) {
@@ -528,7 +525,7 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
     // FP16 storage: the copies of every level and their magnitude bounds
     for (int l = 0; l < ctx->L && ctx->cfg.storage == 1; ++l) {
         CK(cudaMemsetAsync(ctx->lv[l].hmax, 0, 8 * sizeof(unsigned), st));
-        launch_shadow_all(ctx->lv[l].view(), ctx->c5, st);
+        launch_shadow_all(ctx->lv[l].view(), st);
         CK_LAUNCH();
     }
     // list sizes (one synchronisation), then the lists
@@ -844,7 +841,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
     const size_t bytes = (size_t)l.V * C * sizeof(float);
     if (ptr_is_device) {
         launch_set_channels(l.view(), in, C, ctx->stream);
-        launch_shadow_all(l.view(), ctx->c5, ctx->stream);
+        launch_shadow_all(l.view(), ctx->stream);
         CK_LAUNCH();
         return VI_OK;
     }
@@ -853,7 +850,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
     cudaError_t e = cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) {
         launch_set_channels(l.view(), tmp, C, ctx->stream);
-        launch_shadow_all(l.view(), ctx->c5, ctx->stream);
+        launch_shadow_all(l.view(), ctx->stream);
         e = cudaStreamSynchronize(ctx->stream);
     }
     cudaFree(tmp);

@@ -29,8 +29,7 @@ struct Level {
     float4 *x4 = nullptr;
     float *x1 = nullptr;
     uint8_t *code = nullptr;
-    uint2 *h4 = nullptr;              // FP16 storage: copies of x4 / x1, |x| bounds
-    unsigned short *h1 = nullptr;
+    uint2 *h4 = nullptr;              // FP16 storage: copy of x4, |x| bounds
     unsigned *hmax = nullptr;
     Shift *phi[2] = {nullptr, nullptr};
     float *d2[2] = {nullptr, nullptr};
@@ -49,7 +48,6 @@ struct Level {
         v.x1 = x1;
         v.code = code;
         v.h4 = h4;
-        v.h1 = h1;
         v.hmax = hmax;
         return v;
     }

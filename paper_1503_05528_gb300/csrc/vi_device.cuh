@@ -18,10 +18,10 @@ struct __align__(8) Shift {
 };
 
 // One pyramid level as the kernels see it. Channels c0..c3 live in x4 (c3 = 0
-// when C = 3), channel c4 in x1 (C = 5 only). With FP16 storage, h4 / h1 hold
-// the same channels rounded to FP16 (four halves per uint2, one per ushort)
-// and hmax[c] bounds |x_c| over every value the level has held (float bits,
-// raised with atomicMax); h4 == nullptr means FP32 storage only.
+// when C = 3), channel c4 in x1 (C = 5 only). With FP16 storage, h4 holds
+// channels c0..c3 rounded to FP16 (four halves per uint2) and hmax[c] bounds
+// |x_c| over every value the level has held (float bits, raised with
+// atomicMax); h4 == nullptr means FP32 storage only.
 struct LevelView {
     int W, H, T;
     int HW;          // W * H
@@ -30,7 +30,6 @@ struct LevelView {
     float *x1;
     uint8_t *code;
     uint2 *h4;
-    unsigned short *h1;
     unsigned *hmax;
 };
 
@@ -100,10 +99,11 @@ __device__ __forceinline__ float half_lo(unsigned u) { return __half2float(__ush
 __device__ __forceinline__ float half_hi(unsigned u) { return __half2float(__ushort_as_half((unsigned short)(u >> 16))); }
 
 // Adds the terms of voxel pair (r, s) to acc: from the FP32 channels, or with
-// H from their FP16 copies (converted exactly to FP32).
+// H from the FP16 copies of c0..c3 (converted exactly to FP32).
 template <bool C5, bool H = false>
 __device__ __forceinline__ void acc_voxel(const LevelView &L, int r, int s, float &acc)
 {
+    static_assert(!(C5 && H), "the FP16 copy holds channels c0..c3 only");
     float a0, a1, a2, a3, b0, b1, b2, b3;
     if (H) {
         const uint2 ua = __ldg(L.h4 + r), ub = __ldg(L.h4 + s);
@@ -121,11 +121,7 @@ __device__ __forceinline__ void acc_voxel(const LevelView &L, int r, int s, floa
     df = __fsub_rn(a2, b2); acc = __fmaf_rn(df, df, acc);
     df = __fsub_rn(a3, b3); acc = __fmaf_rn(df, df, acc);
     if (C5) {
-        if (H)
-            df = __fsub_rn(__half2float(__ushort_as_half(__ldg(L.h1 + r))),
-                           __half2float(__ushort_as_half(__ldg(L.h1 + s))));
-        else
-            df = __fsub_rn(__ldg(L.x1 + r), __ldg(L.x1 + s));
+        df = __fsub_rn(__ldg(L.x1 + r), __ldg(L.x1 + s));
         acc = __fmaf_rn(df, df, acc);
     }
 }
@@ -363,8 +359,8 @@ __device__ __forceinline__ float group_d2(const LevelView &L, int p, int px, int
     return __fdiv_rn(total, 125.0f);
 }
 
-// FP16 copy of voxel v's channels (FP16 storage: L.h4 != nullptr), and
-// hmax raised to cover the values written. hmax holds |x| as float bits, so
+// FP16 copy of voxel v's channels c0..c3 (FP16 storage: L.h4 != nullptr),
+// and hmax raised to cover the values written. hmax holds |x| as float bits, so
 // unsigned comparison orders it (a NaN compares above +inf and disables the
 // screening below).
 __device__ __forceinline__ unsigned pack_half2(float lo, float hi)
@@ -381,25 +377,19 @@ __device__ __forceinline__ void raise_hmax(unsigned *hmax, int c, unsigned m)
         atomicMax(hmax + c, m);
 }
 
-template <bool C5>
-__device__ __forceinline__ void shadow_store(const LevelView &L, int v, float4 a, float b)
+__device__ __forceinline__ void shadow_store(const LevelView &L, int v, float4 a)
 {
     L.h4[v] = make_uint2(pack_half2(a.x, a.y), pack_half2(a.z, a.w));
-    if (C5)
-        L.h1[v] = __half_as_ushort(__float2half_rn(b));
 }
 
 // shadow_store for one voxel written by a single thread, hmax raised at once.
-template <bool C5>
-__device__ __forceinline__ void shadow_store_raise(const LevelView &L, int v, float4 a, float b)
+__device__ __forceinline__ void shadow_store_raise(const LevelView &L, int v, float4 a)
 {
-    shadow_store<C5>(L, v, a, b);
+    shadow_store(L, v, a);
     raise_hmax(L.hmax, 0, abs_bits(a.x));
     raise_hmax(L.hmax, 1, abs_bits(a.y));
     raise_hmax(L.hmax, 2, abs_bits(a.z));
     raise_hmax(L.hmax, 3, abs_bits(a.w));
-    if (C5)
-        raise_hmax(L.hmax, 4, abs_bits(b));
 }
 
 // ---------------------------------------------------------------------------

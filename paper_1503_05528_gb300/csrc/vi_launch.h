@@ -138,8 +138,9 @@ void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st);
 void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st);
 void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st);
 void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st);
-// FP16 copies of every voxel of a level (no-op for FP32 storage).
-void launch_shadow_all(LevelView L, bool c5, cudaStream_t st);
+// FP16 copies of channels c0..c3 of every voxel of a level (no-op for FP32
+// storage).
+void launch_shadow_all(LevelView L, cudaStream_t st);
 
 }  // namespace vi
 

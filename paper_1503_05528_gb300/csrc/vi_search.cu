@@ -252,16 +252,11 @@ __global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restri
     decode(p, F.W, F.HW, px, py, pt);
     const int q = pt * C.HW + (py >> 1) * C.W + (px >> 1);
     const float4 a = C.x4[q];
-    const float b = c5 ? C.x1[q] : 0.0f;
     F.x4[p] = a;
     if (c5)
-        F.x1[p] = b;
-    if (F.h4) {
-        if (c5)
-            shadow_store_raise<true>(F, p, a, b);
-        else
-            shadow_store_raise<false>(F, p, a, b);
-    }
+        F.x1[p] = C.x1[q];
+    if (F.h4)
+        shadow_store_raise(F, p, a);
 }
 
 void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH, bool c5,

@@ -117,11 +117,10 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
                 const float4 nw = make_float4(n0 / den, n1 / den, n2 / den, n3 / den);
                 change = fabsf(nw.x - old.x) + fabsf(nw.y - old.y) + fabsf(nw.z - old.z);
                 L.x4[p] = nw;
-                const float n4v = C5 ? n4 / den : 0.0f;
                 if (C5)
-                    L.x1[p] = n4v;
+                    L.x1[p] = n4 / den;
                 if (L.h4)
-                    shadow_store_raise<C5>(L, p, nw, n4v);
+                    shadow_store_raise(L, p, nw);
                 if (a.hp)
                     a.hp[p] = 0;
             }
@@ -268,12 +267,11 @@ __global__ void k_final(LevelView L, const int *__restrict__ holes, int nH, cons
         return;
     const int s = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
     const float4 a = L.x4[s];
-    const float b = C5 ? L.x1[s] : 0.0f;
     L.x4[p] = a;
     if (C5)
-        L.x1[p] = b;
+        L.x1[p] = L.x1[s];
     if (L.h4)
-        shadow_store_raise<C5>(L, p, a, b);
+        shadow_store_raise(L, p, a);
 }
 
 void launch_final(LevelView L, const int *holes, int nH, const Shift *phi, const float *d2, bool c5,
@@ -505,36 +503,30 @@ void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st)
 }
 
 // FP16 copies of every voxel of a level; hmax raised once per warp.
-template <bool C5>
 __global__ void k_shadow_all(LevelView L)
 {
-    unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
+    unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < L.V; v += gridDim.x * blockDim.x) {
         const float4 a = L.x4[v];
-        const float b = C5 ? L.x1[v] : 0.0f;
-        shadow_store<C5>(L, v, a, b);
+        shadow_store(L, v, a);
         m0 = max(m0, abs_bits(a.x));
         m1 = max(m1, abs_bits(a.y));
         m2 = max(m2, abs_bits(a.z));
         m3 = max(m3, abs_bits(a.w));
-        m4 = max(m4, abs_bits(b));
     }
     m0 = __reduce_max_sync(0xffffffffu, m0);
     m1 = __reduce_max_sync(0xffffffffu, m1);
     m2 = __reduce_max_sync(0xffffffffu, m2);
     m3 = __reduce_max_sync(0xffffffffu, m3);
-    m4 = __reduce_max_sync(0xffffffffu, m4);
     if ((threadIdx.x & 31) == 0) {
         raise_hmax(L.hmax, 0, m0);
         raise_hmax(L.hmax, 1, m1);
         raise_hmax(L.hmax, 2, m2);
         raise_hmax(L.hmax, 3, m3);
-        if (C5)
-            raise_hmax(L.hmax, 4, m4);
     }
 }
 
-void launch_shadow_all(LevelView L, bool c5, cudaStream_t st)
+void launch_shadow_all(LevelView L, cudaStream_t st)
 {
     if (!L.h4 || L.V <= 0)
         return;
@@ -542,10 +534,7 @@ void launch_shadow_all(LevelView L, bool c5, cudaStream_t st)
     if (g > 152 * 16)
         g = 152 * 16;
     VI_COUNT_LAUNCH();
-    if (c5)
-        k_shadow_all<true><<<(int)g, 256, 0, st>>>(L);
-    else
-        k_shadow_all<false><<<(int)g, 256, 0, st>>>(L);
+    k_shadow_all<<<(int)g, 256, 0, st>>>(L);
 }
 
 }  // namespace vi
