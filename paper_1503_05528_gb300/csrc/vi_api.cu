@@ -109,12 +109,13 @@ void free_state(vi_ctx *ctx)
     dfree(ctx->block_counts);
     dfree(ctx->partials);
     dfree(ctx->partials2);
+    dfree(ctx->chunks);
     dfree(ctx->hp);
     dfree(ctx->layer);
     dfree(ctx->ltgt);
     dfree(ctx->layer_list);
     dfree(ctx->ltgt_list);
-    ctx->partials_cap = ctx->partials2_cap = 0;
+    ctx->partials_cap = ctx->partials2_cap = ctx->chunks_cap = 0;
     ctx->uploaded = ctx->built = false;
 }
 
@@ -247,7 +248,14 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
     launch_vote(a, ctx->c5, ctx->stream);
     CK_LAUNCH();
     if (change_dev) {
-        launch_sum_partials(ctx->partials, l.nH, change_dev, ctx->stream);
+        const int nc = std::max(sum_chunks(l.nH), 1);
+        if (nc > ctx->chunks_cap) {
+            dfree(ctx->chunks);
+            ctx->chunks_cap = 0;
+            TRY(dalloc(ctx, &ctx->chunks, sizeof(double) * (size_t)nc));
+            ctx->chunks_cap = nc;
+        }
+        launch_sum_partials(ctx->partials, l.nH, ctx->chunks, change_dev, ctx->stream);
         CK_LAUNCH();
     }
     return VI_OK;

@@ -51,10 +51,13 @@ struct vi_batch {
 
     int cap = 0;                       // clips the descriptor buffers hold
     BatchClip *d_clips = nullptr, *h_clips = nullptr;
-    int *d_prefix = nullptr, *h_prefix = nullptr;   // targets (cap + 1) then holes (cap + 1)
+    // targets (cap + 1), holes (cap + 1), chunks of the change sums (cap + 1)
+    int *d_prefix = nullptr, *h_prefix = nullptr;
     double *d_e = nullptr, *h_e = nullptr;
     float *d_change = nullptr;
     long long change_cap = 0;
+    double *d_chunks = nullptr;
+    int chunks_cap = 0;
     // rescore evals, step evals, FP32 voxels gathered, FP16 voxels gathered,
     // screened, passed
     unsigned long long *counters = nullptr;
@@ -91,7 +94,7 @@ Entry *find(vi_batch *b, int id)
     return nullptr;
 }
 
-vi_status ensure_capacity(vi_batch *b, int n, long long holes)
+vi_status ensure_capacity(vi_batch *b, int n, long long holes, int chunks = 0)
 {
     if (n > b->cap) {
         int cap = std::max(n, std::max(16, 2 * b->cap));
@@ -107,8 +110,8 @@ vi_status ensure_capacity(vi_batch *b, int n, long long holes)
         b->cap = 0;
         BCK(cudaMalloc((void **)&b->d_clips, sizeof(BatchClip) * cap));
         BCK(cudaMallocHost((void **)&b->h_clips, sizeof(BatchClip) * cap));
-        BCK(cudaMalloc((void **)&b->d_prefix, sizeof(int) * 2 * (cap + 1)));
-        BCK(cudaMallocHost((void **)&b->h_prefix, sizeof(int) * 2 * (cap + 1)));
+        BCK(cudaMalloc((void **)&b->d_prefix, sizeof(int) * 3 * (cap + 1)));
+        BCK(cudaMallocHost((void **)&b->h_prefix, sizeof(int) * 3 * (cap + 1)));
         BCK(cudaMalloc((void **)&b->d_e, sizeof(double) * cap));
         BCK(cudaMallocHost((void **)&b->h_e, sizeof(double) * cap));
         b->cap = cap;
@@ -120,6 +123,14 @@ vi_status ensure_capacity(vi_batch *b, int n, long long holes)
         b->change_cap = 0;
         BCK(cudaMalloc((void **)&b->d_change, sizeof(float) * (size_t)std::max(cap, 1ll)));
         b->change_cap = cap;
+    }
+    if (chunks > b->chunks_cap) {
+        const int cap = std::max(chunks, 2 * b->chunks_cap);
+        if (b->d_chunks) cudaFree(b->d_chunks);
+        b->d_chunks = nullptr;
+        b->chunks_cap = 0;
+        BCK(cudaMalloc((void **)&b->d_chunks, sizeof(double) * (size_t)cap));
+        b->chunks_cap = cap;
     }
     return VI_OK;
 }
@@ -208,6 +219,7 @@ void vi_batch_destroy(vi_batch *b)
     if (b->d_e) cudaFree(b->d_e);
     if (b->h_e) cudaFreeHost(b->h_e);
     if (b->d_change) cudaFree(b->d_change);
+    if (b->d_chunks) cudaFree(b->d_chunks);
     if (b->counters) cudaFree(b->counters);
     for (auto &e : b->events) {
         cudaEventDestroy(e.first);
@@ -254,7 +266,7 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
     if (!b)
         return VI_ERR_ARG;
     std::vector<Entry *> act;
-    long long tot_t = 0, tot_h = 0;
+    long long tot_t = 0, tot_h = 0, tot_c = 0;
     for (Entry &c : b->clips)
         if (c.state == CLIP_ITERATING)
             act.push_back(&c);
@@ -263,17 +275,21 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
         vi_status s = ensure_capacity(b, n, 0);
         if (s != VI_OK)
             return s;
+        int *tpre_h = b->h_prefix, *hpre_h = b->h_prefix + b->cap + 1, *cpre_h = b->h_prefix + 2 * (b->cap + 1);
         for (int i = 0; i < n; ++i) {
-            b->h_prefix[i] = (int)tot_t;
-            b->h_prefix[b->cap + 1 + i] = (int)tot_h;
+            tpre_h[i] = (int)tot_t;
+            hpre_h[i] = (int)tot_h;
+            cpre_h[i] = (int)tot_c;
             tot_t += act[i]->ctx->lv[act[i]->level].nT;
             tot_h += act[i]->ctx->lv[act[i]->level].nH;
+            tot_c += sum_chunks(act[i]->ctx->lv[act[i]->level].nH);
         }
         if (tot_t >= (1ll << 31) || tot_h >= (1ll << 31))
             return bfail(b, VI_ERR_ARG, "vi_batch_step: batch larger than 2^31 targets");
-        b->h_prefix[n] = (int)tot_t;
-        b->h_prefix[b->cap + 1 + n] = (int)tot_h;
-        s = ensure_capacity(b, n, tot_h);
+        tpre_h[n] = (int)tot_t;
+        hpre_h[n] = (int)tot_h;
+        cpre_h[n] = (int)tot_c;
+        s = ensure_capacity(b, n, tot_h, (int)std::max(tot_c, 1ll));
         if (s != VI_OK)
             return s;
         const int c5 = b->cfg.use_texture != 0;
@@ -322,9 +338,9 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
         }
         cudaStream_t st = b->stream;
         BCK(cudaMemcpyAsync(b->d_clips, b->h_clips, sizeof(BatchClip) * n, cudaMemcpyHostToDevice, st));
-        BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(int) * 2 * (b->cap + 1), cudaMemcpyHostToDevice,
+        BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(int) * 3 * (b->cap + 1), cudaMemcpyHostToDevice,
                             st));
-        const int *tpre = b->d_prefix, *hpre = b->d_prefix + b->cap + 1;
+        const int *tpre = b->d_prefix, *hpre = b->d_prefix + b->cap + 1, *cpre = b->d_prefix + 2 * (b->cap + 1);
         const int lanes = b->cfg.lanes_per_target;
         launch_rescore_batch(b->d_clips, tpre, n, (int)tot_t, c5, b->counters, lanes, st);
         for (int k = 1; k <= b->cfg.n_pm; ++k) {
@@ -352,7 +368,7 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
                 launch_copy_targets(l.targets, l.nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], st);
             }
         launch_vote_batch(b->d_clips, hpre, n, (int)tot_h, c5, st);
-        launch_segment_sums(b->d_change, hpre, n, b->d_e, st);
+        launch_segment_sums(b->d_change, hpre, cpre, n, (int)tot_c, b->d_chunks, b->d_e, st);
         BCK(cudaGetLastError());
         BCK(cudaMemcpyAsync(b->h_e, b->d_e, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         BCK(cudaStreamSynchronize(st));

@@ -79,6 +79,8 @@ struct vi_ctx {
     int partials_cap = 0;
     double *partials2 = nullptr;
     int partials2_cap = 0;
+    double *chunks = nullptr;      // chunk sums of the change array (sum_chunks of the largest hole list)
+    int chunks_cap = 0;
     double *scal = nullptr;        // device scalars
     double *host_scal = nullptr;   // pinned
     int *host_counts = nullptr;    // pinned, 64 ints

@@ -95,11 +95,16 @@ struct VoteArgs {
 };
 int vote_blocks(int n);
 void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st);
-// out[0] = sum of partials[0..n) in a fixed order.
-void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st);
-// out[i] = sum of vals[starts[i] .. starts[i+1]) in the same fixed order
-// (starts in device memory, nseg + 1 entries).
-void launch_segment_sums(const float *vals, const int *starts, int nseg, double *out, cudaStream_t st);
+// out[0] = sum of partials[0..n) in a fixed order, in two stages; chunks
+// holds sum_chunks(n) doubles of scratch.
+int sum_chunks(int n);
+void launch_sum_partials(const float *partials, int n, double *chunks, double *out, cudaStream_t st);
+// out[i] = sum of vals[starts[i] .. starts[i+1]) in the same fixed order;
+// cprefix[i] = sum of sum_chunks over the segments before i (nseg + 1
+// entries, total_chunks = cprefix[nseg]); chunks holds total_chunks doubles.
+// starts and cprefix in device memory.
+void launch_segment_sums(const float *vals, const int *starts, const int *cprefix, int nseg, int total_chunks,
+                         double *chunks, double *out, cudaStream_t st);
 void launch_final(LevelView L, const int *holes, int nH, const Shift *phi, const float *d2,
                   bool c5, cudaStream_t st);
 int energy_blocks(int n);

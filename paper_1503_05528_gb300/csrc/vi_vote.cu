@@ -183,9 +183,9 @@ void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st)
 
 // Deterministic sum of n values by one block of 256 threads: thread j adds
 // elements j, j + 256, ... in FP64, then a fixed-order tree in shared
-// memory. The result depends only on the values, not on where they sit, so a
-// clip's sum is the same alone and inside a batch.
-__device__ double block_sum_range(const float *__restrict__ v, int n)
+// memory. The result depends only on the values, not on where they sit.
+template <typename T>
+__device__ double block_sum_range(const T *__restrict__ v, int n)
 {
     __shared__ double s[256];
     double acc = 0.0;
@@ -203,37 +203,78 @@ __device__ double block_sum_range(const float *__restrict__ v, int n)
     return r;
 }
 
-__global__ void k_sum_partials(const float *__restrict__ partials, int n, double *out)
+// The sum of a per-voxel array (the vote's changes, for e) in two stages that
+// spread the FP64 work over the SMs (FP64 is slow on one SM): every chunk of
+// SUM_CHUNK consecutive values, counted from the start of the clip's array,
+// is summed by one block, then the chunk sums by one block, both with
+// block_sum_range. The order depends only on the clip's own values, so a
+// clip's e is the same alone (launch_sum_partials) and in a batch
+// (launch_segment_sums).
+static constexpr int SUM_CHUNK = 2048;
+
+int sum_chunks(int n) { return n > 0 ? (n + SUM_CHUNK - 1) / SUM_CHUNK : 0; }
+
+__global__ void k_chunk_sums(const float *__restrict__ vals, int n, double *__restrict__ chunks)
 {
-    const double r = block_sum_range(partials, n);
+    const int lo = blockIdx.x * SUM_CHUNK;
+    const double r = block_sum_range(vals + lo, min(SUM_CHUNK, n - lo));
+    if (threadIdx.x == 0)
+        chunks[blockIdx.x] = r;
+}
+
+__global__ void k_sum_chunks(const double *__restrict__ chunks, int nc, double *out)
+{
+    const double r = block_sum_range(chunks, nc);
     if (threadIdx.x == 0)
         out[0] = r;
 }
 
-void launch_sum_partials(const float *partials, int n, double *out, cudaStream_t st)
+void launch_sum_partials(const float *partials, int n, double *chunks, double *out, cudaStream_t st)
 {
+    const int nc = sum_chunks(n);
+    if (nc > 0) {
+        VI_COUNT_LAUNCH();
+        k_chunk_sums<<<nc, 256, 0, st>>>(partials, n, chunks);
+    }
     VI_COUNT_LAUNCH();
-    k_sum_partials<<<1, 256, 0, st>>>(partials, n, out);
+    k_sum_chunks<<<1, 256, 0, st>>>(chunks, nc, out);
 }
 
-// One block per segment [starts[i], starts[i+1]) of vals.
-__global__ void k_segment_sums(const float *__restrict__ vals, const int *__restrict__ starts, int nseg,
+// Batch form: segment i of vals is [starts[i], starts[i+1]); its chunks are
+// chunks[cprefix[i] .. cprefix[i+1]).
+__global__ void k_chunk_sums_batch(const float *__restrict__ vals, const int *__restrict__ starts,
+                                   const int *__restrict__ cprefix, int nseg, double *__restrict__ chunks)
+{
+    const int b = blockIdx.x;
+    const int seg = find_segment(cprefix, nseg, b);
+    const int lo = starts[seg] + (b - cprefix[seg]) * SUM_CHUNK;
+    const double r = block_sum_range(vals + lo, min(SUM_CHUNK, starts[seg + 1] - lo));
+    if (threadIdx.x == 0)
+        chunks[b] = r;
+}
+
+__global__ void k_segment_sums(const double *__restrict__ chunks, const int *__restrict__ cprefix, int nseg,
                                double *out)
 {
     const int i = blockIdx.x;
     if (i >= nseg)
         return;
-    const double r = block_sum_range(vals + starts[i], starts[i + 1] - starts[i]);
+    const double r = block_sum_range(chunks + cprefix[i], cprefix[i + 1] - cprefix[i]);
     if (threadIdx.x == 0)
         out[i] = r;
 }
 
-void launch_segment_sums(const float *vals, const int *starts, int nseg, double *out, cudaStream_t st)
+void launch_segment_sums(const float *vals, const int *starts, const int *cprefix, int nseg, int total_chunks,
+                         double *chunks, double *out, cudaStream_t st)
 {
     if (nseg <= 0)
         return;
+    if (total_chunks > 0) {
+        VI_COUNT_LAUNCH();
+        k_chunk_sums_batch<<<total_chunks, 256, 0, st>>>(vals, starts, cprefix, nseg, chunks);
+    }
     VI_COUNT_LAUNCH();
-    k_segment_sums<<<nseg, 256, 0, st>>>(vals, starts, nseg, out);
+    k_segment_sums<<<nseg, 256, 0, st>>>(chunks, cprefix, nseg, out);
 }
 
 // Eq. 6: the occluded voxel p copies u(p + phi(q*)), q* = argmin d2(q) over
