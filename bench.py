@@ -46,12 +46,12 @@ BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
 BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the FP16 copy
 
 # DRAM bytes (read + write) per launch of the PatchMatch step kernel, averaged
-# over the 330 step launches of one inpainting of the default workload with
-# FP32 storage, and the source voxels those launches gathered per launch, from
-# one ncu capture (profiles/k_ann_step_layered_320x240x60.md). Applies to that
-# workload and storage only; set to None when the kernel changes.
-NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
-                    "bytes": 9.016e6, "gathered_voxels": 6499884}
+# over the step launches of one inpainting of the default workload with FP32
+# storage, and the source voxels those launches gathered per launch, from one
+# ncu capture (profiles/k_ann_step_layered_320x240x60.md), as a dict with
+# keys workload, storage, bytes, gathered_voxels. Applies to that workload and
+# storage only; None while the kernel has changed since the capture.
+NCU_STEP_TRAFFIC = None
 
 
 def combine_ranks(values, dist=None, device="cpu"):

@@ -70,13 +70,26 @@ inline int device_sms()
     return sms;
 }
 
-// Grid of a persistent batch launch: one wave of 256-thread blocks, or fewer
-// when the work is smaller.
-inline int persistent_grid(long long threads)
+// Grid of a persistent batch launch: one wave of 256-thread blocks
+// (blocks_per_sm resident on every SM), or fewer when the work is smaller.
+inline int persistent_grid(long long threads, int blocks_per_sm = 8)
 {
-    const long long cap = (long long)device_sms() * 8;   // 8 blocks of 256 threads per SM
+    const long long cap = (long long)device_sms() * blocks_per_sm;
     const long long need = (threads + 255) / 256;
     return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+// Resident blocks per SM the step kernels are compiled for: the register
+// budget per thread is 65536 / (256 * blocks). The step is a chain of
+// dependent gathers that hit L1/L2, so loads in flight per thread matter more
+// than warps: measured on the 320x240x60 workload (ms per inpainting, summed
+// step launches; 4 / 3 / 2 blocks = 64 / 80 / 128 registers): G = 1
+// 16.3 / 16.5 / 15.0, G = 2 5.5 / 4.6 / 4.2, G = 8 2.9 / 2.8 / 3.4, onion
+// peel 1.4 / 1.3 / 1.3.
+template <int G, bool PARTIAL>
+constexpr int step_min_blocks()
+{
+    return (G == 8 && !PARTIAL) ? 3 : 2;
 }
 
 // Lanes per target: the smallest G in {1, 2, 4, 8} that gives the level at
@@ -224,7 +237,7 @@ __device__ __forceinline__ void flush_counts(unsigned long long *ev, unsigned lo
 }
 
 template <bool C5, int G, bool PARTIAL, bool F16>
-__global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
+__global__ void __launch_bounds__(256, step_min_blocks<G, PARTIAL>()) k_ann_step(const AnnArgs a)
 {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = gt / G;
@@ -242,9 +255,9 @@ __global__ void __launch_bounds__(256) k_ann_step(const AnnArgs a)
 // the grid at the resident size whatever the batch holds. ctr: evaluations,
 // FP32 voxels, FP16 voxels, screened, passed.
 template <bool C5, int G, bool F16>
-__global__ void __launch_bounds__(256) k_ann_step_batch(const BatchClip *__restrict__ clips,
-                                                        const int *__restrict__ prefix, int n, int k,
-                                                        unsigned long long *ctr)
+__global__ void __launch_bounds__(256, step_min_blocks<G, false>())
+    k_ann_step_batch(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, int k,
+                     unsigned long long *ctr)
 {
     const int total = __ldg(prefix + n);
     const int sub = (blockIdx.x * blockDim.x + threadIdx.x) & (G - 1);
@@ -292,8 +305,8 @@ template <bool C5, int G, bool F16>
 void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, int total, int k,
                              unsigned long long *ctr, cudaStream_t st)
 {
-    k_ann_step_batch<C5, G, F16><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, k,
-                                                                                       ctr);
+    k_ann_step_batch<C5, G, F16><<<persistent_grid((long long)total * G, step_min_blocks<G, false>()), 256, 0,
+                                   st>>>(clips, tprefix, n, k, ctr);
 }
 
 template <bool F16>
