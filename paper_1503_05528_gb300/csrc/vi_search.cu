@@ -2,19 +2,134 @@
 // the FP32-storage step kernels (vi_ann.cuh), the distance rescoring of the
 // current shifts, the shift-map initialisation and the level transition of
 // Sec. 3.6.
+#include <cmath>
+#include <map>
+#include <mutex>
+
 #include "vi_ann.cuh"
 
 namespace vi {
+
+// ---------------------------------------------------------------------------
+// Autotuning of the lanes per target. G never changes a result (group_d2 adds
+// the slice sums in the same order for every G), so the first launch of a
+// kernel family for a given target count is run with every G in {1, 2, 4, 8},
+// each writing the same outputs, with its counters pointed at a scratch array:
+// one untimed round (module loading, caches) and one timed with events. The
+// fastest G is kept for that (device, family, C, storage, target-count bucket
+// of a quarter octave); the launch that counts then runs with it. The choice
+// depends on the GPU's residency and wave quantisation, which pick_group's
+// rule only approximates.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum TuneFamily : uint32_t { TUNE_STEP = 0, TUNE_STEP_BATCH = 1, TUNE_RESCORE = 2, TUNE_RESCORE_BATCH = 3 };
+
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_tuned;
+unsigned long long *g_tune_scratch[64] = {nullptr};
+
+uint64_t tune_key(TuneFamily fam, bool c5, bool f16, long long n)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int bucket = n > 0 ? (int)std::floor(4.0 * std::log2((double)n)) : 0;
+    return ((uint64_t)(uint32_t)dev << 40) | ((uint64_t)fam << 32) | ((uint64_t)(c5 ? 1 : 0) << 31) |
+           ((uint64_t)(f16 ? 1 : 0) << 30) | (uint64_t)(uint32_t)bucket;
+}
+
+// Scratch counters (8) of the current device, allocated once per process.
+unsigned long long *tune_scratch()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    if (!g_tune_scratch[dev]) {
+        if (cudaMalloc((void **)&g_tune_scratch[dev], 8 * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            g_tune_scratch[dev] = nullptr;
+        }
+    }
+    return g_tune_scratch[dev];
+}
+
+// The tuned G for key, tuning it first when unknown: launch(G, scratch)
+// issues one launch with lanes G and counters at scratch. Returns 0 when the
+// tuning could not run (the caller then uses pick_group).
+template <typename Launch>
+int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end())
+        return it->second;
+    unsigned long long *scratch = tune_scratch();
+    if (!scratch)
+        return 0;
+    static const int Gs[4] = {1, 2, 4, 8};
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j)
+                cudaEventDestroy(ev[j]);
+            cudaGetLastError();
+            return 0;
+        }
+    for (int i = 0; i < 4; ++i)
+        launch(Gs[i], scratch);
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < 4; ++i) {
+        launch(Gs[i], scratch);
+        cudaEventRecord(ev[i + 1], st);
+    }
+    int best = 0;
+    if (cudaEventSynchronize(ev[4]) == cudaSuccess) {
+        float best_ms = 0.0f;
+        for (int i = 0; i < 4; ++i) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess && (best == 0 || ms < best_ms)) {
+                best = Gs[i];
+                best_ms = ms;
+            }
+        }
+    }
+    for (int i = 0; i < 5; ++i)
+        cudaEventDestroy(ev[i]);
+    if (best)
+        g_tuned[key] = best;
+    return best;
+}
+
+}  // namespace
 
 void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
 {
     if (a.nT <= 0)
         return;
     VI_COUNT_LAUNCH();
-    if (a.L.h4 && !a.excl)
-        launch_ann_step_f16(a, c5, st);
-    else
-        launch_ann_step_impl<false>(a, c5, st);
+    const bool f16 = a.L.h4 && !a.excl;
+    auto run = [&](const AnnArgs &b) {
+        if (f16)
+            launch_ann_step_f16(b, c5, st);
+        else
+            launch_ann_step_impl<false>(b, c5, st);
+    };
+    if (a.lanes > 0 || a.excl) {
+        run(a);
+        return;
+    }
+    AnnArgs b = a;
+    b.lanes = tuned_lanes(tune_key(TUNE_STEP, c5, f16, a.nT), st, [&](int G, unsigned long long *scr) {
+        AnnArgs t = a;
+        t.lanes = G;
+        t.evals = scr;
+        t.gathered = scr + 1;
+        t.screen = scr + 2;
+        VI_COUNT_LAUNCH();
+        run(t);
+    });
+    run(b);
 }
 
 void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
@@ -23,10 +138,19 @@ void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, in
     if (total_targets <= 0 || n <= 0)
         return;
     VI_COUNT_LAUNCH();
-    if (f16)
-        launch_ann_step_batch_f16(clips, tprefix, n, total_targets, k, c5, ctr, lanes, st);
-    else
-        launch_ann_step_batch_impl<false>(clips, tprefix, n, total_targets, k, c5, ctr, lanes, st);
+    auto run = [&](int G, unsigned long long *c) {
+        if (f16)
+            launch_ann_step_batch_f16(clips, tprefix, n, total_targets, k, c5, c, G, st);
+        else
+            launch_ann_step_batch_impl<false>(clips, tprefix, n, total_targets, k, c5, c, G, st);
+    };
+    if (lanes <= 0)
+        lanes = tuned_lanes(tune_key(TUNE_STEP_BATCH, c5, f16, total_targets), st,
+                            [&](int G, unsigned long long *scr) {
+                                VI_COUNT_LAUNCH();
+                                run(G, scr);
+                            });
+    run(lanes, ctr);
 }
 
 // Distances of the current shifts (buffer 0) for every target of a batch.
@@ -67,12 +191,9 @@ static void launch_rescore_batch_g(const BatchClip *clips, const int *tprefix, i
     k_rescore_batch<C5, G><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, evals);
 }
 
-void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
-                          unsigned long long *evals, int lanes, cudaStream_t st)
+static void rescore_batch_g(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
+                            unsigned long long *evals, int lanes, cudaStream_t st)
 {
-    if (total_targets <= 0 || n <= 0)
-        return;
-    VI_COUNT_LAUNCH();
     switch ((lanes > 0 ? lanes : pick_group(total_targets)) * 2 + (c5 ? 1 : 0)) {
     case 2: launch_rescore_batch_g<false, 1>(clips, tprefix, n, total_targets, evals, st); break;
     case 3: launch_rescore_batch_g<true, 1>(clips, tprefix, n, total_targets, evals, st); break;
@@ -83,6 +204,21 @@ void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int
     case 16: launch_rescore_batch_g<false, 8>(clips, tprefix, n, total_targets, evals, st); break;
     default: launch_rescore_batch_g<true, 8>(clips, tprefix, n, total_targets, evals, st); break;
     }
+}
+
+void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
+                          unsigned long long *evals, int lanes, cudaStream_t st)
+{
+    if (total_targets <= 0 || n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    if (lanes <= 0)
+        lanes = tuned_lanes(tune_key(TUNE_RESCORE_BATCH, c5, false, total_targets), st,
+                            [&](int G, unsigned long long *scr) {
+                                VI_COUNT_LAUNCH();
+                                rescore_batch_g(clips, tprefix, n, total_targets, c5, scr, G, st);
+                            });
+    rescore_batch_g(clips, tprefix, n, total_targets, c5, evals, lanes, st);
 }
 
 template <bool C5, int G, bool PARTIAL>
@@ -120,6 +256,22 @@ static void launch_rescore_g(LevelView L, const int *targets, int nT, const Shif
                                                                                   d_out, excl, evals);
 }
 
+static void rescore_g(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out, bool c5,
+                      unsigned long long *evals, cudaStream_t st, int lanes)
+{
+    const uint8_t *excl = nullptr;
+    switch ((lanes > 0 ? lanes : pick_group(nT)) * 2 + (c5 ? 1 : 0)) {
+    case 2: launch_rescore_g<false, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 3: launch_rescore_g<true, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 4: launch_rescore_g<false, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 5: launch_rescore_g<true, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 8: launch_rescore_g<false, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 9: launch_rescore_g<true, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    case 16: launch_rescore_g<false, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    default: launch_rescore_g<true, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
+    }
+}
+
 void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, float *d_out,
                     const uint8_t *excl, bool c5, unsigned long long *evals, cudaStream_t st, int lanes)
 {
@@ -133,16 +285,14 @@ void launch_rescore(LevelView L, const int *targets, int nT, const Shift *phi, f
             launch_rescore_g<false, 8, true>(L, targets, nT, phi, d_out, excl, evals, st);
         return;
     }
-    switch ((lanes > 0 ? lanes : pick_group(nT)) * 2 + (c5 ? 1 : 0)) {
-    case 2: launch_rescore_g<false, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 3: launch_rescore_g<true, 1, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 4: launch_rescore_g<false, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 5: launch_rescore_g<true, 2, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 8: launch_rescore_g<false, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 9: launch_rescore_g<true, 4, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    case 16: launch_rescore_g<false, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    default: launch_rescore_g<true, 8, false>(L, targets, nT, phi, d_out, excl, evals, st); break;
-    }
+    // k_rescore reads only the shifts and the channels, so every tuning launch
+    // writes the same distances
+    if (lanes <= 0)
+        lanes = tuned_lanes(tune_key(TUNE_RESCORE, c5, false, nT), st, [&](int G, unsigned long long *scr) {
+            VI_COUNT_LAUNCH();
+            rescore_g(L, targets, nT, phi, d_out, c5, scr, st, G);
+        });
+    rescore_g(L, targets, nT, phi, d_out, c5, evals, st, lanes);
 }
 
 __global__ void k_copy_targets(const int *__restrict__ targets, int nT, const Shift *__restrict__ ps,

@@ -30,13 +30,15 @@ def _clip(spec):
     return synth.layered_clip(W, H, T, 2, (10, 20), frac, L, seed, name=f"c{seed}")
 
 
-def _alone(clip, seed, tag):
+def _alone(clip, seed, tag, with_evals=False):
     with vi.Context(levels=clip.levels, seed=seed, clip=tag) as ctx:
         ctx.upload(clip.rgb, clip.mask)
         ctx.run()
         out = ctx.fetch_result()
         phi, _ = ctx.get_nnf(0)
         st = ctx.stats()
+    if with_evals:
+        return out, phi, st["outer"][:clip.levels], st["evals"]
     return out, phi, st["outer"][:clip.levels]
 
 
@@ -45,14 +47,18 @@ def test_batch_equals_alone():
     with vi.Batch() as b:
         ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=100 + i, clip=i) for i, c in enumerate(clips)]
         b.run()
+        alone_evals = 0
         for i, (cid, c) in enumerate(zip(ids, clips)):
             assert b.poll(cid) == (1, 0)
             got = b.fetch(cid)
-            want, _, outer = _alone(c, 100 + i, i)
+            want, _, outer, ev = _alone(c, 100 + i, i, with_evals=True)
+            alone_evals += ev
             assert (got.view(np.uint32) == want.view(np.uint32)).all(), i
             assert b.clip_stats(cid)["outer"][:c.levels] == outer
         s = b.stats()
         assert s["rounds"] >= 1 and s["evals"] > 0
+        # the batch makes exactly the evaluations the clips make alone
+        assert s["evals"] == alone_evals
 
 
 def test_continuous_batching_join_and_leave():
