@@ -547,7 +547,7 @@ def run_serve(args):
     import torch
 
     from paper_1503_05528_gb300 import vi
-    from paper_1503_05528_gb300.serve import CudaBackend, Server, poisson_arrivals, run_load
+    from paper_1503_05528_gb300.serve import CudaBackend, Server, StreamBackend, poisson_arrivals, run_load
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -566,18 +566,23 @@ def run_serve(args):
     stream = torch.cuda.current_stream()
     budget = int(args.hbm_budget_gb * (1 << 30))
     storage = 1 if args.storage == "fp16" else 0
-    backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1, storage=storage)
+    if args.serve_backend == "batch":
+        backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1, storage=storage)
+    else:
+        backend = StreamBackend(max_workers=args.slots, device=local, levels=0, use_texture=1,
+                                storage=storage)
 
-    # warm-up: a few requests back to back
+    # warm-up: every distinct clip once, alone (also settles the lane autotuner)
     warm = Server(backend, budget, max_slots=args.slots)
-    for i in range(args.warmup):
-        c = pool[i % len(pool)]
+    for i, c in enumerate(pool[:max(args.warmup, len(pool))]):
         warm.submit(c.rgb, c.mask, seed=1, clip=i)
-    while warm.step():
-        pass
+        while warm.step():
+            pass
 
-    backend.batch.profile(True)
-    s0 = backend.batch.stats()
+    batch = getattr(backend, "batch", None)
+    if batch is not None:
+        batch.profile(True)
+    s0 = batch.stats() if batch is not None else None
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -594,15 +599,20 @@ def run_serve(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    s1 = backend.batch.stats()
-    backend.batch.profile(False)
     lat = np.array([srv.done[t].latency for t in range(n)])
     failed = sum(1 for r in srv.done.values() if r.info.get("failed"))
-    evals = s1["evals"] - s0["evals"]
-    step_ms = s1["step_ms"] - s0["step_ms"]
-    gathered = s1["gathered"] - s0["gathered"]
-    gathered_h = s1["gathered_h"] - s0["gathered_h"]
-    rounds = s1["rounds"] - s0["rounds"]
+    if batch is not None:
+        s1 = batch.stats()
+        batch.profile(False)
+        evals = s1["evals"] - s0["evals"]
+        step_ms = s1["step_ms"] - s0["step_ms"]
+        gathered = s1["gathered"] - s0["gathered"]
+        gathered_h = s1["gathered_h"] - s0["gathered_h"]
+        rounds = s1["rounds"] - s0["rounds"]
+    else:
+        evals = None                 # counted below from the plain path (the same evaluations)
+        step_ms = gathered = gathered_h = 0
+        rounds = srv.rounds
     served = {t: srv.done[t].result for t in range(min(n, len(pool)))}
     backend.close()
 
@@ -627,6 +637,8 @@ def run_serve(args):
     lat1 = np.array(lat1)
     plain_wall = free
 
+    if evals is None:
+        evals = single_evals         # every request makes the evaluations it makes alone
     mx, sm = combine_ranks([wall, float(evals), float(sum(hole)), plain_wall, float(single_evals)],
                            dist, "cuda")
     if rank != 0:
@@ -645,7 +657,8 @@ def run_serve(args):
         "config": {"workload": SERVE_WORKLOAD, "requests": n, "rate_per_s": args.rate,
                    "distinct_clips": len(pool), "voxels_mean": float(np.mean(vox)),
                    "hole_voxels": int(sum(hole)), "hbm_budget_gb": args.hbm_budget_gb,
-                   "max_slots": args.slots, "levels": "rule of Sec. 3.6 per clip", "channels": 5,
+                   "max_slots": args.slots, "backend": args.serve_backend,
+                   "levels": "rule of Sec. 3.6 per clip", "channels": 5,
                    "storage": args.storage, "parallelism": f"replicas x{world}",
                    "step": "the whole arrival stream, host buffers in and out",
                    "l2": "inputs larger than L2: every request uploads and rebuilds its state"},
@@ -660,12 +673,13 @@ def run_serve(args):
                             "inpainted_voxels_per_s": sm[2] / mx[3],
                             "busy_s": float(sum(service)),
                             "note": "same arrivals, one request at a time through vi_run"},
-        "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": None,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
-                     "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None},
+        "roofline": ({"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
+                      "achieved": achieved, "peak": peak, "unit": "GB/s",
+                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                      "traffic": None,
+                      "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
+                      "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None}
+                     if args.serve_backend == "batch" else None),
         "e2e": {"value": sm[1] / mx[0], "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v * 13 for v in vox)),
                 "d2h_bytes_per_step": int(sum(v * 12 for v in vox))},
@@ -691,7 +705,9 @@ def main():
     ap.add_argument("--rate", type=float, default=4.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0, help="serving: admission budget")
-    ap.add_argument("--slots", type=int, default=32, help="serving: most requests in the batch")
+    ap.add_argument("--slots", type=int, default=32, help="serving: most requests admitted at once")
+    ap.add_argument("--serve-backend", default="streams", choices=["streams", "batch"],
+                    help="serving: one stream per request by size priority, or one shared batch")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
     ap.add_argument("--lanes", type=int, default=0,

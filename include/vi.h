@@ -84,6 +84,10 @@ typedef struct {
     int lanes_per_target; /* GPU lanes sharing one target in the search kernels:
                              0 = chosen per level from its size, or 1, 2, 4, 8;
                              never changes a result, only the speed */
+    int stream_priority; /* priority of the stream a context creates for itself
+                            (vi_ctx_create with cuda_stream NULL): 0 default,
+                            lower = scheduled first; clamped to the device's
+                            range. Ignored when the caller passes a stream. */
 } vi_config;
 
 /* Per-context counters. evals, step_*: since vi_ctx_create; outer and

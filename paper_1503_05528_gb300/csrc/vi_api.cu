@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -57,28 +58,54 @@ vi_status fail(vi_ctx *ctx, vi_status st, const std::string &msg)
             return s_;                                                                            \
     } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// context's stream, from the device's default pool): allocating and freeing
+// never synchronises the device, so contexts on other streams keep running
+// while one is created, re-uploaded or destroyed.
 template <typename P>
 vi_status dalloc(vi_ctx *ctx, P **ptr, size_t bytes)
 {
     *ptr = nullptr;
     if (bytes == 0)
         bytes = 16;
-    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    cudaError_t e = cudaMallocAsync((void **)ptr, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
         return fail(ctx, e == cudaErrorMemoryAllocation ? VI_ERR_OOM : VI_ERR_CUDA,
-                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+                    std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
     return VI_OK;
 }
 
 template <typename P>
-void dfree(P *&ptr)
+void dfree(vi_ctx *ctx, P *&ptr)
 {
     if (ptr)
-        cudaFree((void *)ptr);
+        cudaFreeAsync((void *)ptr, ctx->stream);
     ptr = nullptr;
+}
+
+// The default pool of each device keeps freed memory for the next
+// allocation instead of returning it at every synchronisation (set once per
+// device and process).
+void keep_pool_memory()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev])
+        return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
 }
 
 void free_state(vi_ctx *ctx)
@@ -86,35 +113,35 @@ void free_state(vi_ctx *ctx)
     if (ctx->stream)
         cudaStreamSynchronize(ctx->stream);
     for (Level &l : ctx->lv) {
-        dfree(l.x4);
-        dfree(l.x1);
-        dfree(l.code);
-        dfree(l.h4);
-        dfree(l.hmax);
-        dfree(l.phi[0]);
-        dfree(l.phi[1]);
-        dfree(l.d2[0]);
-        dfree(l.d2[1]);
-        dfree(l.targets);
-        dfree(l.holes);
-        dfree(l.sources);
+        dfree(ctx, l.x4);
+        dfree(ctx, l.x1);
+        dfree(ctx, l.code);
+        dfree(ctx, l.h4);
+        dfree(ctx, l.hmax);
+        dfree(ctx, l.phi[0]);
+        dfree(ctx, l.phi[1]);
+        dfree(ctx, l.d2[0]);
+        dfree(ctx, l.d2[1]);
+        dfree(ctx, l.targets);
+        dfree(ctx, l.holes);
+        dfree(ctx, l.sources);
     }
     ctx->lv.clear();
-    dfree(ctx->rgb);
-    dfree(ctx->mask);
-    dfree(ctx->out_rgb);
-    dfree(ctx->T0);
-    dfree(ctx->tmpA);
-    dfree(ctx->tmpB);
-    dfree(ctx->block_counts);
-    dfree(ctx->partials);
-    dfree(ctx->partials2);
-    dfree(ctx->chunks);
-    dfree(ctx->hp);
-    dfree(ctx->layer);
-    dfree(ctx->ltgt);
-    dfree(ctx->layer_list);
-    dfree(ctx->ltgt_list);
+    dfree(ctx, ctx->rgb);
+    dfree(ctx, ctx->mask);
+    dfree(ctx, ctx->out_rgb);
+    dfree(ctx, ctx->T0);
+    dfree(ctx, ctx->tmpA);
+    dfree(ctx, ctx->tmpB);
+    dfree(ctx, ctx->block_counts);
+    dfree(ctx, ctx->partials);
+    dfree(ctx, ctx->partials2);
+    dfree(ctx, ctx->chunks);
+    dfree(ctx, ctx->hp);
+    dfree(ctx, ctx->layer);
+    dfree(ctx, ctx->ltgt);
+    dfree(ctx, ctx->layer_list);
+    dfree(ctx, ctx->ltgt_list);
     ctx->partials_cap = ctx->partials2_cap = ctx->chunks_cap = 0;
     ctx->uploaded = ctx->built = false;
 }
@@ -145,7 +172,7 @@ vi_status ensure_partials(vi_ctx *ctx, int n_blocks)
 {
     if (n_blocks <= ctx->partials_cap)
         return VI_OK;
-    dfree(ctx->partials);
+    dfree(ctx, ctx->partials);
     TRY(dalloc(ctx, &ctx->partials, sizeof(float) * (size_t)n_blocks));
     ctx->partials_cap = n_blocks;
     return VI_OK;
@@ -155,7 +182,7 @@ vi_status ensure_partials2(vi_ctx *ctx, int n_blocks)
 {
     if (n_blocks <= ctx->partials2_cap)
         return VI_OK;
-    dfree(ctx->partials2);
+    dfree(ctx, ctx->partials2);
     TRY(dalloc(ctx, &ctx->partials2, 2 * sizeof(double) * (size_t)n_blocks));
     ctx->partials2_cap = n_blocks;
     return VI_OK;
@@ -250,7 +277,7 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
     if (change_dev) {
         const int nc = std::max(sum_chunks(l.nH), 1);
         if (nc > ctx->chunks_cap) {
-            dfree(ctx->chunks);
+            dfree(ctx, ctx->chunks);
             ctx->chunks_cap = 0;
             TRY(dalloc(ctx, &ctx->chunks, sizeof(double) * (size_t)nc));
             ctx->chunks_cap = nc;
@@ -317,6 +344,7 @@ void vi_config_default(vi_config *cfg)
     cfg->seed = 1503;
     cfg->clip = 0;
     cfg->lanes_per_target = 0;
+    cfg->stream_priority = 0;
 }
 
 vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
@@ -345,17 +373,20 @@ vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
     if (cuda_stream) {
         ctx->stream = (cudaStream_t)cuda_stream;
     } else {
-        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        const int prio = std::min(least, std::max(greatest, ctx->cfg.stream_priority));
+        if (cudaStreamCreateWithPriority(&ctx->stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
+            cudaGetLastError();
             delete ctx;
             return VI_ERR_CUDA;
         }
         ctx->own_stream = true;
     }
-    if (cudaMalloc((void **)&ctx->count_dev, 64 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void **)&ctx->scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void **)&ctx->evals_dev, 6 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost((void **)&ctx->host_scal, 8 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost((void **)&ctx->host_counts, 64 * sizeof(int)) != cudaSuccess) {
+    keep_pool_memory();
+    if (dalloc(ctx, &ctx->count_dev, 64 * sizeof(int)) != VI_OK ||
+        dalloc(ctx, &ctx->scal, 8 * sizeof(double)) != VI_OK ||
+        dalloc(ctx, &ctx->evals_dev, 6 * sizeof(unsigned long long)) != VI_OK) {
         vi_ctx_destroy(ctx);
         return VI_ERR_OOM;
     }
@@ -369,13 +400,9 @@ void vi_ctx_destroy(vi_ctx *ctx)
     if (!ctx)
         return;
     free_state(ctx);
-    dfree(ctx->count_dev);
-    dfree(ctx->scal);
-    dfree(ctx->evals_dev);
-    if (ctx->host_scal)
-        cudaFreeHost(ctx->host_scal);
-    if (ctx->host_counts)
-        cudaFreeHost(ctx->host_counts);
+    dfree(ctx, ctx->count_dev);
+    dfree(ctx, ctx->scal);
+    dfree(ctx, ctx->evals_dev);
     for (auto &e : ctx->events) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -436,7 +463,8 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
     if (L <= 0) {
         if (ptr_is_device) {
             std::vector<uint8_t> hm(V0);
-            CK(cudaMemcpy(hm.data(), mask, V0, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpyAsync(hm.data(), mask, V0, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
             L = host_auto_levels(hm.data(), W, H, T);
         } else {
             L = host_auto_levels(mask, W, H, T);
@@ -514,9 +542,9 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
             launch_box_mean(g, ctx->tmpA, W, H, T, 1 << (ctx->L - 1), sum, cnt, ctx->T0, st);
             cudaStreamSynchronize(st);
         }
-        dfree(g);
-        dfree(sum);
-        dfree(cnt);
+        dfree(ctx, g);
+        dfree(ctx, sum);
+        dfree(ctx, cnt);
         TRY(r);
         CK_LAUNCH();
     }
@@ -549,9 +577,9 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
     int max_list = 1, max_t = 1;
     for (int l = 0; l < ctx->L; ++l) {
         Level &lv = ctx->lv[l];
-        dfree(lv.targets);
-        dfree(lv.holes);
-        dfree(lv.sources);
+        dfree(ctx, lv.targets);
+        dfree(ctx, lv.holes);
+        dfree(ctx, lv.sources);
         lv.nT = ctx->host_counts[3 * l];
         lv.nH = ctx->host_counts[3 * l + 1];
         lv.nS = ctx->host_counts[3 * l + 2];
@@ -832,7 +860,7 @@ vi_status vi_get_channels(vi_ctx *ctx, int level, float *out, int ptr_is_device)
     cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(tmp);
+    dfree(ctx, tmp);
     if (e != cudaSuccess)
         return fail(ctx, VI_ERR_CUDA, std::string("vi_get_channels: ") + cudaGetErrorString(e));
     return VI_OK;
@@ -861,7 +889,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
         launch_shadow_all(l.view(), ctx->stream);
         e = cudaStreamSynchronize(ctx->stream);
     }
-    cudaFree(tmp);
+    dfree(ctx, tmp);
     if (e != cudaSuccess)
         return fail(ctx, VI_ERR_CUDA, std::string("vi_set_channels: ") + cudaGetErrorString(e));
     return VI_OK;
@@ -949,7 +977,7 @@ vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n
     TRY(dalloc(ctx, &dp, sizeof(int) * 6 * (size_t)n));
     vi_status r = dalloc(ctx, &dout, sizeof(float) * (size_t)n);
     if (r != VI_OK) {
-        cudaFree(dp);
+        dfree(ctx, dp);
         return r;
     }
     cudaError_t e = cudaMemcpyAsync(dp, pairs_host, sizeof(int) * 6 * (size_t)n, cudaMemcpyHostToDevice,
@@ -962,8 +990,8 @@ vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n
         e = cudaMemcpyAsync(out_host, dout, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(dp);
-    cudaFree(dout);
+    dfree(ctx, dp);
+    dfree(ctx, dout);
     if (e != cudaSuccess)
         return fail(ctx, VI_ERR_CUDA, std::string("vi_patch_dist: ") + cudaGetErrorString(e));
     return VI_OK;

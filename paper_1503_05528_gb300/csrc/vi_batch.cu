@@ -98,38 +98,38 @@ vi_status ensure_capacity(vi_batch *b, int n, long long holes, int chunks = 0)
 {
     if (n > b->cap) {
         int cap = std::max(n, std::max(16, 2 * b->cap));
-        if (b->d_clips) cudaFree(b->d_clips);
+        if (b->d_clips) cudaFreeAsync(b->d_clips, b->stream);
         if (b->h_clips) cudaFreeHost(b->h_clips);
-        if (b->d_prefix) cudaFree(b->d_prefix);
+        if (b->d_prefix) cudaFreeAsync(b->d_prefix, b->stream);
         if (b->h_prefix) cudaFreeHost(b->h_prefix);
-        if (b->d_e) cudaFree(b->d_e);
+        if (b->d_e) cudaFreeAsync(b->d_e, b->stream);
         if (b->h_e) cudaFreeHost(b->h_e);
         b->d_clips = b->h_clips = nullptr;
         b->d_prefix = b->h_prefix = nullptr;
         b->d_e = b->h_e = nullptr;
         b->cap = 0;
-        BCK(cudaMalloc((void **)&b->d_clips, sizeof(BatchClip) * cap));
+        BCK(cudaMallocAsync((void **)&b->d_clips, sizeof(BatchClip) * cap, b->stream));
         BCK(cudaMallocHost((void **)&b->h_clips, sizeof(BatchClip) * cap));
-        BCK(cudaMalloc((void **)&b->d_prefix, sizeof(int) * 3 * (cap + 1)));
+        BCK(cudaMallocAsync((void **)&b->d_prefix, sizeof(int) * 3 * (cap + 1), b->stream));
         BCK(cudaMallocHost((void **)&b->h_prefix, sizeof(int) * 3 * (cap + 1)));
-        BCK(cudaMalloc((void **)&b->d_e, sizeof(double) * cap));
+        BCK(cudaMallocAsync((void **)&b->d_e, sizeof(double) * cap, b->stream));
         BCK(cudaMallocHost((void **)&b->h_e, sizeof(double) * cap));
         b->cap = cap;
     }
     if (holes > b->change_cap) {
         long long cap = std::max(holes, 2 * b->change_cap);
-        if (b->d_change) cudaFree(b->d_change);
+        if (b->d_change) cudaFreeAsync(b->d_change, b->stream);
         b->d_change = nullptr;
         b->change_cap = 0;
-        BCK(cudaMalloc((void **)&b->d_change, sizeof(float) * (size_t)std::max(cap, 1ll)));
+        BCK(cudaMallocAsync((void **)&b->d_change, sizeof(float) * (size_t)std::max(cap, 1ll), b->stream));
         b->change_cap = cap;
     }
     if (chunks > b->chunks_cap) {
         const int cap = std::max(chunks, 2 * b->chunks_cap);
-        if (b->d_chunks) cudaFree(b->d_chunks);
+        if (b->d_chunks) cudaFreeAsync(b->d_chunks, b->stream);
         b->d_chunks = nullptr;
         b->chunks_cap = 0;
-        BCK(cudaMalloc((void **)&b->d_chunks, sizeof(double) * (size_t)cap));
+        BCK(cudaMallocAsync((void **)&b->d_chunks, sizeof(double) * (size_t)cap, b->stream));
         b->chunks_cap = cap;
     }
     return VI_OK;
@@ -195,7 +195,7 @@ vi_status vi_batch_create(const vi_config *cfg, void *cuda_stream, vi_batch **ou
         }
         b->own_stream = true;
     }
-    if (cudaMalloc((void **)&b->counters, 6 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&b->counters, 6 * sizeof(unsigned long long), b->stream) != cudaSuccess) {
         vi_batch_destroy(b);
         return VI_ERR_OOM;
     }
@@ -212,15 +212,15 @@ void vi_batch_destroy(vi_batch *b)
         cudaStreamSynchronize(b->stream);
     for (Entry &c : b->clips)
         vi_ctx_destroy(c.ctx);
-    if (b->d_clips) cudaFree(b->d_clips);
+    if (b->d_clips) cudaFreeAsync(b->d_clips, b->stream);
     if (b->h_clips) cudaFreeHost(b->h_clips);
-    if (b->d_prefix) cudaFree(b->d_prefix);
+    if (b->d_prefix) cudaFreeAsync(b->d_prefix, b->stream);
     if (b->h_prefix) cudaFreeHost(b->h_prefix);
-    if (b->d_e) cudaFree(b->d_e);
+    if (b->d_e) cudaFreeAsync(b->d_e, b->stream);
     if (b->h_e) cudaFreeHost(b->h_e);
-    if (b->d_change) cudaFree(b->d_change);
-    if (b->d_chunks) cudaFree(b->d_chunks);
-    if (b->counters) cudaFree(b->counters);
+    if (b->d_change) cudaFreeAsync(b->d_change, b->stream);
+    if (b->d_chunks) cudaFreeAsync(b->d_chunks, b->stream);
+    if (b->counters) cudaFreeAsync(b->counters, b->stream);
     for (auto &e : b->events) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);

@@ -82,8 +82,8 @@ struct vi_ctx {
     double *chunks = nullptr;      // chunk sums of the change array (sum_chunks of the largest hole list)
     int chunks_cap = 0;
     double *scal = nullptr;        // device scalars
-    double *host_scal = nullptr;   // pinned
-    int *host_counts = nullptr;    // pinned, 64 ints
+    double host_scal[8] = {0};     // host copies of scal (read after a stream synchronisation)
+    int host_counts[64] = {0};     // host copies of count_dev
     // [0] rescore evals, [1] step evals, [2] FP32 voxels gathered by the step,
     // [3] FP16 voxels gathered, [4] candidates screened, [5] screened and passed
     unsigned long long *evals_dev = nullptr;

@@ -1,17 +1,24 @@
-"""Continuous-batching inpainting server on one GPU.
+"""Inpainting server on one GPU: admission by an HBM budget, requests
+running concurrently.
 
-Requests (a clip and its occlusion mask) queue in arrival order. Between
-batch rounds the server admits queued requests while their device footprint
-(``vi_footprint_bytes``) fits the HBM budget and a slot is free; an admitted
-request is prepared (pyramid, initialisation, onion peel) and joins the
-running batch, so its iterations share launches with the requests already on
-the GPU. A finished request is fetched and removed at once, which frees its
-memory and slot for the next one. Every job's result is bit-identical to
-running it alone (``vi_batch_*`` guarantees it).
+Requests (a clip and its occlusion mask) queue in arrival order. The server
+admits queued requests while their device footprint (``vi_footprint_bytes``)
+fits the HBM budget and a slot is free, and hands a finished request back at
+once, which frees its memory and slot for the next one. Two backends run the
+admitted requests:
 
-The scheduling logic is plain Python over a small backend interface
+- ``CudaBackend``: continuous batching (``vi_batch_*``). An admitted request
+  joins the running batch, and every round runs one search/reconstruction
+  iteration of every request in shared launches.
+- ``StreamBackend``: every request runs alone (``vi_run``) in a worker thread
+  on a stream of its own, smaller requests on higher-priority streams; the
+  GPU interleaves the streams, so a small request is not held back to the pace
+  of a large one.
+
+Either way every job's result is bit-identical to running it alone. The
+scheduling logic is plain Python over a small backend interface
 (add / step / poll / fetch / remove / footprint), so it runs unchanged over
-the CUDA batch or over a stand-in in tests.
+either backend or over a stand-in in tests.
 """
 from __future__ import annotations
 
@@ -42,8 +49,15 @@ class Request:
         return None if self.finished is None else self.finished - self.arrival
 
 
+def _footprint(vi, defaults, req):
+    import ctypes
+    T, H, W = req.mask.shape[:3]
+    cfg = vi.default_config(**{**defaults, **req.job})
+    return int(vi.load().vi_footprint_bytes(ctypes.byref(cfg), W, H, T, int(req.hole_voxels)))
+
+
 class CudaBackend:
-    """The vi_batch of the CUDA library."""
+    """The vi_batch of the CUDA library (continuous batching)."""
 
     def __init__(self, stream=None, **cfg):
         from . import vi
@@ -52,10 +66,7 @@ class CudaBackend:
         self.cfg = vi.default_config(**cfg)
 
     def footprint(self, req):
-        import ctypes
-        T, H, W = req.mask.shape[:3]
-        cfg = self.vi.default_config(**{**self.batch.defaults, **req.job})
-        return int(self.vi.load().vi_footprint_bytes(ctypes.byref(cfg), W, H, T, int(req.hole_voxels)))
+        return _footprint(self.vi, self.batch.defaults, req)
 
     def add(self, req):
         return self.batch.add(req.rgb, req.mask, **req.job)
@@ -74,6 +85,73 @@ class CudaBackend:
 
     def close(self):
         self.batch.close()
+
+
+class StreamBackend:
+    """Every admitted request runs alone through vi_run in a worker thread, on
+    a stream the context creates with a priority by size: requests under
+    2M / 8M / 32M voxels get the three highest priorities, larger ones the
+    default. Stream-ordered device memory in the library keeps one request's
+    allocation and release from stalling the others."""
+
+    SIZE_CUTS = (2_000_000, 8_000_000, 32_000_000)
+
+    def __init__(self, max_workers=8, device=None, **cfg):
+        from concurrent.futures import ThreadPoolExecutor
+
+        from . import vi
+        self.vi = vi
+        self.cfg = dict(cfg)
+        init = None
+        if device is not None:
+            def init():
+                import torch
+                torch.cuda.set_device(device)
+        self.pool = ThreadPoolExecutor(max_workers, initializer=init)
+        self.jobs = {}
+        self.next_id = 0
+
+    def footprint(self, req):
+        return _footprint(self.vi, self.cfg, req)
+
+    @classmethod
+    def priority(cls, voxels):
+        import bisect
+        return bisect.bisect_right(cls.SIZE_CUTS, voxels) - len(cls.SIZE_CUTS)
+
+    def _run(self, rgb, mask, job):
+        with self.vi.Context(**job) as ctx:
+            ctx.upload(rgb, mask)
+            ctx.run()
+            return ctx.fetch_result()
+
+    def add(self, req):
+        voxels = int(np.prod(req.mask.shape[:3]))
+        job = {**self.cfg, **req.job, "stream_priority": self.priority(voxels)}
+        cid = self.next_id
+        self.next_id += 1
+        self.jobs[cid] = self.pool.submit(self._run, req.rgb, req.mask, job)
+        return cid
+
+    def step(self):
+        from concurrent.futures import FIRST_COMPLETED, wait
+        if self.jobs:
+            wait(list(self.jobs.values()), timeout=0.002, return_when=FIRST_COMPLETED)
+
+    def poll(self, cid):
+        f = self.jobs[cid]
+        if not f.done():
+            return 0
+        return -1 if f.exception() is not None else 1
+
+    def fetch(self, cid):
+        return self.jobs[cid].result()
+
+    def remove(self, cid):
+        self.jobs.pop(cid, None)
+
+    def close(self):
+        self.pool.shutdown(wait=True)
 
 
 class Server:

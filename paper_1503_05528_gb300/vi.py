@@ -38,7 +38,8 @@ class ViConfig(C.Structure):
     _fields_ = [("lambda_", C.c_float), ("n_pm", C.c_int), ("rho", C.c_float),
                 ("levels", C.c_int), ("max_outer", C.c_int), ("stop", C.c_float),
                 ("weighted", C.c_int), ("use_texture", C.c_int), ("storage", C.c_int),
-                ("seed", C.c_uint64), ("clip", C.c_uint32), ("lanes_per_target", C.c_int)]
+                ("seed", C.c_uint64), ("clip", C.c_uint32), ("lanes_per_target", C.c_int),
+                ("stream_priority", C.c_int)]
 
 
 class ViStats(C.Structure):

@@ -1,13 +1,14 @@
-"""The continuous-batching server over the CUDA batch: requests that arrive
-while others iterate, under a memory budget that holds only some of them at
-once, each come back bit-identical to the same clip run alone with vi_run."""
+"""The server over both CUDA backends (the shared batch, and one
+priority stream per request): requests that arrive while others run, under
+a memory budget that holds only some of them at once, each come back
+bit-identical to the same clip run alone with vi_run."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
 from paper_1503_05528_gb300 import synth, vi  # noqa: E402
-from paper_1503_05528_gb300.serve import CudaBackend, Server  # noqa: E402
+from paper_1503_05528_gb300.serve import CudaBackend, Server, StreamBackend  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -31,9 +32,13 @@ def _alone(clip, seed, tag):
         return ctx.fetch_result()
 
 
-def test_served_equals_alone():
+@pytest.mark.parametrize("kind", ["batch", "streams"])
+def test_served_equals_alone(kind):
     clips = [synth.fast_layered_clip(W, H, T, f, seed=2100 + i) for i, (W, H, T, f) in enumerate(SIZES)]
-    backend = CudaBackend(levels=0, use_texture=1)
+    if kind == "batch":
+        backend = CudaBackend(levels=0, use_texture=1)
+    else:
+        backend = StreamBackend(max_workers=4, device=0, levels=0, use_texture=1)
     try:
         probe = Server(backend, 1 << 62)
         fps = []

@@ -4,7 +4,7 @@ first served, removal of finished and failed jobs, latency bookkeeping."""
 import numpy as np
 import pytest
 
-from paper_1503_05528_gb300.serve import Server, poisson_arrivals, run_load
+from paper_1503_05528_gb300.serve import Server, StreamBackend, poisson_arrivals, run_load
 
 
 class FakeBackend:
@@ -169,3 +169,10 @@ def test_run_load_feeds_by_arrival_time():
     assert lat.shape == (6,) and np.all(lat > 0)
     for r in srv.done.values():
         assert r.admitted >= r.arrival
+
+
+def test_stream_priority_by_size():
+    # smaller requests get higher priority (lower number); the largest get 0
+    p = [StreamBackend.priority(v) for v in (1, 1_999_999, 2_000_000, 7_999_999, 8_000_000, 31_999_999,
+                                             32_000_000, 10 ** 9)]
+    assert p == [-3, -3, -2, -2, -1, -1, 0, 0]
