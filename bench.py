@@ -51,7 +51,8 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # ncu capture (profiles/k_ann_step_layered_320x240x60.md), as a dict with
 # keys workload, storage, bytes, gathered_voxels. Applies to that workload and
 # storage only; None while the kernel has changed since the capture.
-NCU_STEP_TRAFFIC = None
+NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
+                    "bytes": 8.9997e6, "gathered_voxels": 6121580}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
@@ -126,6 +127,20 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _tune_load(args, vi):
+    """Imports a lanes-per-target table (--tune-load), e.g. the one an
+    unprofiled run saved, so that a profiled run launches the same kernels."""
+    if getattr(args, "tune_load", None):
+        with open(args.tune_load) as f:
+            vi.tune_import(f.read())
+
+
+def _tune_save(args, vi):
+    if getattr(args, "tune_save", None):
+        with open(args.tune_save, "w") as f:
+            f.write(vi.tune_export())
 
 
 def _dist():
@@ -247,6 +262,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vi.load(build_if_missing=True)
+    _tune_load(args, vi)
     clip = make_clip(rank, args.workload)
     rgb_d = torch.from_numpy(clip.rgb).cuda()
     mask_d = torch.from_numpy(clip.mask).cuda()
@@ -264,6 +280,7 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
+    _tune_save(args, vi)
     ctx.profile(True)
     s0 = ctx.stats()
     uuid = None
@@ -374,6 +391,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(clip.rgb.nbytes + clip.mask.nbytes),
                 "d2h_bytes_per_step": int(clip.rgb.nbytes)},
         "gpu_launches": launches,
+        "lanes_tuned": vi.tune_export().splitlines(),
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -414,6 +432,7 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vi.load(build_if_missing=True)
+    _tune_load(args, vi)
     clips = make_batch_clips(rank)
     dev = [(torch.from_numpy(c.rgb).cuda(), torch.from_numpy(c.mask).cuda()) for c in clips]
     outs = [torch.empty_like(r) for r, _ in dev]
@@ -433,6 +452,7 @@ def run_batch(args):
 
     for _ in range(args.warmup):
         step()
+    _tune_save(args, vi)
     b.profile(True)
     s0 = b.stats()
     uuid = None
@@ -556,6 +576,7 @@ def run_serve(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vi.load(build_if_missing=True)
+    _tune_load(args, vi)
     pool = make_serve_pool(rank, args.serve_pool)
     n = args.requests
     reqs = [(pool[i % len(pool)].rgb, pool[i % len(pool)].mask, {"seed": 7000 + i, "clip": i})
@@ -579,6 +600,7 @@ def run_serve(args):
         while warm.step():
             pass
 
+    _tune_save(args, vi)
     batch = getattr(backend, "batch", None)
     if batch is not None:
         batch.profile(True)
@@ -710,6 +732,8 @@ def main():
                     help="serving: one stream per request by size priority, or one shared batch")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
+    ap.add_argument("--tune-save", default=None, help="write the lanes autotuning table after warm-up")
+    ap.add_argument("--tune-load", default=None, help="import a lanes autotuning table before warm-up")
     ap.add_argument("--lanes", type=int, default=0,
                     help="GPU lanes per target in the search kernels (0: chosen per level)")
     args = ap.parse_args()

@@ -282,6 +282,21 @@ vi_status vi_profile(vi_ctx *ctx, int enable);
 /* The context's counters (synchronises to read event times). */
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
 
+/* Lanes-per-target autotuning (no counterpart in the paper; speed only, never
+ * a result). With lanes_per_target = 0 the first PatchMatch step or rescore
+ * launch of a kernel family for a target count (per device, channels,
+ * storage, quarter-octave bucket of the count) is run once with every lane
+ * group size in {1, 2, 4, 8}, timed, and the fastest is kept for the
+ * process. vi_tune_export writes the table as text lines
+ * "device family c5 fp16 bucket lanes" (family 0 step, 1 batch step, 2
+ * rescore, 3 batch rescore) into buf (cap bytes, NUL-terminated, truncated
+ * if short; buf may be NULL) and returns the bytes needed including the NUL.
+ * vi_tune_import adds such lines to the table (a profiler, which serialises
+ * the timing launches, can then run the choices of an unprofiled run).
+ * Errors: VI_ERR_ARG on a malformed line (nothing imported). */
+int vi_tune_export(char *buf, int cap);
+vi_status vi_tune_import(const char *text);
+
 /* ---------------------------------------------------------------------------
  * Batches: many clips, one launch per step.
  *

@@ -2,10 +2,15 @@
 // the FP32-storage step kernels (vi_ann.cuh), the distance rescoring of the
 // current shifts, the shift-map initialisation and the level transition of
 // Sec. 3.6.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 
+#include "vi.h"
 #include "vi_ann.cuh"
 
 namespace vi {
@@ -103,6 +108,65 @@ int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch)
 
 }  // namespace
 
+}  // namespace vi
+
+extern "C" {
+
+int vi_tune_export(char *buf, int cap)
+{
+    using namespace vi;
+    std::string out;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto &kv : g_tuned) {
+            const uint64_t k = kv.first;
+            char line[96];
+            std::snprintf(line, sizeof(line), "%u %u %u %u %d %d\n", (unsigned)(k >> 40),
+                          (unsigned)((k >> 32) & 0xFFu), (unsigned)((k >> 31) & 1u), (unsigned)((k >> 30) & 1u),
+                          (int)(int32_t)(uint32_t)(k & 0x3FFFFFFFu), kv.second);
+            out += line;
+        }
+    }
+    if (buf && cap > 0) {
+        const size_t n = std::min(out.size(), (size_t)cap - 1);
+        std::memcpy(buf, out.data(), n);
+        buf[n] = '\0';
+    }
+    return (int)out.size() + 1;
+}
+
+vi_status vi_tune_import(const char *text)
+{
+    using namespace vi;
+    if (!text)
+        return VI_ERR_ARG;
+    std::map<uint64_t, int> add;
+    const char *p = text;
+    while (*p) {
+        unsigned dev, fam, c5, f16;
+        int bucket, G, used = 0;
+        while (*p == '\n' || *p == ' ' || *p == '\r' || *p == '\t')
+            ++p;
+        if (!*p)
+            break;
+        if (std::sscanf(p, "%u %u %u %u %d %d%n", &dev, &fam, &c5, &f16, &bucket, &G, &used) != 6 ||
+            dev >= 64 || fam > 3 || c5 > 1 || f16 > 1 || bucket < 0 || bucket > 0x3FFFFFFF ||
+            !(G == 1 || G == 2 || G == 4 || G == 8))
+            return VI_ERR_ARG;
+        add[((uint64_t)dev << 40) | ((uint64_t)fam << 32) | ((uint64_t)c5 << 31) | ((uint64_t)f16 << 30) |
+            (uint64_t)bucket] = G;
+        p += used;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto &kv : add)
+        g_tuned[kv.first] = kv.second;
+    return VI_OK;
+}
+
+}  // extern "C"
+
+namespace vi {
+
 void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
 {
     if (a.nT <= 0)
@@ -155,7 +219,7 @@ void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, in
 
 // Distances of the current shifts (buffer 0) for every target of a batch.
 template <bool C5, int G>
-__global__ void __launch_bounds__(256) k_rescore_batch(const BatchClip *__restrict__ clips,
+__global__ void __launch_bounds__(256, step_min_blocks<G, false>()) k_rescore_batch(const BatchClip *__restrict__ clips,
                                                        const int *__restrict__ prefix, int n,
                                                        unsigned long long *evals_ctr)
 {
@@ -188,7 +252,8 @@ template <bool C5, int G>
 static void launch_rescore_batch_g(const BatchClip *clips, const int *tprefix, int n, int total,
                                    unsigned long long *evals, cudaStream_t st)
 {
-    k_rescore_batch<C5, G><<<persistent_grid((long long)total * G), 256, 0, st>>>(clips, tprefix, n, evals);
+    k_rescore_batch<C5, G><<<persistent_grid((long long)total * G, step_min_blocks<G, false>()), 256, 0, st>>>(
+        clips, tprefix, n, evals);
 }
 
 static void rescore_batch_g(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
@@ -222,7 +287,7 @@ void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int
 }
 
 template <bool C5, int G, bool PARTIAL>
-__global__ void __launch_bounds__(256) k_rescore(LevelView L, const int *__restrict__ targets, int nT,
+__global__ void __launch_bounds__(256, step_min_blocks<G, PARTIAL>()) k_rescore(LevelView L, const int *__restrict__ targets, int nT,
                                                  const Shift *__restrict__ phi, float *__restrict__ d_out,
                                                  const uint8_t *excl, unsigned long long *evals_ctr)
 {

@@ -68,17 +68,41 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
         if (n > 0) {
             float sigma2 = 0.0f;
             if (a.weighted) {
-                const unsigned rank = (unsigned)((3 * n + 3) / 4 - 1);   // 0-based nearest rank
-                unsigned X = 0;
-                for (int b = 30; b >= 0; --b) {
+                // Radix select of the value of 0-based rank r over the bit
+                // patterns (non-negative finite floats order like their bits,
+                // all below 2^31). Invariant before bit b: the answer's bits
+                // above b are those of X (its bits <= b are 0), lo = #{v < X}
+                // and hi = #{v < X + 2^(b+1)}, so lo <= r < hi. Once a single
+                // value is left in [X, X + 2^(b+1)) it is the answer, and the
+                // search stops there: about log2(n) steps for distinct values
+                // instead of 31.
+                const unsigned r = (unsigned)((3 * n + 3) / 4 - 1);   // 0-based nearest rank
+                unsigned X = 0, lo = 0, hi = (unsigned)n;
+                int b = 30;
+                for (; b >= 0 && hi - lo > 1; --b) {
                     const unsigned Tt = X | (1u << b);
                     unsigned c = 0;
 #pragma unroll
                     for (int m = 0; m < 4; ++m)
                         c += ((okm >> m) & 1u) && (__float_as_uint(dq[m]) < Tt);
                     c = __reduce_add_sync(0xffffffffu, c);
-                    if (c <= rank)
+                    if (c <= r) {
                         X = Tt;
+                        lo = c;
+                    } else {
+                        hi = c;
+                    }
+                }
+                if (hi - lo == 1) {
+                    // the one value in [X, X + 2^(b+1)): the smallest v >= X
+                    unsigned mn = 0xffffffffu;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const unsigned u = __float_as_uint(dq[m]);
+                        if (((okm >> m) & 1u) && u >= X && u < mn)
+                            mn = u;
+                    }
+                    X = __reduce_min_sync(0xffffffffu, mn);
                 }
                 sigma2 = __uint_as_float(X);
             }

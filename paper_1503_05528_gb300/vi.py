@@ -27,7 +27,7 @@ EXPORTS = [
     "vi_prepare", "vi_rescore", "vi_ann", "vi_reconstruct", "vi_iterate", "vi_next_level",
     "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
     "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
-    "vi_profile", "vi_get_stats", "vi_energy_noalloc",
+    "vi_profile", "vi_get_stats", "vi_energy_noalloc", "vi_tune_export", "vi_tune_import",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -114,6 +114,9 @@ def _declare(L):
     L.vi_profile.argtypes = [vp, i]
     L.vi_get_stats.argtypes = [vp, P(ViStats)]
     L.vi_energy_noalloc.argtypes = [vp, i, vp, vp, i, i, i, vp, vp]
+    L.vi_tune_export.argtypes = [C.c_char_p, i]
+    L.vi_tune_export.restype = i
+    L.vi_tune_import.argtypes = [C.c_char_p]
     ull = C.c_ulonglong
     L.vi_batch_create.argtypes = [P(ViConfig), vp, P(vp)]
     L.vi_batch_destroy.argtypes = [vp]
@@ -413,6 +416,21 @@ class Batch:
 
     def profile(self, enable=True):
         self._ck(self.lib.vi_batch_profile(self.h, 1 if enable else 0))
+
+
+def tune_export():
+    """The lanes-per-target autotuning table as text (see vi.h)."""
+    L = load()
+    n = L.vi_tune_export(None, 0)
+    buf = C.create_string_buffer(n)
+    L.vi_tune_export(buf, n)
+    return buf.value.decode()
+
+
+def tune_import(text):
+    st = load().vi_tune_import(text.encode())
+    if st != VI_OK:
+        raise ViError(st, "vi_tune_import: malformed line")
 
 
 def auto_levels(mask):
