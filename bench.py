@@ -270,7 +270,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     storage = 1 if args.storage == "fp16" else 0
     ctx = vi.Context(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank,
-                     stream=stream.cuda_stream, lanes_per_target=args.lanes, storage=storage)
+                     stream=stream.cuda_stream, lanes_per_target=args.lanes, storage=storage,
+                     rs_mode=1 if args.rs_mode == "multi" else 0, sub_sweeps=args.sub_sweeps)
     n_hole = int(clip.mask.sum())
 
     def step():
@@ -305,6 +306,7 @@ def run_gpu(args):
     clocks = sampler.stop()
     s1 = ctx.stats()
     ctx.profile(False)
+    energy = ctx.energy(0)          # Eq. 1 over H and over H~ at the finest level, after the run
     ms = e0.elapsed_time(e1)
     evals = s1["evals"] - s0["evals"]
     step_evals = s1["step_evals"] - s0["step_evals"]
@@ -365,12 +367,14 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "levels": clip.levels, "channels": 5, "storage": args.storage,
+                   "random_search": args.rs_mode, "sub_sweeps": args.sub_sweeps,
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
                    "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
         "inpainted_voxels_per_s": hole_tot * args.steps / (ms_max / 1e3),
         "evals_per_step": evals / args.steps,
         "outer_iterations_per_level": outer[:clip.levels],
+        "energy_level0": {"E_H": energy[0], "E_Htilde": energy[1]},
         "screening": ({"screened": screened, "passed": passed,
                        "pass_rate": passed / screened if screened else None,
                        "fp16_voxels": step_gathered_h, "fp32_voxels": step_gathered}
@@ -732,6 +736,9 @@ def main():
                     help="serving: one stream per request by size priority, or one shared batch")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
+    ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],
+                    help="random search: one radius per iteration (Eq. 3) or every radius")
+    ap.add_argument("--sub-sweeps", type=int, default=1, help="propagation sweeps per iteration")
     ap.add_argument("--tune-save", default=None, help="write the lanes autotuning table after warm-up")
     ap.add_argument("--tune-load", default=None, help="import a lanes autotuning table before warm-up")
     ap.add_argument("--lanes", type=int, default=0,

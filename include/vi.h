@@ -88,6 +88,16 @@ typedef struct {
                             (vi_ctx_create with cuda_stream NULL): 0 default,
                             lower = scheduled first; clamped to the device's
                             range. Ignored when the caller passes a stream. */
+    int rs_mode;         /* random search: 0 = Algorithm 1 / Eq. 3, one candidate
+                            per PatchMatch iteration k at radius r_max rho^k;
+                            1 = the original PatchMatch search, a candidate at
+                            every radius r_max rho^i >= 1 (i = 0, 1, ...) per
+                            k, each around the best shift so far (Sec. 3.1
+                            discusses both) */
+    int sub_sweeps;      /* propagation sweeps per PatchMatch iteration, the
+                            last one followed by the random search (1, the
+                            paper's; more spread a good shift further per
+                            parallel iteration); 1..16; batches need 1 */
 } vi_config;
 
 /* Per-context counters. evals, step_*: since vi_ctx_create; outer and

@@ -105,6 +105,9 @@ def _declare(L):
     L.vio_ann.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p, i, i, i, d,
                           u32, u32, u32, u32]
     L.vio_ann.restype = C.c_longlong
+    L.vio_ann2.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p, i, i, i, d,
+                           u32, u32, u32, u32, i, i]
+    L.vio_ann2.restype = C.c_longlong
     L.vio_bruteforce_nn.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p]
     L.vio_vote.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _u8p, _i32p, _f32p, i, i, _OptU8]
     L.vio_vote.restype = d
@@ -234,9 +237,13 @@ def upsample_nnf(phi_c, target_f, dtilde_f, key, tag_word, clip=0):
 
 
 def ann(x, target, dtilde, phi, d2, n_pm=10, schedule="JAC", rmax=None, rho=0.5,
-        key=(0, 0), tag_base=0, clip=0, excl=None):
+        key=(0, 0), tag_base=0, clip=0, excl=None, rs_mode=0, sub_sweeps=1):
     """Algorithm 1 in place on (phi, d2). Returns the number of distance
-    evaluations. ``schedule``: "SEQ" (Algorithm 1 as printed) or "JAC"."""
+    evaluations. ``schedule``: "SEQ" (Algorithm 1 as printed) or "JAC".
+    ``rs_mode`` 0: one random candidate per k at radius r_max rho^k (Eq. 3);
+    1: a candidate at every radius r_max rho^i >= 1 per k (the original
+    PatchMatch search). ``sub_sweeps``: propagation sweeps before each random
+    search."""
     x = _c(x, np.float32)
     T, H, W, Cn = x.shape
     assert phi.dtype == np.int32 and phi.flags.c_contiguous
@@ -244,11 +251,13 @@ def ann(x, target, dtilde, phi, d2, n_pm=10, schedule="JAC", rmax=None, rho=0.5,
     if rmax is None:
         rmax = max(W, H, T)
     sched = {"SEQ": 0, "JAC": 1}[schedule]
-    return lib().vio_ann(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
-                         _c(dtilde, np.uint8).reshape(-1),
-                         None if excl is None else _c(excl, np.uint8).reshape(-1),
-                         phi.reshape(-1), d2.reshape(-1), int(n_pm), sched, int(rmax),
-                         float(rho), key[0], key[1], int(tag_base), int(clip))
+    assert rs_mode in (0, 1) and sub_sweeps >= 1
+    return lib().vio_ann2(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
+                          _c(dtilde, np.uint8).reshape(-1),
+                          None if excl is None else _c(excl, np.uint8).reshape(-1),
+                          phi.reshape(-1), d2.reshape(-1), int(n_pm), sched, int(rmax),
+                          float(rho), key[0], key[1], int(tag_base), int(clip), int(rs_mode),
+                          int(sub_sweeps))
 
 
 def bruteforce_nn(x, target, dtilde, excl=None):
@@ -318,6 +327,8 @@ class Params:
     clip: int = 0
     schedule: str = "JAC"      # "SEQ" (Algorithm 1 as printed) or "JAC"
     fixed_outer: object = None  # None, an int, or a list per level (coarsest first)
+    rs_mode: int = 0           # 0: Eq. 3 (one radius per k); 1: every radius r_max rho^i >= 1
+    sub_sweeps: int = 1        # propagation sweeps before each random search
 
     @property
     def key(self):
@@ -395,7 +406,8 @@ def onion_peel(lv, prm, level_index):
         targets = dilate5(layer) & (1 - Hp)
         evals += ann(lv.x, targets, lv.dtilde, lv.phi, lv.d2, n_pm=prm.n_pm,
                      schedule=prm.schedule, rho=prm.rho, key=prm.key,
-                     tag_base=tag(PURPOSE_ONION, level_index, n_layer), clip=prm.clip, excl=Hp)
+                     tag_base=tag(PURPOSE_ONION, level_index, n_layer), clip=prm.clip, excl=Hp,
+                     rs_mode=prm.rs_mode, sub_sweeps=prm.sub_sweeps)
         x_new, _, deferred = vote(lv.x, layer, targets, lv.phi, lv.d2, weighted=prm.weighted,
                                   n_diff=0, want_deferred=True)
         lv.x = x_new
@@ -434,7 +446,8 @@ def iterate_level(lv, prm, level_index, n_outer=None, start_call=0):
             break
         evals += ann(lv.x, lv.htilde, lv.dtilde, lv.phi, lv.d2, n_pm=prm.n_pm,
                      schedule=prm.schedule, rho=prm.rho, key=prm.key,
-                     tag_base=tag(PURPOSE_SEARCH, level_index, start_call + k), clip=prm.clip)
+                     tag_base=tag(PURPOSE_SEARCH, level_index, start_call + k), clip=prm.clip,
+                     rs_mode=prm.rs_mode, sub_sweeps=prm.sub_sweeps)
         lv.x, change = vote(lv.x, lv.hole, lv.htilde, lv.phi, lv.d2, weighted=prm.weighted,
                             n_diff=3)
         e = change / (3.0 * max(nH, 1))

@@ -506,29 +506,57 @@ static void propagate_one(ann_ctx *a, size_t p, int k, const int32_t *phi_src,
     d2[p] = bd;
 }
 
-static void random_search_one(ann_ctx *a, size_t p, int k, int rmax, double rho,
+/* The random search of iteration k around the target's current shift.
+ * rs_mode 0 (Algorithm 1, Eq. 3): one candidate at radius r_max rho^k,
+ * drawn from counter (p, tag | k, clip, 0). rs_mode 1 (the original
+ * PatchMatch's search): candidates at every radius r_max rho^i >= 1, i = 0,
+ * 1, ..., largest first, each drawn from counter (p, tag | k, clip, i) around
+ * the best shift so far. */
+static void random_search_one(ann_ctx *a, size_t p, int k, int rmax, double rho, int rs_mode,
                               uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip,
                               int32_t *phi, float *d2)
 {
     int px, py, pt;
     coords(p, a->W, a->H, &px, &py, &pt);
-    uint32_t w[4];
-    draw((uint32_t)p, tag_base | (uint32_t)k, clip, key0, key1, w);
-    double radius = (double)rmax * pow(rho, (double)k);
-    int ox = (int)floor(radius * vio_unit_symmetric(w[0]));
-    int oy = (int)floor(radius * vio_unit_symmetric(w[1]));
-    int ot = (int)floor(radius * vio_unit_symmetric(w[2]));
     int32_t best[3] = {phi[3 * p], phi[3 * p + 1], phi[3 * p + 2]};
     float bd = d2[p];
-    try_shift(a, px, py, pt, best[0] + ox, best[1] + oy, best[2] + ot, best, &bd);
+    for (int i = 0;; ++i) {
+        double radius;
+        uint32_t w[4];
+        uint32_t ctr[4] = {(uint32_t)p, tag_base | (uint32_t)k, clip, 0u};
+        uint32_t key[2] = {key0, key1};
+        if (rs_mode == 0) {
+            radius = (double)rmax * pow(rho, (double)k);
+        } else {
+            radius = (double)rmax * pow(rho, (double)i);
+            if (radius < 1.0)
+                break;
+            ctr[3] = (uint32_t)i;
+        }
+        vio_philox4x32_10(ctr, key, w);
+        int ox = (int)floor(radius * vio_unit_symmetric(w[0]));
+        int oy = (int)floor(radius * vio_unit_symmetric(w[1]));
+        int ot = (int)floor(radius * vio_unit_symmetric(w[2]));
+        try_shift(a, px, py, pt, best[0] + ox, best[1] + oy, best[2] + ot, best, &bd);
+        if (rs_mode == 0)
+            break;
+    }
     phi[3 * p] = best[0]; phi[3 * p + 1] = best[1]; phi[3 * p + 2] = best[2];
     d2[p] = bd;
 }
 
-long long vio_ann(const float *x, int W, int H, int T, int C,
-                  const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
-                  int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,
-                  uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip)
+/* Algorithm 1 on the targets, in place on (phi, d2); returns the number of
+ * distance evaluations (candidates that land in D~, plus the initial
+ * distances). schedule 0: the sequential sweep as printed (in-place
+ * propagation in scan order); 1: Jacobi (every target reads the shifts the
+ * sweep started from). sub_sweeps >= 1 propagation sweeps (same direction)
+ * run before the random search of each iteration k; rs_mode as in
+ * random_search_one. */
+long long vio_ann2(const float *x, int W, int H, int T, int C,
+                   const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
+                   int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,
+                   uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip, int rs_mode,
+                   int sub_sweeps)
 {
     size_t V = (size_t)W * H * T;
     ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0};
@@ -553,28 +581,39 @@ long long vio_ann(const float *x, int W, int H, int T, int C,
         phi_old = (int32_t *)malloc(V * 3 * sizeof(int32_t));
 
     for (int k = 1; k <= n_pm; ++k) {
-        if (schedule == 0) {
-            if (k % 2 == 0) {
+        for (int j = 0; j < sub_sweeps; ++j) {
+            if (schedule == 0) {
+                if (k % 2 == 0) {
+                    for (size_t p = 0; p < V; ++p)
+                        if (target[p])
+                            propagate_one(&a, p, k, phi, phi, d2);
+                } else {
+                    for (size_t i = V; i-- > 0;)
+                        if (target[i])
+                            propagate_one(&a, i, k, phi, phi, d2);
+                }
+            } else {
+                memcpy(phi_old, phi, V * 3 * sizeof(int32_t));
                 for (size_t p = 0; p < V; ++p)
                     if (target[p])
-                        propagate_one(&a, p, k, phi, phi, d2);
-            } else {
-                for (size_t i = V; i-- > 0;)
-                    if (target[i])
-                        propagate_one(&a, i, k, phi, phi, d2);
+                        propagate_one(&a, p, k, phi_old, phi, d2);
             }
-        } else {
-            memcpy(phi_old, phi, V * 3 * sizeof(int32_t));
-            for (size_t p = 0; p < V; ++p)
-                if (target[p])
-                    propagate_one(&a, p, k, phi_old, phi, d2);
         }
         for (size_t p = 0; p < V; ++p)
             if (target[p])
-                random_search_one(&a, p, k, rmax, rho, key0, key1, tag_base, clip, phi, d2);
+                random_search_one(&a, p, k, rmax, rho, rs_mode, key0, key1, tag_base, clip, phi, d2);
     }
     free(phi_old);
     return a.evals;
+}
+
+long long vio_ann(const float *x, int W, int H, int T, int C,
+                  const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
+                  int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,
+                  uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip)
+{
+    return vio_ann2(x, W, H, T, C, target, dtilde, excl, phi, d2, n_pm, schedule, rmax, rho, key0, key1,
+                    tag_base, clip, 0, 1);
 }
 
 /* Exhaustive nearest neighbour over D~ in FP32 (ties: first source in

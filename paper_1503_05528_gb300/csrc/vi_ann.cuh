@@ -206,14 +206,26 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub,
     try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s2, c2.dx, c2.dy, c2.dt, cur, d, rej, D, n, sub,
                                            gmask);
 
-    // random search (Eq. 3)
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip, 0u), a.key0, a.key1);
-    const int shift = a.rho_log2 * k + 24;
-    const int cdx = cur.dx + random_offset(w.x, a.rmax, shift);
-    const int cdy = cur.dy + random_offset(w.y, a.rmax, shift);
-    const int cdt = cur.dt + random_offset(w.z, a.rmax, shift);
-    const int s3 = source_of(L, px, py, pt, cdx, cdy, cdt);
-    try_candidate_g<C5, G, PARTIAL, F16>(a, p, px, py, pt, s3, cdx, cdy, cdt, cur, d, rej, D, n, sub, gmask);
+    // random search: Eq. 3 (one radius per k), or every radius rmax rho^i >= 1
+    // around the best shift so far (counter word 3 = i)
+    if (a.do_random) {
+        for (int i = 0; i < 31; ++i) {
+            const int sh = a.rs_mode ? a.rho_log2 * i : a.rho_log2 * k;
+            if (a.rs_mode && (sh > 30 || (a.rmax >> sh) < 1))
+                break;
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
+                                                     a.rs_mode ? (uint32_t)i : 0u),
+                                          a.key0, a.key1);
+            const int cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
+            const int cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
+            const int cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
+            const int s3 = source_of(L, px, py, pt, cdx, cdy, cdt);
+            try_candidate_g<C5, G, PARTIAL, F16>(a, p, px, py, pt, s3, cdx, cdy, cdt, cur, d, rej, D, n, sub,
+                                                 gmask);
+            if (!a.rs_mode)
+                break;
+        }
+    }
     if (sub == 0) {
         a.phi_out[p] = cur;
         a.d_out[p] = d;

@@ -149,6 +149,7 @@ void free_state(vi_ctx *ctx)
 vi_status check_config(vi_ctx *ctx, const vi_config *c)
 {
     if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
+        c->rs_mode < 0 || c->rs_mode > 1 || c->sub_sweeps < 1 || c->sub_sweeps > 16 ||
         c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
           c->lanes_per_target == 4 || c->lanes_per_target == 8))
@@ -225,32 +226,38 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
                    ctx->cfg.lanes_per_target);
     CK_LAUNCH();
     const int rmax = std::max(l.W, std::max(l.H, l.T));
+    // launch s reads buffer s & 1 and writes the other one
+    int s = 0;
     for (int k = 1; k <= ctx->cfg.n_pm; ++k) {
-        AnnArgs a;
-        a.L = v;
-        a.targets = targets;
-        a.nT = nT;
-        a.phi_in = l.phi[(k - 1) & 1];
-        a.d_in = l.d2[(k - 1) & 1];
-        a.phi_out = l.phi[k & 1];
-        a.d_out = l.d2[k & 1];
-        a.tmask = tmask;
-        a.tbit = tbit;
-        a.excl = excl;
-        a.k = k;
-        a.rmax = rmax;
-        a.rho_log2 = ctx->rho_log2;
-        a.key0 = (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull);
-        a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
-        a.tag = tag;
-        a.clip = ctx->cfg.clip;
-        a.evals = ctx->evals_dev + 1;
-        a.gathered = ctx->evals_dev + 2;
-        a.screen = ctx->evals_dev + 3;
-        a.lanes = ctx->cfg.lanes_per_target;
-        TRY(step_launch(ctx, a));
+        for (int j = 0; j < ctx->cfg.sub_sweeps; ++j, ++s) {
+            AnnArgs a;
+            a.L = v;
+            a.targets = targets;
+            a.nT = nT;
+            a.phi_in = l.phi[s & 1];
+            a.d_in = l.d2[s & 1];
+            a.phi_out = l.phi[(s + 1) & 1];
+            a.d_out = l.d2[(s + 1) & 1];
+            a.tmask = tmask;
+            a.tbit = tbit;
+            a.excl = excl;
+            a.k = k;
+            a.rmax = rmax;
+            a.rho_log2 = ctx->rho_log2;
+            a.key0 = (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull);
+            a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
+            a.tag = tag;
+            a.clip = ctx->cfg.clip;
+            a.evals = ctx->evals_dev + 1;
+            a.gathered = ctx->evals_dev + 2;
+            a.screen = ctx->evals_dev + 3;
+            a.lanes = ctx->cfg.lanes_per_target;
+            a.rs_mode = ctx->cfg.rs_mode;
+            a.do_random = j == ctx->cfg.sub_sweeps - 1;
+            TRY(step_launch(ctx, a));
+        }
     }
-    if (ctx->cfg.n_pm & 1) {
+    if (s & 1) {
         launch_copy_targets(targets, nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], ctx->stream);
         CK_LAUNCH();
     }
@@ -345,6 +352,8 @@ void vi_config_default(vi_config *cfg)
     cfg->clip = 0;
     cfg->lanes_per_target = 0;
     cfg->stream_priority = 0;
+    cfg->rs_mode = 0;
+    cfg->sub_sweeps = 1;
 }
 
 vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)

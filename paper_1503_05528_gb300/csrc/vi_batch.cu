@@ -240,6 +240,8 @@ vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, 
     vi_config cfg = job_cfg ? *job_cfg : b->cfg;
     if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm || cfg.storage != b->cfg.storage)
         return bfail(b, VI_ERR_ARG, "vi_batch_add: use_texture, n_pm and storage must match the batch");
+    if (cfg.sub_sweeps != 1)
+        return bfail(b, VI_ERR_ARG, "vi_batch_add: batches run one propagation sweep per iteration");
     vi_ctx *ctx = nullptr;
     vi_status s = vi_ctx_create(&cfg, b->stream, &ctx);
     if (s != VI_OK)
@@ -312,6 +314,8 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
             a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
             a.tag = make_tag(PURPOSE_SEARCH, level, act[i]->outer);
             a.clip = ctx->cfg.clip;
+            a.rs_mode = ctx->cfg.rs_mode;
+            a.do_random = 1;
             a.phi_in = l.phi[0];
             a.d_in = l.d2[0];
             a.phi_out = l.phi[1];

@@ -59,6 +59,9 @@ struct AnnArgs {
     unsigned long long *gathered;  // FP32 source voxels actually read
     unsigned long long *screen;    // FP16 storage: FP16 voxels read, screened, passed (3 counters)
     int lanes;                     // lanes per target (1, 2, 4, 8); 0: by target count
+    int rs_mode;                   // 0: one random candidate at radius rmax rho^k (Eq. 3);
+                                   // 1: one at every radius rmax rho^i >= 1, i = 0, 1, ...
+    int do_random;                 // 0: propagation only (a sub-sweep before the last)
 };
 // FP16 screening when a.L.h4 is set (full distance only; the partial
 // distance of Eq. 11 always runs on the FP32 channels).

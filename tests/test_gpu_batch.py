@@ -86,3 +86,18 @@ def test_batch_rejects_mismatched_channels():
         c = _clip(SPECS[2])
         with pytest.raises(vi.ViError):
             b.add(c.rgb, c.mask, use_texture=0)
+
+
+def test_batch_multi_radius_search_equals_alone():
+    clips = [_clip(s) for s in SPECS[:3]]
+    with vi.Batch(rs_mode=1) as b:
+        ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=300 + i, clip=i) for i, c in enumerate(clips)]
+        b.run()
+        for i, (cid, c) in enumerate(zip(ids, clips)):
+            with vi.Context(levels=c.levels, seed=300 + i, clip=i, rs_mode=1) as ctx:
+                ctx.upload(c.rgb, c.mask)
+                ctx.run()
+                want = ctx.fetch_result()
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
+        with pytest.raises(vi.ViError):
+            b.add(clips[0].rgb, clips[0].mask, sub_sweeps=2)

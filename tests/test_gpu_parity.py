@@ -40,12 +40,12 @@ CASES = {
 }
 
 
-def _make(case, seed=11, n_pm=10, weighted=1):
+def _make(case, seed=11, n_pm=10, weighted=1, **cfg):
     spec = CASES[case]
     clip = spec["clip"]()
     pyr = O.build_pyramid(clip.rgb, clip.mask, spec["levels"], spec["tex"])
     ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm,
-                     weighted=weighted)
+                     weighted=weighted, **cfg)
     ctx.upload(clip.rgb, clip.mask)
     ctx.build_pyramid()
     return clip, pyr, ctx
@@ -132,6 +132,30 @@ def test_ann_bit_exact(case, n_pm, call):
             assert (gphi[m] == phi[m]).all()
             assert (gd2[m].view(np.uint32) == d2[m].view(np.uint32)).all()
             # the same candidates were compared (valid candidates of Algorithm 1)
+            assert g_evals == o_evals
+
+
+@pytest.mark.parametrize("case,n_pm,rs_mode,sub_sweeps", [("tiny_rgb", 10, 1, 1), ("layered_tex", 4, 1, 3),
+                                                         ("odd_sizes", 3, 0, 2), ("layered_tex", 5, 0, 4)])
+def test_ann_options_bit_exact(case, n_pm, rs_mode, sub_sweeps):
+    # the multi-radius random search and propagation sub-sweeps (with an odd
+    # or even total number of sweeps) match the oracle bit for bit
+    clip, pyr, ctx = _make(case, seed=37, n_pm=n_pm, rs_mode=rs_mode, sub_sweeps=sub_sweeps)
+    with ctx:
+        for level, lv in enumerate(pyr):
+            x, phi, d2 = _state(lv, level, 37)
+            ctx.set_channels(level, x)
+            ctx.set_nnf(level, phi, d2)
+            e0 = ctx.stats()["evals"]
+            ctx.ann(level, 2)
+            g_evals = ctx.stats()["evals"] - e0
+            gphi, gd2 = ctx.get_nnf(level)
+            o_evals = O.ann(x, lv.htilde, lv.dtilde, phi, d2, n_pm=n_pm, schedule="JAC", key=(37, 0),
+                            tag_base=O.tag(O.PURPOSE_SEARCH, level, 2), rs_mode=rs_mode,
+                            sub_sweeps=sub_sweeps)
+            m = lv.htilde == 1
+            assert (gphi[m] == phi[m]).all()
+            assert (gd2[m].view(np.uint32) == d2[m].view(np.uint32)).all()
             assert g_evals == o_evals
 
 

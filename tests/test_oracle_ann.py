@@ -1,7 +1,9 @@
 """Pins for the oracle's 3D PatchMatch (Sec. 3.1, Algorithm 1): validity of
 the shift map, monotone distances, the exhaustive nearest neighbour, the scan
-directions of the printed (sequential) algorithm, and the random-search
-radius r_max rho^k (Eq. 3)."""
+directions of the printed (sequential) algorithm, the random-search radius
+r_max rho^k (Eq. 3); and for the two options beside it: the original
+PatchMatch multi-radius search (every r_max rho^i >= 1 per iteration) and
+several propagation sub-sweeps per iteration."""
 import numpy as np
 import pytest
 
@@ -174,3 +176,92 @@ def test_random_search_is_schedule_independent():
     O.ann(x, iso, dt, b, db, n_pm=10, schedule="JAC", key=(4, 4))
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(da, db)
+
+
+def test_jacobi_sub_sweeps_spread_one_voxel_each():
+    # J propagation sweeps per iteration k: during each forward iteration
+    # (k even) the seed's shift travels J voxels, during k odd none (the row's
+    # seed is its leftmost voxel)
+    x, target, dt, phi0, xs = _translation_row_case()
+    for n_pm, J in [(2, 1), (2, 3), (4, 2), (3, 4), (4, 5)]:
+        phi = phi0.copy()
+        d2 = np.full(target.shape, np.inf, np.float32)
+        O.ann(x, target, dt, phi, d2, n_pm=n_pm, schedule="JAC", rmax=0, sub_sweeps=J)
+        want = min(1 + J * (n_pm // 2), len(xs))
+        assert (d2[6, 8, xs] == 0.0).sum() == want, (n_pm, J)
+
+
+def _flat_case():
+    W, H, T = 64, 64, 64
+    x = np.full((T, H, W, 1), 0.5, np.float32)
+    x[30:35, 30:35, 30:35, 0] = 0.9        # the bad source patch at (32, 32, 32)
+    hole = np.zeros((T, H, W), np.uint8)
+    _, dt = O.masks(hole)
+    target = np.zeros((T, H, W), np.uint8)
+    target[8:56:2, 8:56:2, 8:56:2] = 1     # isolated targets: no propagation
+    tt, yy, xx = np.nonzero(target)
+    phi = np.zeros((T, H, W, 3), np.int32)
+    phi[tt, yy, xx, 0] = 32 - xx
+    phi[tt, yy, xx, 1] = 32 - yy
+    phi[tt, yy, xx, 2] = 32 - tt
+    return x, target, dt, phi, (tt, yy, xx)
+
+
+def test_multi_radius_search_starts_at_r_max():
+    # the original PatchMatch search tries r_max rho^i for i = 0, 1, ...: its
+    # first candidate (accepted whenever valid and clear of the bad patch, as
+    # almost every source matches exactly) moves the shift by
+    # floor(r_max delta), spanning [-r_max, r_max - 1]
+    # (r_max = 24 keeps every first candidate inside D~: sources 32 +- 24)
+    x, target, dt, phi0, (tt, yy, xx) = _flat_case()
+    phi = phi0.copy()
+    d2 = np.full(target.shape, np.inf, np.float32)
+    rmax = 24
+    O.ann(x, target, dt, phi, d2, n_pm=1, schedule="JAC", rmax=rmax, key=(5, 6), rs_mode=1)
+    off = (phi - phi0)[tt, yy, xx]
+    moved = (off != 0).any(axis=1)
+    assert moved.mean() > 0.9
+    assert off.min() == -rmax and off.max() == rmax - 1
+
+
+def test_multi_radius_search_counts_every_radius():
+    # isolated targets whose every candidate is valid make one evaluation per
+    # radius r_max 2^-i >= 1 per iteration (plus the initial distance): with
+    # r_max = 8, radii 8, 4, 2, 1
+    x, target, dt, phi0, (tt, yy, xx) = _flat_case()
+    one = np.zeros_like(target)
+    one[32, 32, 32] = 1
+    phi = np.zeros_like(phi0)
+    d2 = np.full(target.shape, np.inf, np.float32)
+    ev = O.ann(x, one, dt, phi, d2, n_pm=3, schedule="JAC", rmax=8, key=(1, 1), rs_mode=1)
+    assert ev == 1 + 3 * 4
+    ev = O.ann(x, one, dt, phi, d2, n_pm=3, schedule="JAC", rmax=8, key=(1, 1), rs_mode=0)
+    assert ev == 1 + 3 * 1
+
+
+def test_multi_radius_with_one_radius_matches_eq3():
+    # r_max = 1: the multi-radius search has the single radius 1, drawn from
+    # counter word 3 = 0, which is Eq. 3's candidate at k = 1 with r_max = 2
+    x, hole, ht, dt, phi0 = _setup(seed=6)
+    a, b = phi0.copy(), phi0.copy()
+    da = np.full(hole.shape, np.inf, np.float32)
+    db = da.copy()
+    ea = O.ann(x, ht, dt, a, da, n_pm=1, schedule="JAC", rmax=1, key=(3, 3), rs_mode=1)
+    eb = O.ann(x, ht, dt, b, db, n_pm=1, schedule="JAC", rmax=2, key=(3, 3), rs_mode=0)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(da, db)
+    assert ea == eb
+
+
+@pytest.mark.parametrize("schedule", ["SEQ", "JAC"])
+def test_multi_radius_and_sub_sweeps_keep_validity_and_monotonicity(schedule):
+    x, hole, ht, dt, phi = _setup(seed=8)
+    d2 = np.full(hole.shape, np.inf, np.float32)
+    O.ann(x, ht, dt, phi, d2, n_pm=0)
+    prev = d2.copy()
+    for call in range(3):
+        O.ann(x, ht, dt, phi, d2, n_pm=4, schedule=schedule, key=(2, 3), tag_base=call,
+              rs_mode=1, sub_sweeps=2)
+        assert _valid(phi, ht, dt)
+        assert (d2[ht == 1] <= prev[ht == 1]).all()
+        prev = d2.copy()
