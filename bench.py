@@ -274,7 +274,25 @@ def run_gpu(args):
                      rs_mode=1 if args.rs_mode == "multi" else 0, sub_sweeps=args.sub_sweeps)
     n_hole = int(clip.mask.sum())
 
+    T = clip.mask.shape[0]
+    if args.realign:
+        al_d, am_d = torch.empty_like(rgb_d), torch.empty_like(mask_d)
+        res_d = torch.empty_like(rgb_d)
+
+    def realign_in():
+        to_ref = vi.affine_to_reference(vi.affine_estimate(rgb_d, mask_d, stream=stream.cuda_stream), T)
+        vi.affine_align(rgb_d, mask_d, to_ref, al_d, am_d, stream=stream.cuda_stream)
+        return to_ref
+
     def step():
+        if args.realign:
+            # Algorithm 4 with AlignVideo first and UnwarpVideo last
+            to_ref = realign_in()
+            ctx.upload(al_d, am_d)
+            ctx.run()
+            ctx.fetch_result(res_d)
+            vi.affine_unwarp(rgb_d, mask_d, res_d, to_ref, out_d, stream=stream.cuda_stream)
+            return
         ctx.upload(rgb_d, mask_d)
         ctx.run()
         ctx.fetch_result(out_d)
@@ -318,6 +336,16 @@ def run_gpu(args):
     step_launches = s1["step_timed"] - s0["step_timed"]
     launches = s1["launches"] - s0["launches"]
     outer = s1["outer"]
+
+    realign_ms = None
+    if args.realign:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            to_ref = realign_in()
+            vi.affine_unwarp(rgb_d, mask_d, res_d, to_ref, out_d, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        realign_ms = 1e3 * (time.perf_counter() - t) / args.steps
 
     # end to end through host buffers: upload from pinned memory, fetch to host
     rgb_h = torch.from_numpy(clip.rgb).pin_memory()
@@ -368,6 +396,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "levels": clip.levels, "channels": 5, "storage": args.storage,
                    "random_search": args.rs_mode, "sub_sweeps": args.sub_sweeps,
+                   "realign": bool(args.realign),
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
                    "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
@@ -375,6 +404,7 @@ def run_gpu(args):
         "evals_per_step": evals / args.steps,
         "outer_iterations_per_level": outer[:clip.levels],
         "energy_level0": {"E_H": energy[0], "E_Htilde": energy[1]},
+        "realign_ms_per_step": realign_ms,
         "screening": ({"screened": screened, "passed": passed,
                        "pass_rate": passed / screened if screened else None,
                        "fp16_voxels": step_gathered_h, "fp32_voxels": step_gathered}
@@ -739,6 +769,8 @@ def main():
     ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],
                     help="random search: one radius per iteration (Eq. 3) or every radius")
     ap.add_argument("--sub-sweeps", type=int, default=1, help="propagation sweeps per iteration")
+    ap.add_argument("--realign", action="store_true",
+                    help="AlignVideo (Sec. 3.4) before and UnwarpVideo after every inpainting")
     ap.add_argument("--tune-save", default=None, help="write the lanes autotuning table after warm-up")
     ap.add_argument("--tune-load", default=None, help="import a lanes autotuning table before warm-up")
     ap.add_argument("--lanes", type=int, default=0,

@@ -292,6 +292,51 @@ vi_status vi_profile(vi_ctx *ctx, int enable);
 /* The context's counters (synchronises to read event times). */
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
 
+/* ---------------------------------------------------------------------------
+ * Affine realignment: Sec. 3.4, Algorithm 2 (AlignVideo) and the UnwarpVideo
+ * step that ends Algorithm 4. The paper estimates the dominant affine motion
+ * between successive frames with the robust method of Odobez and Bouthemy;
+ * this library's reading: a point p = (x, y) of frame n lies at A(p) = p +
+ * w(p) in frame n+1, w(p) = (a0 + a1 x + a2 y, a3 + a4 x + a5 y) (theta =
+ * a0..a5, pixel centres at integer coordinates), fitted by Gauss-Newton with
+ * iteratively reweighted least squares (Tukey biweight, c = 4.6851 sigma) on
+ * the grey level (R+G+B)/3 of the known pixels, coarse to fine over a 2x2
+ * mean pyramid. All functions run on cuda_stream (NULL: the legacy default
+ * stream) and synchronise it before returning. rgb: [T][H][W][3] float32;
+ * mask: [T][H][W] uint8 (1 = occluded); ptr_is_device says where rgb, mask
+ * and the other video buffers live (theta arrays are always host memory).
+ * Errors: VI_ERR_ARG (null pointer, sizes), VI_ERR_OOM, VI_ERR_CUDA; the text
+ * of the last error of the calling thread is vi_realign_last_error().
+ * ------------------------------------------------------------------------- */
+const char *vi_realign_last_error(void);
+
+/* Pyramid levels the estimation uses by default: the most (up to 6) that keep
+ * the smallest side of the coarsest level at least 16 pixels. */
+int vi_affine_levels(int W, int H);
+
+/* theta_{n,n+1} for n = 0 .. T-2 into theta_out[T-1][6] (host). levels = 0:
+ * vi_affine_levels; iters: Gauss-Newton iterations per level (10). Occluded
+ * pixels and samples touching occluded pixels take no part. */
+vi_status vi_affine_estimate(const float *rgb, const uint8_t *mask, int W, int H, int T, int ptr_is_device,
+                             int levels, int iters, double *theta_out, void *cuda_stream);
+
+/* theta_{n,N_m} for every frame (host arrays): the successive motions
+ * composed towards the reference frame N_m = floor(T/2) counted from 1
+ * (index max(0, T/2 - 1)); inverses after it. to_ref_out[T][6]. */
+vi_status vi_affine_to_reference(const double *theta_pairs, int T, double *to_ref_out);
+
+/* AlignVideo: aligned frame n samples frame n bilinearly at
+ * theta_{n,N_m}^-1(q) for every pixel q; a sample outside frame n, or whose
+ * bilinear neighbours with non-zero weight include an occluded pixel, is
+ * occluded in mask_out (its rgb_out value is meaningless). */
+vi_status vi_affine_align(const float *rgb, const uint8_t *mask, int W, int H, int T, const double *to_ref,
+                          float *rgb_out, uint8_t *mask_out, int ptr_is_device, void *cuda_stream);
+
+/* UnwarpVideo: rgb_out = rgb where mask = 0; where mask = 1, the inpainted
+ * aligned video sampled bilinearly at theta_{n,N_m}(y), clamped to the frame. */
+vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *aligned_result, int W, int H,
+                           int T, const double *to_ref, float *rgb_out, int ptr_is_device, void *cuda_stream);
+
 /* Lanes-per-target autotuning (no counterpart in the paper; speed only, never
  * a result). With lanes_per_target = 0 the first PatchMatch step or rescore
  * launch of a kernel family for a target count (per device, channels,

@@ -28,6 +28,8 @@ EXPORTS = [
     "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
     "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
     "vi_profile", "vi_get_stats", "vi_energy_noalloc", "vi_tune_export", "vi_tune_import",
+    "vi_realign_last_error", "vi_affine_levels", "vi_affine_estimate", "vi_affine_to_reference",
+    "vi_affine_align", "vi_affine_unwarp",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -117,6 +119,13 @@ def _declare(L):
     L.vi_tune_export.argtypes = [C.c_char_p, i]
     L.vi_tune_export.restype = i
     L.vi_tune_import.argtypes = [C.c_char_p]
+    L.vi_realign_last_error.argtypes = []
+    L.vi_realign_last_error.restype = C.c_char_p
+    L.vi_affine_levels.argtypes = [i, i]
+    L.vi_affine_estimate.argtypes = [vp, vp, i, i, i, i, i, i, vp, vp]
+    L.vi_affine_to_reference.argtypes = [vp, i, vp]
+    L.vi_affine_align.argtypes = [vp, vp, i, i, i, vp, vp, vp, i, vp]
+    L.vi_affine_unwarp.argtypes = [vp, vp, vp, i, i, i, vp, vp, i, vp]
     ull = C.c_ulonglong
     L.vi_batch_create.argtypes = [P(ViConfig), vp, P(vp)]
     L.vi_batch_destroy.argtypes = [vp]
@@ -433,15 +442,91 @@ def tune_import(text):
         raise ViError(st, "vi_tune_import: malformed line")
 
 
+def _rck(st, what):
+    if st != VI_OK:
+        raise ViError(st, f"{what}: " + load().vi_realign_last_error().decode(errors="replace"))
+
+
+def affine_estimate(rgb, mask, levels=0, iters=10, stream=None):
+    """Sec. 3.4: theta_{n,n+1} for every pair of successive frames, [T-1][6]."""
+    rgb = np.ascontiguousarray(rgb, np.float32) if isinstance(rgb, np.ndarray) else rgb
+    mask = np.ascontiguousarray(mask, np.uint8) if isinstance(mask, np.ndarray) else mask
+    T, H, W = mask.shape[:3]
+    out = np.zeros((max(T - 1, 0), 6), np.float64)
+    pr, dr = _ptr(rgb)
+    pm, dm = _ptr(mask)
+    assert dr == dm
+    _rck(load().vi_affine_estimate(pr, pm, W, H, T, dr, levels, iters, out.ctypes.data,
+                                   C.c_void_p(stream) if stream else None), "vi_affine_estimate")
+    return out
+
+
+def affine_to_reference(theta_pairs, T):
+    th = np.ascontiguousarray(theta_pairs, np.float64).reshape(-1, 6)
+    out = np.zeros((T, 6), np.float64)
+    _rck(load().vi_affine_to_reference(th.ctypes.data if th.size else None, T, out.ctypes.data),
+         "vi_affine_to_reference")
+    return out
+
+
+def affine_align(rgb, mask, to_ref, rgb_out=None, mask_out=None, stream=None):
+    """AlignVideo: (aligned rgb, aligned occlusion)."""
+    rgb = np.ascontiguousarray(rgb, np.float32) if isinstance(rgb, np.ndarray) else rgb
+    mask = np.ascontiguousarray(mask, np.uint8) if isinstance(mask, np.ndarray) else mask
+    T, H, W = mask.shape[:3]
+    tr = np.ascontiguousarray(to_ref, np.float64)
+    pr, dev = _ptr(rgb)
+    pm, _ = _ptr(mask)
+    if rgb_out is None:
+        rgb_out = np.empty((T, H, W, 3), np.float32)
+        mask_out = np.empty((T, H, W), np.uint8)
+    po, _ = _ptr(rgb_out)
+    pq, _ = _ptr(mask_out)
+    _rck(load().vi_affine_align(pr, pm, W, H, T, tr.ctypes.data, po, pq, dev,
+                                C.c_void_p(stream) if stream else None), "vi_affine_align")
+    return rgb_out, mask_out
+
+
+def affine_unwarp(rgb, mask, aligned_result, to_ref, out=None, stream=None):
+    """UnwarpVideo: the original video with its occluded pixels taken from
+    the inpainted aligned video."""
+    rgb = np.ascontiguousarray(rgb, np.float32) if isinstance(rgb, np.ndarray) else rgb
+    mask = np.ascontiguousarray(mask, np.uint8) if isinstance(mask, np.ndarray) else mask
+    res = np.ascontiguousarray(aligned_result, np.float32) if isinstance(aligned_result, np.ndarray) \
+        else aligned_result
+    T, H, W = mask.shape[:3]
+    tr = np.ascontiguousarray(to_ref, np.float64)
+    pr, dev = _ptr(rgb)
+    pm, _ = _ptr(mask)
+    pa, _ = _ptr(res)
+    if out is None:
+        out = np.empty((T, H, W, 3), np.float32)
+    po, _ = _ptr(out)
+    _rck(load().vi_affine_unwarp(pr, pm, pa, W, H, T, tr.ctypes.data, po, dev,
+                                 C.c_void_p(stream) if stream else None), "vi_affine_unwarp")
+    return out
+
+
 def auto_levels(mask):
     mask = np.ascontiguousarray(mask, np.uint8)
     T, H, W = mask.shape
     return load().vi_auto_levels(mask.ctypes.data, W, H, T)
 
 
-def inpaint(rgb, mask, **cfg):
-    """Run the whole method on one clip and return the inpainted video."""
+def inpaint(rgb, mask, realign=False, **cfg):
+    """Run the whole method on one clip and return the inpainted video. With
+    realign, Algorithm 4 as printed: AlignVideo (Sec. 3.4) first, inpainting
+    in the aligned domain, UnwarpVideo last."""
+    if not realign:
+        with Context(**cfg) as ctx:
+            ctx.upload(rgb, mask)
+            ctx.run()
+            return ctx.fetch_result()
+    T = mask.shape[0]
+    to_ref = affine_to_reference(affine_estimate(rgb, mask), T)
+    al, al_mask = affine_align(rgb, mask, to_ref)
     with Context(**cfg) as ctx:
-        ctx.upload(rgb, mask)
+        ctx.upload(al, al_mask)
         ctx.run()
-        return ctx.fetch_result()
+        res = ctx.fetch_result()
+    return affine_unwarp(rgb, mask, res, to_ref)
