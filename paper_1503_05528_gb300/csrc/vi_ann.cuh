@@ -198,13 +198,41 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub,
     // clip): FP32 storage 38.0 (320x240x60) and 490 (1280x720x100); all four
     // candidates screened on five channels 52.6 and 661; the random one only,
     // screened on c0..c3, 39.4 and 462.
+    //
+    // A neighbour whose shift did not change in the last two sweeps offers
+    // the candidate this target already judged two sweeps ago, in the same
+    // direction, on the same video (the channels are fixed within an ANN
+    // call): then it either lost (its distance was >= this target's distance,
+    // which has not grown since) or won and has been kept or beaten since.
+    // Either way it cannot be strictly better now, so it is counted and
+    // skipped without a gather; every decision stays the same.
     Rejected rej;
-    try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s0, c0.dx, c0.dy, c0.dt, cur, d, rej, D, n, sub,
-                                           gmask);
-    try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s1, c1.dx, c1.dy, c1.dt, cur, d, rej, D, n, sub,
-                                           gmask);
-    try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s2, c2.dx, c2.dy, c2.dt, cur, d, rej, D, n, sub,
-                                           gmask);
+    const bool stale_ok = a.chg_in != nullptr && k >= 3;
+    const bool st0 = stale_ok && t0 && (a.chg_in[r0] & 3u) == 0;
+    const bool st1 = stale_ok && t1 && (a.chg_in[r1] & 3u) == 0;
+    const bool st2 = stale_ok && t2 && (a.chg_in[r2] & 3u) == 0;
+    const Shift start = cur;
+    if (st0) {
+        if (s0 >= 0)
+            ++n.evals;
+    } else {
+        try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s0, c0.dx, c0.dy, c0.dt, cur, d, rej, D, n, sub,
+                                               gmask);
+    }
+    if (st1) {
+        if (s1 >= 0)
+            ++n.evals;
+    } else {
+        try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s1, c1.dx, c1.dy, c1.dt, cur, d, rej, D, n, sub,
+                                               gmask);
+    }
+    if (st2) {
+        if (s2 >= 0)
+            ++n.evals;
+    } else {
+        try_candidate_g<C5, G, PARTIAL, false>(a, p, px, py, pt, s2, c2.dx, c2.dy, c2.dt, cur, d, rej, D, n, sub,
+                                               gmask);
+    }
 
     // random search: Eq. 3 (one radius per k), or every radius rmax rho^i >= 1
     // around the best shift so far (counter word 3 = i)
@@ -229,6 +257,10 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub,
     if (sub == 0) {
         a.phi_out[p] = cur;
         a.d_out[p] = d;
+        if (a.chg_out) {
+            const bool changed = cur.dx != start.dx || cur.dy != start.dy || cur.dt != start.dt;
+            a.chg_out[p] = (uint8_t)((changed ? 1u : 0u) | ((a.chg_in[p] & 1u) << 1));
+        }
     }
 }
 

@@ -122,6 +122,8 @@ void free_state(vi_ctx *ctx)
         dfree(ctx, l.phi[1]);
         dfree(ctx, l.d2[0]);
         dfree(ctx, l.d2[1]);
+        dfree(ctx, l.chg[0]);
+        dfree(ctx, l.chg[1]);
         dfree(ctx, l.targets);
         dfree(ctx, l.holes);
         dfree(ctx, l.sources);
@@ -254,6 +256,9 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
             a.lanes = ctx->cfg.lanes_per_target;
             a.rs_mode = ctx->cfg.rs_mode;
             a.do_random = j == ctx->cfg.sub_sweeps - 1;
+            const bool flags = ctx->cfg.sub_sweeps == 1;
+            a.chg_in = flags ? l.chg[s & 1] : nullptr;
+            a.chg_out = flags ? l.chg[(s + 1) & 1] : nullptr;
             TRY(step_launch(ctx, a));
         }
     }
@@ -439,9 +444,9 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
     int w = W, h = H;
     for (int l = 0; l < L; ++l) {
         const size_t V = (size_t)w * h * T;
-        // x4, x1, code, 2 shift + 2 distance buffers, three lists (upper bound),
+        // x4, x1, code, 2 shift + 2 distance + 2 change-flag buffers, three lists (upper bound),
         // FP16 copies
-        total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 12);
+        total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 2 + 12);
         if (cfg && cfg->storage == 1)
             total += V * 8 + 256;
         w = (w + 1) / 2;
@@ -509,6 +514,7 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
         for (int b = 0; b < 2; ++b) {
             TRY(dalloc(ctx, &lv.phi[b], V * sizeof(Shift)));
             TRY(dalloc(ctx, &lv.d2[b], V * sizeof(float)));
+            TRY(dalloc(ctx, &lv.chg[b], V));
             CK(cudaMemsetAsync(lv.phi[b], 0, V * sizeof(Shift), ctx->stream));
             launch_fill_f32(lv.d2[b], INFINITY, (long long)V, ctx->stream);
             CK_LAUNCH();

@@ -320,11 +320,15 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
             a.d_in = l.d2[0];
             a.phi_out = l.phi[1];
             a.d_out = l.d2[1];
+            a.chg_in = l.chg[0];
+            a.chg_out = l.chg[1];
             bc.odd = a;
             a.phi_in = l.phi[1];
             a.d_in = l.d2[1];
             a.phi_out = l.phi[0];
             a.d_out = l.d2[0];
+            a.chg_in = l.chg[1];
+            a.chg_out = l.chg[0];
             bc.even = a;
             VoteArgs v;
             v.L = l.view();

@@ -33,6 +33,7 @@ struct Level {
     unsigned *hmax = nullptr;
     Shift *phi[2] = {nullptr, nullptr};
     float *d2[2] = {nullptr, nullptr};
+    uint8_t *chg[2] = {nullptr, nullptr};   // change flags of the last two sweeps, ping-pong with phi
     int *targets = nullptr, *holes = nullptr, *sources = nullptr;
     int nT = 0, nH = 0, nS = 0;
 

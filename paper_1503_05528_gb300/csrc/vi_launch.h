@@ -62,6 +62,11 @@ struct AnnArgs {
     int rs_mode;                   // 0: one random candidate at radius rmax rho^k (Eq. 3);
                                    // 1: one at every radius rmax rho^i >= 1, i = 0, 1, ...
     int do_random;                 // 0: propagation only (a sub-sweep before the last)
+    // Change flags (one sweep per PatchMatch iteration only): chg_in[r] bit 0
+    // = r's shift changed in the previous sweep, bit 1 = in the one before;
+    // chg_out receives the flags after this sweep. nullptr: no flags.
+    const uint8_t *chg_in;
+    uint8_t *chg_out;
 };
 // FP16 screening when a.L.h4 is set (full distance only; the partial
 // distance of Eq. 11 always runs on the FP32 channels).
