@@ -101,7 +101,6 @@ struct VoteArgs {
     uint8_t *hp;           // onion peel: cleared for filled voxels (nullable)
     float *partials;       // per-block sum of |change| over the colour channels
 };
-int vote_blocks(int n);
 void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st);
 // out[0] = sum of partials[0..n) in a fixed order, in two stages; chunks
 // holds sum_chunks(n) doubles of scratch.

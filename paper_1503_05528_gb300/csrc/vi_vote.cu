@@ -14,10 +14,28 @@ static inline int blocks_for(long long n, int block)
 static constexpr int VOTE_BLOCK = 256;            // 8 warps, one occluded voxel per warp
 static constexpr int VOTE_WARPS = VOTE_BLOCK / 32;
 
-int vote_blocks(int n) { return blocks_for(n, VOTE_WARPS); }
+// The patch offsets a lane owns: j = l, l+32, l+64, l+96 (j < 125), offset
+// (j%5 - 2, (j/5)%5 - 2, j/25 - 2), packed as bytes (dx+2, dy+2, dt+2, 1 if
+// j < 125).
+struct VoteLane {
+    unsigned off[4];
+};
 
-// One warp per voxel p. Lane l owns the patch offsets j = l, l+32, l+64, l+96
-// (j < 125; offset (j%5 - 2, (j/5)%5 - 2, j/25 - 2)), i.e. the q in N_p.
+__device__ __forceinline__ VoteLane vote_lane(int lane)
+{
+    VoteLane v;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int j = lane + 32 * m;
+        v.off[m] = j < 125 ? ((unsigned)(j % 5) | ((unsigned)((j / 5) % 5) << 8) | ((unsigned)(j / 25) << 16) |
+                              (1u << 24))
+                           : 0u;
+    }
+    return v;
+}
+
+// One warp per voxel p; lane l handles the q = p + offset of its offsets
+// (the q in N_p).
 //  1. each lane loads d2(q) of its contributors (q inside the video, allowed,
 //     finite);
 //  2. sigma_p^2 = the element of rank ceil(0.75 n) of the n values (nearest
@@ -27,8 +45,10 @@ int vote_blocks(int n) { return blocks_for(n, VOTE_WARPS); }
 //     unweighted); each lane accumulates s_q u(p + phi(q)) over all channels;
 //  4. warp sums; lane 0 writes u(p) and stores |u_new - u_old| summed over
 //     R, G, B in the voxel's slot of partials.
+// A voxel at least 2 from every border has its whole patch inside the video
+// and skips those tests.
 template <bool C5>
-__device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
+__device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, const VoteLane &vl)
 {
     float change = 0.0f;
     {
@@ -36,18 +56,20 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
         const int p = a.list[item];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);
+        const bool interior = px >= 2 && px < L.W - 2 && py >= 2 && py < L.H - 2 && pt >= 2 && pt < L.T - 2;
         float dq[4];
         int qv[4];
         unsigned okm = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const int j = lane + 32 * m;
+            const unsigned o = vl.off[m];
             dq[m] = 0.0f;
             qv[m] = 0;
-            if (j < 125) {
-                const int qx = px + (j % 5) - 2, qy = py + ((j / 5) % 5) - 2, qt = pt + (j / 25) - 2;
-                if (inside(L, qx, qy, qt)) {
-                    const int q = qt * L.HW + qy * L.W + qx;
+            if (o) {
+                const int ox = (int)(o & 0xFFu) - 2, oy = (int)((o >> 8) & 0xFFu) - 2,
+                          ot = (int)((o >> 16) & 0xFFu) - 2;
+                if (interior || inside(L, px + ox, py + oy, pt + ot)) {
+                    const int q = p + ot * L.HW + oy * L.W + ox;
                     if (a.allowed[q] & a.abit) {
                         const float d = a.d2[q];
                         const Shift f = a.phi[q];
@@ -107,6 +129,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
                 sigma2 = __uint_as_float(X);
             }
             float n0 = 0.f, n1 = 0.f, n2 = 0.f, n3 = 0.f, n4 = 0.f, den = 0.f;
+            const float inv2s = sigma2 > 0.0f ? 1.0f / (2.0f * sigma2) : 0.0f;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 if (!((okm >> m) & 1u))
@@ -115,7 +138,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane)
                 if (!a.weighted)
                     w = 1.0f;
                 else if (sigma2 > 0.0f)
-                    w = expf(-(dq[m] / (2.0f * sigma2)));
+                    w = dq[m] > 0.0f ? expf(-(dq[m] * inv2s)) : 1.0f;   // inv2s may be +inf
                 else
                     w = (dq[m] == 0.0f) ? 1.0f : 0.0f;
                 const Shift f = a.phi[qv[m]];
@@ -159,7 +182,7 @@ __global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
 {
     const int item = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5);
     if (item < a.n)
-        vote_one<C5>(a, item, threadIdx.x & 31);
+        vote_one<C5>(a, item, threadIdx.x & 31, vote_lane(threadIdx.x & 31));
 }
 
 // Batch form: warp g of the launch grid-strides over the occluded voxels of
@@ -168,12 +191,29 @@ template <bool C5>
 __global__ void __launch_bounds__(VOTE_BLOCK) k_vote_batch(const BatchClip *__restrict__ clips,
                                                            const int *__restrict__ prefix, int n)
 {
+    const VoteLane vl = vote_lane(threadIdx.x & 31);
     const int total = __ldg(prefix + n);
     const int nwarps = gridDim.x * VOTE_WARPS;
     for (int g = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5); g < total; g += nwarps) {
         const int c = find_segment(prefix, n, g);
-        vote_one<C5>(clips[c].vote, g - __ldg(prefix + c), threadIdx.x & 31);
+        vote_one<C5>(clips[c].vote, g - __ldg(prefix + c), threadIdx.x & 31, vl);
     }
+}
+
+// One wave of VOTE_BLOCK blocks (8 per SM at the vote's register count), or
+// fewer when there is less work.
+static int vote_grid(long long items)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    const long long need = (items + VOTE_WARPS - 1) / VOTE_WARPS;
+    const long long cap = (long long)sms * 8;
+    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
 void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int total_holes, bool c5,
@@ -181,12 +221,7 @@ void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int to
 {
     if (total_holes <= 0 || n <= 0)
         return;
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = vote_blocks(total_holes);
-    if (grid > sms * 8)
-        grid = sms * 8;
+    const int grid = vote_grid(total_holes);
     VI_COUNT_LAUNCH();
     if (c5)
         k_vote_batch<true><<<grid, VOTE_BLOCK, 0, st>>>(clips, hprefix, n);
@@ -199,10 +234,11 @@ void launch_vote(const VoteArgs &a, bool c5, cudaStream_t st)
     if (a.n <= 0)
         return;
     VI_COUNT_LAUNCH();
+    const int grid = blocks_for(a.n, VOTE_WARPS);   // one warp per voxel
     if (c5)
-        k_vote<true><<<vote_blocks(a.n), VOTE_BLOCK, 0, st>>>(a);
+        k_vote<true><<<grid, VOTE_BLOCK, 0, st>>>(a);
     else
-        k_vote<false><<<vote_blocks(a.n), VOTE_BLOCK, 0, st>>>(a);
+        k_vote<false><<<grid, VOTE_BLOCK, 0, st>>>(a);
 }
 
 // Deterministic sum of n values by one block of 256 threads: thread j adds
