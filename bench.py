@@ -51,8 +51,7 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # ncu capture (profiles/k_ann_step_layered_320x240x60.md), as a dict with
 # keys workload, storage, bytes, gathered_voxels. Applies to that workload and
 # storage only; None while the kernel has changed since the capture.
-NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
-                    "bytes": 9.1417e6, "gathered_voxels": 3121057}
+NCU_STEP_TRAFFIC = None
 
 
 def combine_ranks(values, dist=None, device="cpu"):
