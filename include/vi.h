@@ -98,6 +98,11 @@ typedef struct {
                             last one followed by the random search (1, the
                             paper's; more spread a good shift further per
                             parallel iteration); 1..16; batches need 1 */
+    int time_subsample;  /* 0: pyramid levels keep every frame (Sec. 3.6); 1: the
+                            option the paper uses once for long occlusions:
+                            every level also halves the frames (2x2x2 means,
+                            occlusion by OR, features sampled at (2^l x, 2^l y,
+                            2^l t), shifts upsampled with dt doubled) */
 } vi_config;
 
 /* Per-context counters. evals, step_*: since vi_ctx_create; outer and

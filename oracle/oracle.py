@@ -102,6 +102,10 @@ def _declare(L):
     L.vio_init_nnf.restype = i
     L.vio_upsample_nnf.argtypes = [_i32p, i, i, _u8p, _u8p, i, i, i, u32, u32, u32, u32, _i32p]
     L.vio_upsample_nnf.restype = i
+    L.vio_subsample_features_t.argtypes = [_f64p, i, i, i, i, i, i, i, i, _f64p]
+    L.vio_downsample_t.argtypes = [_f32p, _u8p, i, i, i, i, i, _f32p, _u8p]
+    L.vio_upsample_nnf_t.argtypes = [_i32p, i, i, i, _u8p, _u8p, i, i, i, i, u32, u32, u32, u32, _i32p]
+    L.vio_upsample_nnf_t.restype = i
     L.vio_ann.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p, i, i, i, d,
                           u32, u32, u32, u32]
     L.vio_ann.restype = C.c_longlong
@@ -189,25 +193,28 @@ def texture_features(rgb, hole, nu_side):
     return out
 
 
-def subsample_features(T0, level, Wl, Hl):
-    """Eq. 8: T^l(x, y, t) = T(2^l x, 2^l y, t)."""
+def subsample_features(T0, level, Wl, Hl, Tl=None, tsub=False):
+    """Eq. 8: T^l(x, y, t) = T(2^l x, 2^l y, t); with tsub T(2^l x, 2^l y, 2^l t)."""
     T0 = _c(T0, np.float64)
     T, H0, W0, _ = T0.shape
-    out = np.zeros((T, Hl, Wl, 2), np.float64)
-    lib().vio_subsample_features(T0.reshape(-1), W0, H0, T, int(level), Wl, Hl, out.reshape(-1))
+    Tl = T if Tl is None else Tl
+    out = np.zeros((Tl, Hl, Wl, 2), np.float64)
+    lib().vio_subsample_features_t(T0.reshape(-1), W0, H0, T, int(level), Wl, Hl, Tl, 1 if tsub else 0,
+                                   out.reshape(-1))
     return out
 
 
-def downsample(x, hole):
-    """One level of the colour / occlusion pyramids."""
+def downsample(x, hole, tsub=False):
+    """One level of the colour / occlusion pyramids (2x2, or 2x2x2 with tsub)."""
     x = _c(x, np.float32)
     hole = _c(hole, np.uint8)
     T, Hf, Wf, Cn = x.shape
     Wc, Hc = (Wf + 1) // 2, (Hf + 1) // 2
-    xc = np.zeros((T, Hc, Wc, Cn), np.float32)
-    hc = np.zeros((T, Hc, Wc), np.uint8)
-    lib().vio_downsample(x.reshape(-1), hole.reshape(-1), Wf, Hf, T, Cn, xc.reshape(-1),
-                         hc.reshape(-1))
+    Tc = (T + 1) // 2 if tsub else T
+    xc = np.zeros((Tc, Hc, Wc, Cn), np.float32)
+    hc = np.zeros((Tc, Hc, Wc), np.uint8)
+    lib().vio_downsample_t(x.reshape(-1), hole.reshape(-1), Wf, Hf, T, Cn, 1 if tsub else 0, xc.reshape(-1),
+                           hc.reshape(-1))
     return xc, hc
 
 
@@ -222,15 +229,15 @@ def init_nnf(target, dtilde, key, tag_word, clip=0):
     return phi
 
 
-def upsample_nnf(phi_c, target_f, dtilde_f, key, tag_word, clip=0):
+def upsample_nnf(phi_c, target_f, dtilde_f, key, tag_word, clip=0, tsub=False):
     phi_c = _c(phi_c, np.int32)
     Tc, Hc, Wc, _ = phi_c.shape
     target_f = _c(target_f, np.uint8)
     Wf, Hf, T = _dims(target_f)
     phi_f = np.zeros((T, Hf, Wf, 3), np.int32)
-    rc = lib().vio_upsample_nnf(phi_c.reshape(-1), Wc, Hc, target_f.reshape(-1),
-                                _c(dtilde_f, np.uint8).reshape(-1), Wf, Hf, T,
-                                key[0], key[1], tag_word, clip, phi_f.reshape(-1))
+    rc = lib().vio_upsample_nnf_t(phi_c.reshape(-1), Wc, Hc, Tc, target_f.reshape(-1),
+                                  _c(dtilde_f, np.uint8).reshape(-1), Wf, Hf, T, 1 if tsub else 0,
+                                  key[0], key[1], tag_word, clip, phi_f.reshape(-1))
     if rc != 0:
         raise ValueError("no valid source patch (D~ is empty)")
     return phi_f
@@ -329,6 +336,7 @@ class Params:
     fixed_outer: object = None  # None, an int, or a list per level (coarsest first)
     rs_mode: int = 0           # 0: Eq. 3 (one radius per k); 1: every radius r_max rho^i >= 1
     sub_sweeps: int = 1        # propagation sweeps before each random search
+    time_subsample: bool = False  # halve the frames at every pyramid level too (Sec. 3.6 option)
 
     @property
     def key(self):
@@ -357,10 +365,11 @@ def sqrt_lambda(lam):
     return float(np.float32(math.sqrt(lam)))
 
 
-def build_pyramid(rgb, mask, levels, use_texture=True, lam=50.0):
+def build_pyramid(rgb, mask, levels, use_texture=True, lam=50.0, tsub=False):
     """ImagePyramid, TextureFeaturePyramid and OcclusionPyramid of Algorithm 4
     (level 0 = finest). Channels: R, G, B (+ sqrt(lambda) T_x, sqrt(lambda) T_y).
-    Values on occluded voxels are unknown and set to 0."""
+    Values on occluded voxels are unknown and set to 0. tsub: the temporal
+    subsampling option (frames halved at every level too)."""
     rgb = _c(rgb, np.float32)
     mask = _c(mask, np.uint8)
     T0 = None
@@ -371,10 +380,10 @@ def build_pyramid(rgb, mask, levels, use_texture=True, lam=50.0):
     col, hole = rgb.copy(), mask.copy()
     for lv in range(levels):
         if lv > 0:
-            col, hole = downsample(col, hole)
+            col, hole = downsample(col, hole, tsub)
         T, H, W, _ = col.shape
         if use_texture:
-            Tl = subsample_features(T0, lv, W, H)
+            Tl = subsample_features(T0, lv, W, H, T, tsub)
             x = np.concatenate([col, (s * Tl).astype(np.float32)], axis=-1)
         else:
             x = col.copy()
@@ -465,11 +474,11 @@ def next_level(coarse, fine, prm, fine_index):
     distances of Eq. 5 need a video to compare); distances; reconstruction of
     u and T at the finer level (Eq. 4/5, Eq. 9)."""
     fine.phi = upsample_nnf(coarse.phi, fine.htilde, fine.dtilde, prm.key,
-                            tag(PURPOSE_UPSAMPLE, fine_index), prm.clip)
+                            tag(PURPOSE_UPSAMPLE, fine_index), prm.clip, prm.time_subsample)
     fine.d2 = np.full(fine.hole.shape, np.inf, np.float32)
     T, Hf, Wf, _ = fine.x.shape
     tt, yy, xx = np.nonzero(fine.hole)
-    fine.x[tt, yy, xx] = coarse.x[tt, yy // 2, xx // 2]
+    fine.x[tt, yy, xx] = coarse.x[tt // 2 if prm.time_subsample else tt, yy // 2, xx // 2]
     ev = _rescore(fine, prm)
     fine.x, _ = vote(fine.x, fine.hole, fine.htilde, fine.phi, fine.d2,
                      weighted=prm.weighted, n_diff=3)
@@ -480,7 +489,7 @@ def inpaint(rgb, mask, levels, use_texture=True, prm=None, return_levels=False):
     """Algorithm 4 (the affine realignment of Algorithm 2 is not part of this
     path). Returns the inpainted RGB video float32 [T][H][W][3]."""
     prm = prm or Params()
-    pyr = build_pyramid(rgb, mask, levels, use_texture, prm.lam)
+    pyr = build_pyramid(rgb, mask, levels, use_texture, prm.lam, prm.time_subsample)
     L = levels
     top = pyr[L - 1]
     if top.dtilde.sum() == 0:

@@ -319,49 +319,68 @@ void vio_texture_features(const float *rgb, const uint8_t *hole, int W, int H, i
 }
 
 /* Texture pyramid, Eq. 8: T^l(x, y, t) = T(2^l x, 2^l y, t), no filtering. */
-void vio_subsample_features(const double *T0, int W0, int H0, int T, int level,
-                            int Wl, int Hl, double *Tl)
+/* Eq. 8 with the temporal subsampling option: T^l(x, y, t) = T(2^l x, 2^l y,
+ * t), or T(2^l x, 2^l y, 2^l t) when tsub (Tl frames at level l). */
+void vio_subsample_features_t(const double *T0, int W0, int H0, int T, int level,
+                              int Wl, int Hl, int Tl, int tsub, double *out)
 {
-    for (int t = 0; t < T; ++t)
+    (void)T;
+    for (int t = 0; t < Tl; ++t)
         for (int y = 0; y < Hl; ++y)
             for (int x = 0; x < Wl; ++x) {
-                size_t src = vidx(x << level, y << level, t, W0, H0);
+                size_t src = vidx(x << level, y << level, tsub ? (t << level) : t, W0, H0);
                 size_t dst = vidx(x, y, t, Wl, Hl);
-                Tl[2 * dst] = T0[2 * src];
-                Tl[2 * dst + 1] = T0[2 * src + 1];
+                out[2 * dst] = T0[2 * src];
+                out[2 * dst + 1] = T0[2 * src + 1];
             }
 }
 
-/* Colour and occlusion pyramids (Algorithm 4, "ImagePyramid" and
- * "OcclusionPyramid"; no temporal subsampling, Sec. 3.6). A coarse voxel is
- * occluded when any of its (up to) 2x2 children is; a known coarse voxel is
- * the mean of its children. Coarse size is ceil(W/2) x ceil(H/2) x T. */
-void vio_downsample(const float *xf, const uint8_t *hole_f, int Wf, int Hf, int T, int C,
-                    float *xc, uint8_t *hole_c)
+void vio_subsample_features(const double *T0, int W0, int H0, int T, int level,
+                            int Wl, int Hl, double *Tl)
 {
-    int Wc = (Wf + 1) / 2, Hc = (Hf + 1) / 2;
-    for (int t = 0; t < T; ++t)
+    vio_subsample_features_t(T0, W0, H0, T, level, Wl, Hl, T, 0, Tl);
+}
+
+/* Colour and occlusion pyramids (Algorithm 4, "ImagePyramid" and
+ * "OcclusionPyramid"). A coarse voxel is occluded when any of its children
+ * is; a known coarse voxel is the mean of its children. Children: the (up
+ * to) 2x2 spatial ones of the same frame (Sec. 3.6: no temporal
+ * subsampling), or with tsub the (up to) 2x2x2 of frames 2t and 2t+1 (the
+ * option the paper uses once, for long occlusions). Coarse size ceil(W/2) x
+ * ceil(H/2) x (tsub ? ceil(T/2) : T). */
+void vio_downsample_t(const float *xf, const uint8_t *hole_f, int Wf, int Hf, int Tf, int C, int tsub,
+                      float *xc, uint8_t *hole_c)
+{
+    int Wc = (Wf + 1) / 2, Hc = (Hf + 1) / 2, Tc = tsub ? (Tf + 1) / 2 : Tf;
+    for (int t = 0; t < Tc; ++t)
         for (int y = 0; y < Hc; ++y)
             for (int x = 0; x < Wc; ++x) {
                 size_t o = vidx(x, y, t, Wc, Hc);
                 int occl = 0, n = 0;
                 double acc[8] = {0};
-                for (int j = 0; j < 2; ++j)
-                    for (int i = 0; i < 2; ++i) {
-                        int fx = 2 * x + i, fy = 2 * y + j;
-                        if (fx >= Wf || fy >= Hf)
-                            continue;
-                        size_t f = vidx(fx, fy, t, Wf, Hf);
-                        if (hole_f[f])
-                            occl = 1;
-                        for (int c = 0; c < C && c < 8; ++c)
-                            acc[c] += (double)xf[f * (size_t)C + c];
-                        ++n;
-                    }
+                for (int k = 0; k <= (tsub ? 1 : 0); ++k)
+                    for (int j = 0; j < 2; ++j)
+                        for (int i = 0; i < 2; ++i) {
+                            int fx = 2 * x + i, fy = 2 * y + j, ft = tsub ? 2 * t + k : t;
+                            if (fx >= Wf || fy >= Hf || ft >= Tf)
+                                continue;
+                            size_t f = vidx(fx, fy, ft, Wf, Hf);
+                            if (hole_f[f])
+                                occl = 1;
+                            for (int c = 0; c < C && c < 8; ++c)
+                                acc[c] += (double)xf[f * (size_t)C + c];
+                            ++n;
+                        }
                 hole_c[o] = (uint8_t)occl;
                 for (int c = 0; c < C; ++c)
                     xc[o * (size_t)C + c] = occl ? 0.0f : (float)(acc[c] / n);
             }
+}
+
+void vio_downsample(const float *xf, const uint8_t *hole_f, int Wf, int Hf, int T, int C,
+                    float *xc, uint8_t *hole_c)
+{
+    vio_downsample_t(xf, hole_f, Wf, Hf, T, C, 0, xc, hole_c);
 }
 
 /* ------------------------------------------------------------------------
@@ -405,13 +424,16 @@ int vio_init_nnf(const uint8_t *target, const uint8_t *dtilde, int W, int H, int
 
 /* Level transition (Sec. 3.6, Algorithm 4 "UpSample(phi, 2)"): the fine voxel
  * (x, y, t) takes the shift of its coarse parent (x/2, y/2, t) with the spatial
- * components doubled (nearest-neighbour upsampling; no temporal scaling). A
- * shift that does not land in the fine D~ is redrawn uniformly from D~. */
-int vio_upsample_nnf(const int32_t *phi_c, int Wc, int Hc, const uint8_t *target_f,
-                     const uint8_t *dtilde_f, int Wf, int Hf, int T,
-                     uint32_t key0, uint32_t key1, uint32_t tag, uint32_t clip, int32_t *phi_f)
+ * components doubled (nearest-neighbour upsampling; no temporal scaling), or,
+ * with the temporal subsampling option (tsub), of the parent (x/2, y/2, t/2)
+ * with all three components doubled. A shift that does not land in the fine
+ * D~ is redrawn uniformly from D~. */
+int vio_upsample_nnf_t(const int32_t *phi_c, int Wc, int Hc, int Tc, const uint8_t *target_f,
+                       const uint8_t *dtilde_f, int Wf, int Hf, int Tf, int tsub,
+                       uint32_t key0, uint32_t key1, uint32_t tag, uint32_t clip, int32_t *phi_f)
 {
-    size_t V = (size_t)Wf * Hf * T, nS;
+    (void)Tc;
+    size_t V = (size_t)Wf * Hf * Tf, nS;
     size_t *src = source_list(dtilde_f, V, &nS);
     if (nS == 0) { free(src); return -1; }
     for (size_t p = 0; p < V; ++p) {
@@ -419,10 +441,10 @@ int vio_upsample_nnf(const int32_t *phi_c, int Wc, int Hc, const uint8_t *target
             continue;
         int px, py, pt;
         coords(p, Wf, Hf, &px, &py, &pt);
-        size_t P = vidx(px / 2, py / 2, pt, Wc, Hc);
-        int dx = 2 * phi_c[3 * P], dy = 2 * phi_c[3 * P + 1], dt = phi_c[3 * P + 2];
+        size_t P = vidx(px / 2, py / 2, tsub ? pt / 2 : pt, Wc, Hc);
+        int dx = 2 * phi_c[3 * P], dy = 2 * phi_c[3 * P + 1], dt = (tsub ? 2 : 1) * phi_c[3 * P + 2];
         int sx = px + dx, sy = py + dy, st = pt + dt;
-        if (!(inside(sx, sy, st, Wf, Hf, T) && dtilde_f[vidx(sx, sy, st, Wf, Hf)])) {
+        if (!(inside(sx, sy, st, Wf, Hf, Tf) && dtilde_f[vidx(sx, sy, st, Wf, Hf)])) {
             uint32_t w[4];
             draw((uint32_t)p, tag, clip, key0, key1, w);
             size_t s = src[vio_uniform_index(w[0], (uint32_t)nS)];
@@ -433,6 +455,14 @@ int vio_upsample_nnf(const int32_t *phi_c, int Wc, int Hc, const uint8_t *target
     }
     free(src);
     return 0;
+}
+
+int vio_upsample_nnf(const int32_t *phi_c, int Wc, int Hc, const uint8_t *target_f,
+                     const uint8_t *dtilde_f, int Wf, int Hf, int T,
+                     uint32_t key0, uint32_t key1, uint32_t tag, uint32_t clip, int32_t *phi_f)
+{
+    return vio_upsample_nnf_t(phi_c, Wc, Hc, T, target_f, dtilde_f, Wf, Hf, T, 0, key0, key1, tag, clip,
+                              phi_f);
 }
 
 /* ------------------------------------------------------------------------

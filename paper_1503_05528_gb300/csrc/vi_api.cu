@@ -152,6 +152,7 @@ vi_status check_config(vi_ctx *ctx, const vi_config *c)
 {
     if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
         c->rs_mode < 0 || c->rs_mode > 1 || c->sub_sweeps < 1 || c->sub_sweeps > 16 ||
+        c->time_subsample < 0 || c->time_subsample > 1 ||
         c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
           c->lanes_per_target == 4 || c->lanes_per_target == 8))
@@ -359,6 +360,7 @@ void vi_config_default(vi_config *cfg)
     cfg->stream_priority = 0;
     cfg->rs_mode = 0;
     cfg->sub_sweeps = 1;
+    cfg->time_subsample = 0;
 }
 
 vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)
@@ -495,13 +497,13 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
     TRY(dalloc(ctx, &ctx->block_counts, sizeof(int) * (size_t)(compact_blocks(ctx->V0) + 1)));
 
     ctx->lv.assign(L, Level());
-    int w = W, h = H;
+    int w = W, h = H, tl = T;
     for (int l = 0; l < L; ++l) {
         Level &lv = ctx->lv[l];
         lv.W = w;
         lv.H = h;
-        lv.T = T;
-        lv.V = w * h * T;
+        lv.T = tl;
+        lv.V = w * h * tl;
         const size_t V = (size_t)lv.V;
         TRY(dalloc(ctx, &lv.x4, V * sizeof(float4)));
         if (ctx->c5)
@@ -521,6 +523,8 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
         }
         w = (w + 1) / 2;
         h = (h + 1) / 2;
+        if (ctx->cfg.time_subsample)
+            tl = (tl + 1) / 2;
     }
     // evaluation / launch / time counters accumulate over the context's life;
     // the per-run counters restart with every upload
@@ -568,7 +572,8 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
     launch_codes(ctx->lv[0].view(), ctx->tmpA, ctx->tmpB, st);
     CK_LAUNCH();
     for (int l = 1; l < ctx->L; ++l) {
-        launch_downsample(ctx->lv[l - 1].view(), ctx->lv[l].view(), l, ctx->T0, W, H, s, ctx->c5, st);
+        launch_downsample(ctx->lv[l - 1].view(), ctx->lv[l].view(), l, ctx->T0, W, H, s, ctx->c5,
+                          ctx->cfg.time_subsample != 0, st);
         CK_LAUNCH();
         launch_codes(ctx->lv[l].view(), ctx->tmpA, ctx->tmpB, st);
         CK_LAUNCH();
@@ -777,11 +782,12 @@ vi_status vi_next_level(vi_ctx *ctx, int level)
         return fail(ctx, VI_ERR_ARG, "vi_next_level: level must be in [1, L)");
     Level &c = ctx->lv[level];
     Level &f = ctx->lv[level - 1];
-    launch_upsample_nnf(c.view(), c.phi[0], f.view(), f.targets, f.nT, f.sources, f.nS, f.phi[0],
+    launch_upsample_nnf(c.view(), c.phi[0], f.view(), ctx->cfg.time_subsample != 0, f.targets, f.nT, f.sources,
+                        f.nS, f.phi[0],
                         (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull), (uint32_t)(ctx->cfg.seed >> 32),
                         make_tag(PURPOSE_UPSAMPLE, level - 1, 0), ctx->cfg.clip, ctx->stream);
     CK_LAUNCH();
-    launch_provisional_fill(c.view(), f.view(), f.holes, f.nH, ctx->c5, ctx->stream);
+    launch_provisional_fill(c.view(), f.view(), f.holes, f.nH, ctx->c5, ctx->cfg.time_subsample != 0, ctx->stream);
     CK_LAUNCH();
     TRY(vi_rescore(ctx, level - 1));
     return vote_level(ctx, level - 1, nullptr);

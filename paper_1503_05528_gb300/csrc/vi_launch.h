@@ -29,8 +29,9 @@ void launch_level0_channels(const float *rgb, const uint8_t *hole, const float2 
                             float sqrt_lambda, bool c5, LevelView L, cudaStream_t st);
 // Coarse level from the finer one: 2x2 mean of known children, OR of the
 // occlusion, texture features subsampled from T0 (Eq. 8).
+// tsub: the temporal subsampling option (coarse frames = ceil(fine / 2)).
 void launch_downsample(LevelView fine, LevelView coarse, int level, const float2 *T0, int W0,
-                       int H0, float sqrt_lambda, bool c5, cudaStream_t st);
+                       int H0, float sqrt_lambda, bool c5, bool tsub, cudaStream_t st);
 // code = H | H~ | D~ of a level from its occlusion bits (3 separable dilations).
 void launch_codes(LevelView L, uint8_t *tmp_a, uint8_t *tmp_b, cudaStream_t st);
 // Raster-ordered compaction of {v : (flags[v] & bits) != 0} into list.
@@ -81,11 +82,11 @@ void launch_copy_targets(const int *targets, int nT, const Shift *phi_src, const
 void launch_init_nnf(LevelView L, const int *targets, int nT, const int *sources, int nS,
                      Shift *phi, uint32_t key0, uint32_t key1, uint32_t tag, uint32_t clip,
                      cudaStream_t st);
-void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, const int *targets_f,
-                         int nT, const int *sources_f, int nS, Shift *phi_f, uint32_t key0,
+void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, bool tsub,
+                         const int *targets_f, int nT, const int *sources_f, int nS, Shift *phi_f, uint32_t key0,
                          uint32_t key1, uint32_t tag, uint32_t clip, cudaStream_t st);
 void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH,
-                             bool c5, cudaStream_t st);
+                             bool c5, bool tsub, cudaStream_t st);
 void launch_patch_dist(LevelView L, const int *pairs, int n, float *out, bool c5, cudaStream_t st);
 
 // ---- reconstruction (vi_vote.cu) -----------------------------------------------

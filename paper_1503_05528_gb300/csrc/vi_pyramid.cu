@@ -166,9 +166,12 @@ void launch_level0_channels(const float *rgb, const uint8_t *hole, const float2 
     k_level0_channels<<<grid_for(L.V, 256), 256, 0, st>>>(rgb, hole, T0, sqrt_lambda, c5 ? 1 : 0, L);
 }
 
-// Colour / occlusion pyramid step and Eq. 8 subsampling of the features.
+// Colour / occlusion pyramid step and Eq. 8 subsampling of the features:
+// 2x2 children of the same frame, or with tsub (the temporal subsampling
+// option) 2x2x2 children of frames 2t, 2t+1, the features then sampled at
+// frame 2^level t.
 __global__ void k_downsample(LevelView F, LevelView Cs, int level, const float2 *__restrict__ T0,
-                             int W0, int H0, float s, int c5)
+                             int W0, int H0, float s, int c5, int tsub)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < Cs.V;
          v += (long long)gridDim.x * blockDim.x) {
@@ -178,18 +181,19 @@ __global__ void k_downsample(LevelView F, LevelView Cs, int level, const float2 
         bool occl = false;
         int n = 0;
         float r = 0.f, g = 0.f, b = 0.f;
-        for (int j = 0; j < 2; ++j)
-            for (int i = 0; i < 2; ++i) {
-                const int fx = 2 * x + i, fy = 2 * y + j;
-                if (fx >= F.W || fy >= F.H)
-                    continue;
-                const long long f = (long long)t * F.HW + (long long)fy * F.W + fx;
-                if (F.code[f] & CODE_HOLE)
-                    occl = true;
-                const float4 a = F.x4[f];
-                r += a.x; g += a.y; b += a.z;
-                ++n;
-            }
+        for (int k = 0; k <= tsub; ++k)
+            for (int j = 0; j < 2; ++j)
+                for (int i = 0; i < 2; ++i) {
+                    const int fx = 2 * x + i, fy = 2 * y + j, ft = tsub ? 2 * t + k : t;
+                    if (fx >= F.W || fy >= F.H || ft >= F.T)
+                        continue;
+                    const long long f = (long long)ft * F.HW + (long long)fy * F.W + fx;
+                    if (F.code[f] & CODE_HOLE)
+                        occl = true;
+                    const float4 a = F.x4[f];
+                    r += a.x; g += a.y; b += a.z;
+                    ++n;
+                }
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
         float o1 = 0.0f;
         if (!occl) {
@@ -197,7 +201,8 @@ __global__ void k_downsample(LevelView F, LevelView Cs, int level, const float2 
             out.y = g / (float)n;
             out.z = b / (float)n;
             if (c5) {
-                const long long q = (long long)t * W0 * H0 + (long long)(y << level) * W0 + (x << level);
+                const int t0 = tsub ? (t << level) : t;
+                const long long q = (long long)t0 * W0 * H0 + (long long)(y << level) * W0 + (x << level);
                 const float2 tq = T0[q];
                 out.w = s * tq.x;
                 o1 = s * tq.y;
@@ -211,11 +216,11 @@ __global__ void k_downsample(LevelView F, LevelView Cs, int level, const float2 
 }
 
 void launch_downsample(LevelView fine, LevelView coarse, int level, const float2 *T0, int W0, int H0,
-                       float sqrt_lambda, bool c5, cudaStream_t st)
+                       float sqrt_lambda, bool c5, bool tsub, cudaStream_t st)
 {
     VI_COUNT_LAUNCH();
     k_downsample<<<grid_for(coarse.V, 256), 256, 0, st>>>(fine, coarse, level, T0, W0, H0,
-                                                           sqrt_lambda, c5 ? 1 : 0);
+                                                           sqrt_lambda, c5 ? 1 : 0, tsub ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------

@@ -413,9 +413,11 @@ void launch_init_nnf(LevelView L, const int *targets, int nT, const int *sources
                                                     clip);
 }
 
-// Sec. 3.6: phi_fine(x, y, t) = (2 dx, 2 dy, dt) of phi_coarse(x/2, y/2, t);
-// a shift that does not land in the fine D~ is redrawn uniformly from D~.
-__global__ void k_upsample_nnf(LevelView C, const Shift *__restrict__ phi_c, LevelView F,
+// Sec. 3.6: phi_fine(x, y, t) = (2 dx, 2 dy, dt) of phi_coarse(x/2, y/2, t)
+// (with tsub, the temporal subsampling option: (2 dx, 2 dy, 2 dt) of
+// phi_coarse(x/2, y/2, t/2)); a shift that does not land in the fine D~ is
+// redrawn uniformly from D~.
+__global__ void k_upsample_nnf(LevelView C, const Shift *__restrict__ phi_c, LevelView F, int tsub,
                                const int *__restrict__ targets, int nT, const int *__restrict__ sources,
                                int nS, Shift *__restrict__ phi_f, uint32_t k0, uint32_t k1, uint32_t tag,
                                uint32_t clip)
@@ -426,8 +428,8 @@ __global__ void k_upsample_nnf(LevelView C, const Shift *__restrict__ phi_c, Lev
     const int p = targets[i];
     int px, py, pt;
     decode(p, F.W, F.HW, px, py, pt);
-    const Shift pc = phi_c[pt * C.HW + (py >> 1) * C.W + (px >> 1)];
-    int dx = 2 * pc.dx, dy = 2 * pc.dy, dt = pc.dt;
+    const Shift pc = phi_c[(tsub ? pt >> 1 : pt) * C.HW + (py >> 1) * C.W + (px >> 1)];
+    int dx = 2 * pc.dx, dy = 2 * pc.dy, dt = tsub ? 2 * pc.dt : pc.dt;
     if (source_of(F, px, py, pt, dx, dy, dt) < 0) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)p, tag, clip, 0u), k0, k1);
         const int s = sources[uniform_index(w.x, (uint32_t)nS)];
@@ -445,19 +447,20 @@ __global__ void k_upsample_nnf(LevelView C, const Shift *__restrict__ phi_c, Lev
     phi_f[p] = c;
 }
 
-void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, const int *targets_f,
+void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, bool tsub, const int *targets_f,
                          int nT, const int *sources_f, int nS, Shift *phi_f, uint32_t key0, uint32_t key1,
                          uint32_t tag, uint32_t clip, cudaStream_t st)
 {
     if (nT <= 0)
         return;
     VI_COUNT_LAUNCH();
-    k_upsample_nnf<<<blocks_for(nT, 256), 256, 0, st>>>(coarse, phi_c, fine, targets_f, nT, sources_f, nS,
-                                                        phi_f, key0, key1, tag, clip);
+    k_upsample_nnf<<<blocks_for(nT, 256), 256, 0, st>>>(coarse, phi_c, fine, tsub ? 1 : 0, targets_f, nT,
+                                                        sources_f, nS, phi_f, key0, key1, tag, clip);
 }
 
 // Occluded voxels of the finer level take their coarse parent's channels.
-__global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restrict__ holes, int nH, int c5)
+__global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restrict__ holes, int nH, int c5,
+                                   int tsub)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nH)
@@ -465,7 +468,7 @@ __global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restri
     const int p = holes[i];
     int px, py, pt;
     decode(p, F.W, F.HW, px, py, pt);
-    const int q = pt * C.HW + (py >> 1) * C.W + (px >> 1);
+    const int q = (tsub ? pt >> 1 : pt) * C.HW + (py >> 1) * C.W + (px >> 1);
     const float4 a = C.x4[q];
     F.x4[p] = a;
     if (c5)
@@ -474,13 +477,14 @@ __global__ void k_provisional_fill(LevelView C, LevelView F, const int *__restri
         shadow_store_raise(F, p, a);
 }
 
-void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH, bool c5,
+void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH, bool c5, bool tsub,
                              cudaStream_t st)
 {
     if (nH <= 0)
         return;
     VI_COUNT_LAUNCH();
-    k_provisional_fill<<<blocks_for(nH, 256), 256, 0, st>>>(coarse, fine, holes_f, nH, c5 ? 1 : 0);
+    k_provisional_fill<<<blocks_for(nH, 256), 256, 0, st>>>(coarse, fine, holes_f, nH, c5 ? 1 : 0,
+                                                            tsub ? 1 : 0);
 }
 
 template <bool C5>

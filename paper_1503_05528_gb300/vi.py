@@ -41,7 +41,8 @@ class ViConfig(C.Structure):
                 ("levels", C.c_int), ("max_outer", C.c_int), ("stop", C.c_float),
                 ("weighted", C.c_int), ("use_texture", C.c_int), ("storage", C.c_int),
                 ("seed", C.c_uint64), ("clip", C.c_uint32), ("lanes_per_target", C.c_int),
-                ("stream_priority", C.c_int), ("rs_mode", C.c_int), ("sub_sweeps", C.c_int)]
+                ("stream_priority", C.c_int), ("rs_mode", C.c_int), ("sub_sweeps", C.c_int),
+                ("time_subsample", C.c_int)]
 
 
 class ViStats(C.Structure):

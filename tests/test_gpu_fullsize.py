@@ -153,3 +153,40 @@ def test_bench_workload_full_size():
 
 def test_hd_workload_full_size():
     _check_run("layered_1280x720x100", 120, 2)
+
+
+def _golden_seq_energy():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "seq_energy_layered_320x240x60.txt")
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, *v = line.split()
+            vals[k] = [float(x) for x in v]
+    return vals
+
+
+def test_full_run_energy_within_2pct_of_the_sequential_oracle():
+    # the whole method on the bench workload (parallel Jacobi sweep) against
+    # the oracle's sequential sweep (Algorithm 1 as printed), compared by the
+    # Eq. 1 energy over H at level 0 after the last iteration and before the
+    # final step, both evaluated by the oracle (the stored value was written
+    # by tests/golden/make_seq_energy.py)
+    gold = _golden_seq_energy()
+    clip = bench.make_clip(0, "layered_320x240x60")
+    with vi.Context(levels=clip.levels, use_texture=1, seed=1503) as ctx:
+        ctx.upload(clip.rgb, clip.mask)
+        ctx.prepare()
+        for level in range(clip.levels - 1, -1, -1):
+            ctx.iterate(level)
+            if level > 0:
+                ctx.next_level(level)
+        x = ctx.get_channels(0)
+        phi, _ = ctx.get_nnf(0)
+        code = ctx.get_masks(0)
+    e_h, e_ht = O.energy(x, code & 1, (code >> 1) & 1, phi)
+    assert e_h <= 1.02 * gold["E_H"][0], (e_h, gold["E_H"][0])
+    assert e_ht <= 1.02 * gold["E_Htilde"][0], (e_ht, gold["E_Htilde"][0])

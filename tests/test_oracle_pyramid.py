@@ -176,3 +176,75 @@ def test_pyramid_known_coarse_voxels_have_known_children():
             assert blk.sum() == 0
         assert coarse.x.shape[-1] == 5
         assert (coarse.x[coarse.hole == 1] == 0).all()
+
+
+# ---- the temporal subsampling option (Sec. 3.6, used once in the paper) ----
+
+def test_temporal_downsample_box_mean_and_or():
+    rng = np.random.default_rng(11)
+    for T, H, W in [(7, 6, 5), (8, 4, 4), (1, 5, 7)]:
+        x = rng.random((T, H, W, 3)).astype(np.float32)
+        hole = _random_mask((T, H, W), 0.1, T)
+        xc, hc = O.downsample(x, hole, tsub=True)
+        assert xc.shape == ((T + 1) // 2, (H + 1) // 2, (W + 1) // 2, 3)
+        for t, y, xx in itertools.product(range(xc.shape[0]), range(xc.shape[1]), range(xc.shape[2])):
+            kids = [(2 * t + k, 2 * y + j, 2 * xx + i) for k in (0, 1) for j in (0, 1) for i in (0, 1)]
+            kids = [q for q in kids if q[0] < T and q[1] < H and q[2] < W]
+            occl = any(hole[q] for q in kids)
+            assert hc[t, y, xx] == int(occl)
+            if not occl:
+                want = np.mean([x[q].astype(np.float64) for q in kids], axis=0)
+                np.testing.assert_allclose(xc[t, y, xx], want, rtol=0, atol=2e-7)
+            else:
+                assert (xc[t, y, xx] == 0).all()
+
+
+def test_temporal_pyramid_sizes_constants_and_features():
+    T, H, W = 9, 20, 24
+    rgb = np.full((T, H, W, 3), 0.25, np.float32)
+    hole = np.zeros((T, H, W), np.uint8)
+    hole[3:5, 8:12, 9:14] = 1
+    pyr = O.build_pyramid(rgb, hole, 3, True, tsub=True)
+    assert [lv.x.shape[:3] for lv in pyr] == [(9, 20, 24), (5, 10, 12), (3, 5, 6)]
+    for lv in pyr:
+        known = lv.hole == 0
+        assert np.allclose(lv.x[known][:, :3], 0.25) and np.allclose(lv.x[known][:, 3:], 0.0)
+    # features are sampled at (2^l x, 2^l y, 2^l t) of the full-resolution field
+    rng = np.random.default_rng(3)
+    T0 = rng.random((T, H, W, 2))
+    sub = O.subsample_features(T0, 2, 6, 5, 3, tsub=True)
+    for t, y, x in itertools.product(range(3), range(5), range(6)):
+        assert (sub[t, y, x] == T0[4 * t, 4 * y, 4 * x]).all()
+    assert (O.subsample_features(T0, 1, 12, 10) == T0[:, ::2, ::2]).all()
+
+
+def test_temporal_upsampling_doubles_all_components():
+    T, H, W = 12, 16, 16
+    hole = np.zeros((T, H, W), np.uint8)
+    hole[5:7, 6:10, 6:10] = 1
+    ht, dt = O.masks(hole)
+    phic = np.zeros(((T + 1) // 2, H // 2, W // 2, 3), np.int32)
+    phic[...] = (2, -1, 1)
+    f = O.upsample_nnf(phic, ht, dt, (1, 1), 7, tsub=True)
+    tt, yy, xx = np.nonzero(ht)
+    ok = [(t, y, x) for t, y, x in zip(tt, yy, xx)
+          if 0 <= t + 2 < T and 0 <= y - 2 < H and 0 <= x + 4 < W and dt[t + 2, y - 2, x + 4]]
+    assert ok
+    for q in ok:
+        assert tuple(f[q]) == (4, -2, 2)
+    # without the option dt is kept
+    phic2 = np.zeros((T, H // 2, W // 2, 3), np.int32)
+    phic2[...] = (2, -1, 1)
+    g = O.upsample_nnf(phic2, ht, dt, (1, 1), 7)
+    ok2 = [(t, y, x) for t, y, x in zip(tt, yy, xx)
+           if 0 <= t + 1 < T and 0 <= y - 2 < H and 0 <= x + 4 < W and dt[t + 1, y - 2, x + 4]]
+    for q in ok2:
+        assert tuple(g[q]) == (4, -2, 1)
+
+
+def test_temporal_option_full_run():
+    from paper_1503_05528_gb300 import synth
+    clip = synth.small_layered(W=48, H=40, T=12, levels=2, seed=1530)
+    out = O.inpaint(clip.rgb, clip.mask, 2, True, O.Params(time_subsample=True, fixed_outer=2))
+    assert np.isfinite(out).all()
+    assert np.array_equal(out[clip.mask == 0], clip.rgb[clip.mask == 0])
