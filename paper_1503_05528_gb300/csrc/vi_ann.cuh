@@ -178,7 +178,8 @@ __device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px,
 // writes phi_out / d_out. The three neighbours' shifts and their sources' set
 // codes are loaded together before any distance.
 template <bool C5, int G, bool PARTIAL, bool F16>
-__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub, unsigned gmask, StepCount &n)
+__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span, int sub, unsigned gmask,
+                                        StepCount &n)
 {
     const LevelView &L = a.L;
     const float D = F16 ? screen_d2bound(L) : 0.0f;
@@ -207,18 +208,21 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub,
     // candidates screened on five channels 52.6 and 661; the random one only,
     // screened on c0..c3, 39.4 and 462.
     //
-    // A neighbour whose shift did not change in the last two sweeps offers
-    // the candidate this target already judged two sweeps ago, in the same
-    // direction, on the same video (the channels are fixed within an ANN
-    // call): then it either lost (its distance was >= this target's distance,
-    // which has not grown since) or won and has been kept or beaten since.
-    // Either way it cannot be strictly better now, so it is counted and
-    // skipped without a gather; every decision stays the same.
+    // A neighbour whose shift did not change since this target last judged
+    // the same neighbour in the same direction (chg_span sweeps back: two with
+    // one sweep per iteration; with sub-sweeps one within an iteration, and
+    // the sub-sweeps of the iteration between plus one at its first) offers
+    // the candidate this target already judged, on the same video (the
+    // channels are fixed within an ANN call): then it either lost (its
+    // distance was >= this target's distance, which has not grown since) or
+    // won and has been kept or beaten since. Either way it cannot be strictly
+    // better now, so it is counted and skipped without a gather; every
+    // decision stays the same.
     Rejected rej;
-    const bool stale_ok = a.chg_in != nullptr && k >= 3;
-    const bool st0 = stale_ok && t0 && (a.chg_in[r0] & 3u) == 0;
-    const bool st1 = stale_ok && t1 && (a.chg_in[r1] & 3u) == 0;
-    const bool st2 = stale_ok && t2 && (a.chg_in[r2] & 3u) == 0;
+    const unsigned span_mask = a.chg_in != nullptr && span > 0 ? (1u << span) - 1u : 0u;
+    const bool st0 = span_mask && t0 && (a.chg_in[r0] & span_mask) == 0;
+    const bool st1 = span_mask && t1 && (a.chg_in[r1] & span_mask) == 0;
+    const bool st2 = span_mask && t2 && (a.chg_in[r2] & span_mask) == 0;
     const Shift start = cur;
     if (st0) {
         if (s0 >= 0)
@@ -267,7 +271,7 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int sub,
         a.d_out[p] = d;
         if (a.chg_out) {
             const bool changed = cur.dx != start.dx || cur.dy != start.dy || cur.dt != start.dt;
-            a.chg_out[p] = (uint8_t)((changed ? 1u : 0u) | ((a.chg_in[p] & 1u) << 1));
+            a.chg_out[p] = (uint8_t)((changed ? 1u : 0u) | ((unsigned)a.chg_in[p] << 1));
         }
     }
 }
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, PARTIAL>() * (2
     const unsigned gmask = group_mask<G>();
     StepCount n;
     if (i < a.nT)
-        ann_one<C5, G, PARTIAL, F16>(a, i, a.k, sub, gmask, n);
+        ann_one<C5, G, PARTIAL, F16>(a, i, a.k, a.chg_span, sub, gmask, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, sub);
 }
 
@@ -320,7 +324,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
         const int c = find_segment(prefix, n, g);
         const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
-        ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), k, sub, gmask, cnt);
+        // one sweep per iteration: the same neighbours were judged two sweeps ago
+        ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), k, k >= 3 ? 2 : 0, sub, gmask, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, sub);
 }

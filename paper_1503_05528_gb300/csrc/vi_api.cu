@@ -257,9 +257,18 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
             a.lanes = ctx->cfg.lanes_per_target;
             a.rs_mode = ctx->cfg.rs_mode;
             a.do_random = j == ctx->cfg.sub_sweeps - 1;
-            const bool flags = ctx->cfg.sub_sweeps == 1;
-            a.chg_in = flags ? l.chg[s & 1] : nullptr;
-            a.chg_out = flags ? l.chg[(s + 1) & 1] : nullptr;
+            // sweeps since the same targets judged the same neighbours in the
+            // same direction: the previous sub-sweep, or at the first
+            // sub-sweep of iteration k >= 3 the last of iteration k - 2
+            const int J = ctx->cfg.sub_sweeps;
+            int span = 0;
+            if (j > 0)
+                span = 1;
+            else if (k >= 3 && J + 1 <= 8)
+                span = J + 1;
+            a.chg_in = l.chg[s & 1];
+            a.chg_out = l.chg[(s + 1) & 1];
+            a.chg_span = span;
             TRY(step_launch(ctx, a));
         }
     }

@@ -316,6 +316,7 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
             a.clip = ctx->cfg.clip;
             a.rs_mode = ctx->cfg.rs_mode;
             a.do_random = 1;
+            a.chg_span = 0;     // the batch step kernel sets the span from k
             a.phi_in = l.phi[0];
             a.d_in = l.d2[0];
             a.phi_out = l.phi[1];

@@ -63,11 +63,15 @@ struct AnnArgs {
     int rs_mode;                   // 0: one random candidate at radius rmax rho^k (Eq. 3);
                                    // 1: one at every radius rmax rho^i >= 1, i = 0, 1, ...
     int do_random;                 // 0: propagation only (a sub-sweep before the last)
-    // Change flags (one sweep per PatchMatch iteration only): chg_in[r] bit 0
-    // = r's shift changed in the previous sweep, bit 1 = in the one before;
-    // chg_out receives the flags after this sweep. nullptr: no flags.
+    // Change history: chg_in[r] bit i = r's shift changed in the sweep i + 1
+    // sweeps back; chg_out receives the history after this sweep. chg_span >
+    // 0 (single-clip launches; the batch step derives it from k): the sweeps
+    // since this target last judged the same neighbours in the same
+    // direction; a neighbour unchanged over all of them offers no new
+    // candidate. nullptr / 0: no history.
     const uint8_t *chg_in;
     uint8_t *chg_out;
+    int chg_span;
 };
 // FP16 screening when a.L.h4 is set (full distance only; the partial
 // distance of Eq. 11 always runs on the FP32 channels).

