@@ -600,7 +600,8 @@ def run_serve(args):
     import torch
 
     from paper_1503_05528_gb300 import vi
-    from paper_1503_05528_gb300.serve import CudaBackend, Server, StreamBackend, poisson_arrivals, run_load
+    from paper_1503_05528_gb300.serve import (CudaBackend, NativeServer, Server, StreamBackend,
+                                              poisson_arrivals, run_load)
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -620,14 +621,17 @@ def run_serve(args):
     stream = torch.cuda.current_stream()
     budget = int(args.hbm_budget_gb * (1 << 30))
     storage = 1 if args.storage == "fp16" else 0
+    native = args.serve_backend == "native"
     if args.serve_backend == "batch":
         backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1, storage=storage)
+    elif native:
+        backend = NativeServer(budget, args.slots, levels=0, use_texture=1, storage=storage)
     else:
         backend = StreamBackend(max_workers=args.slots, device=local, levels=0, use_texture=1,
                                 storage=storage)
 
     # warm-up: every distinct clip once, alone (also settles the lane autotuner)
-    warm = Server(backend, budget, max_slots=args.slots)
+    warm = backend if native else Server(backend, budget, max_slots=args.slots)
     for i, c in enumerate(pool[:max(args.warmup, len(pool))]):
         warm.submit(c.rgb, c.mask, seed=1, clip=i)
         while warm.step():
@@ -648,7 +652,12 @@ def run_serve(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    srv = Server(backend, budget, max_slots=args.slots)
+    if native:
+        backend.done.clear()
+        backend.next_ticket, backend.max_concurrent, backend.rounds = 0, 0, 0
+        srv = backend
+    else:
+        srv = Server(backend, budget, max_slots=args.slots)
     wall, srv = run_load(srv, reqs, arrivals)
     torch.cuda.synchronize()
     if dist:
@@ -761,8 +770,9 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0, help="serving: admission budget")
     ap.add_argument("--slots", type=int, default=32, help="serving: most requests admitted at once")
-    ap.add_argument("--serve-backend", default="streams", choices=["streams", "batch"],
-                    help="serving: one stream per request by size priority, or one shared batch")
+    ap.add_argument("--serve-backend", default="streams", choices=["streams", "batch", "native"],
+                    help="serving: one stream per request by size priority (Python front), one shared batch, "
+                         "or the library server (vi_server_*)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
     ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],

@@ -298,6 +298,50 @@ vi_status vi_profile(vi_ctx *ctx, int enable);
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
 
 /* ---------------------------------------------------------------------------
+ * Serving (no counterpart in the paper, which runs one clip at a time). A
+ * server admits submitted requests in arrival order while their device
+ * footprint (vi_footprint_bytes) fits hbm_budget and one of max_slots worker
+ * threads is free; each admitted request runs alone (vi_run, one context) on a
+ * stream its context creates with a priority by size (requests under 2M / 8M
+ * / 32M voxels first), so the GPU interleaves requests and a small one is not
+ * held to the pace of a large one. The result is bit-identical to the same
+ * clip run alone. Thread-safe. The caller keeps rgb, mask and rgb_out (host
+ * or device memory, as ptr_is_device says) alive and untouched until the
+ * request is done or failed; device inputs must be complete when submitted
+ * (the worker reads them on its own stream), and a device result is complete
+ * when vi_server_poll reports the request done.
+ * ------------------------------------------------------------------------- */
+typedef struct vi_server vi_server;
+
+/* Errors: VI_ERR_ARG (zero budget, max_slots outside 1..256), VI_ERR_NO_DEVICE,
+ * VI_ERR_OOM. The server runs on the calling thread's current device. */
+vi_status vi_server_create(size_t hbm_budget, int max_slots, vi_server **out);
+
+/* Queues one request (cfg NULL: vi_config_default); *ticket identifies it.
+ * Non-blocking. Errors: VI_ERR_ARG, VI_ERR_TOO_LARGE (footprint above the
+ * budget), VI_ERR_STATE (server shutting down). */
+vi_status vi_server_submit(vi_server *s, const vi_config *cfg, const float *rgb, const uint8_t *mask, int W,
+                           int H, int T, int ptr_is_device, float *rgb_out, uint64_t *ticket);
+
+/* *done: 1 finished (rgb_out written), -1 failed, 0 queued or running. */
+vi_status vi_server_poll(vi_server *s, uint64_t ticket, int *done);
+
+/* Blocks until the request finishes or timeout_s elapses (timeout_s < 0:
+ * no limit); *done as in vi_server_poll. */
+vi_status vi_server_wait(vi_server *s, uint64_t ticket, double timeout_s, int *done);
+
+/* Forgets a finished or failed request and returns its status (the text of
+ * its error into err_buf, err_cap bytes, nullable). VI_ERR_STATE while it is
+ * still queued or running. */
+vi_status vi_server_release(vi_server *s, uint64_t ticket, char *err_buf, int err_cap);
+
+/* Requests waiting, requests running, footprint bytes admitted. Nullable. */
+vi_status vi_server_info(vi_server *s, int *queued, int *running, size_t *bytes_in_use);
+
+/* Lets running requests finish, fails the queued ones, joins the workers. */
+void vi_server_destroy(vi_server *s);
+
+/* ---------------------------------------------------------------------------
  * Affine realignment: Sec. 3.4, Algorithm 2 (AlignVideo) and the UnwarpVideo
  * step that ends Algorithm 4. The paper estimates the dominant affine motion
  * between successive frames with the robust method of Odobez and Bouthemy;

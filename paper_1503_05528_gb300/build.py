@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvi.so")
 SOURCES = ["vi_pyramid.cu", "vi_search.cu", "vi_search_h.cu", "vi_vote.cu", "vi_api.cu", "vi_batch.cu",
-           "vi_noalloc.cu", "vi_realign.cu"]
+           "vi_noalloc.cu", "vi_realign.cu", "vi_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -15,6 +15,10 @@ admitted requests:
   GPU interleaves the streams, so a small request is not held back to the pace
   of a large one.
 
+``NativeServer`` offers the same front (submit / step / pending / done) over
+the library's own server (``vi_server_*``), which does the admission and the
+per-request streams in C++ worker threads.
+
 Either way every job's result is bit-identical to running it alone. The
 scheduling logic is plain Python over a small backend interface
 (add / step / poll / fetch / remove / footprint), so it runs unchanged over
@@ -223,6 +227,59 @@ class Server:
 
     def latencies(self):
         return np.array([r.latency for r in self.done.values() if r.latency is not None])
+
+
+class NativeServer:
+    """The library's server (vi_server_*: FCFS admission by footprint and a
+    slot limit, one worker thread and one size-priority stream per running
+    request) behind the front of ``Server``; step() hands back finished
+    requests and waits briefly on the oldest running one."""
+
+    def __init__(self, hbm_budget, max_slots=8, clock=time.perf_counter, **cfg):
+        from . import vi
+        self.srv = vi.Server(hbm_budget, max_slots, **cfg)
+        self.clock = clock
+        self.running = {}            # native ticket -> Request
+        self.done = {}               # ticket -> Request
+        self.next_ticket = 0
+        self.max_concurrent = 0
+        self.rounds = 0
+
+    def submit(self, rgb, mask, arrival=None, **job):
+        req = Request(self.next_ticket, rgb, mask, job, self.clock() if arrival is None else arrival)
+        native = self.srv.submit(rgb, mask, **job)
+        req.admitted = self.clock()
+        self.next_ticket += 1
+        self.running[native] = req
+        return req.ticket
+
+    def step(self):
+        for native in list(self.running):
+            state = self.srv.poll(native)
+            if state == 0:
+                continue
+            req = self.running.pop(native)
+            req.finished = self.clock()
+            try:
+                req.result = self.srv.release(native)
+            except Exception as e:   # the request failed: keep the message
+                req.info["failed"] = True
+                req.info["error"] = str(e)
+            self.done[req.ticket] = req
+        self.max_concurrent = max(self.max_concurrent, self.srv.info()["running"])
+        if self.running:
+            self.rounds += 1
+            self.srv.wait(next(iter(self.running)), 0.001)
+        return bool(self.running)
+
+    def pending(self):
+        return len(self.running)
+
+    def latencies(self):
+        return np.array([r.latency for r in self.done.values() if r.latency is not None])
+
+    def close(self):
+        self.srv.close()
 
 
 def poisson_arrivals(n, rate, seed):

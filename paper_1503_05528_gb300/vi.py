@@ -30,6 +30,8 @@ EXPORTS = [
     "vi_profile", "vi_get_stats", "vi_energy_noalloc", "vi_tune_export", "vi_tune_import",
     "vi_realign_last_error", "vi_affine_levels", "vi_affine_estimate", "vi_affine_to_reference",
     "vi_affine_align", "vi_affine_unwarp",
+    "vi_server_create", "vi_server_submit", "vi_server_poll", "vi_server_wait", "vi_server_release",
+    "vi_server_info", "vi_server_destroy",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -120,6 +122,14 @@ def _declare(L):
     L.vi_tune_export.argtypes = [C.c_char_p, i]
     L.vi_tune_export.restype = i
     L.vi_tune_import.argtypes = [C.c_char_p]
+    L.vi_server_create.argtypes = [C.c_size_t, i, P(vp)]
+    L.vi_server_submit.argtypes = [vp, P(ViConfig), vp, vp, i, i, i, i, vp, P(C.c_uint64)]
+    L.vi_server_poll.argtypes = [vp, C.c_uint64, P(i)]
+    L.vi_server_wait.argtypes = [vp, C.c_uint64, d, P(i)]
+    L.vi_server_release.argtypes = [vp, C.c_uint64, C.c_char_p, i]
+    L.vi_server_info.argtypes = [vp, P(i), P(i), P(C.c_size_t)]
+    L.vi_server_destroy.argtypes = [vp]
+    L.vi_server_destroy.restype = None
     L.vi_realign_last_error.argtypes = []
     L.vi_realign_last_error.restype = C.c_char_p
     L.vi_affine_levels.argtypes = [i, i]
@@ -441,6 +451,86 @@ def tune_import(text):
     st = load().vi_tune_import(text.encode())
     if st != VI_OK:
         raise ViError(st, "vi_tune_import: malformed line")
+
+
+class Server:
+    """The native server (vi_server_*): submit() queues a request and returns
+    its ticket; the arrays are kept alive here until the request is
+    released."""
+
+    def __init__(self, hbm_budget, max_slots=8, **defaults):
+        self.lib = load()
+        h = C.c_void_p()
+        st = self.lib.vi_server_create(int(hbm_budget), int(max_slots), C.byref(h))
+        if st != VI_OK:
+            raise ViError(st, "vi_server_create failed")
+        self.h = h
+        self.defaults = dict(defaults)
+        self._keep = {}
+
+    def submit(self, rgb, mask, out=None, **job):
+        if isinstance(rgb, np.ndarray):
+            rgb = np.ascontiguousarray(rgb, np.float32)
+        if isinstance(mask, np.ndarray):
+            mask = np.ascontiguousarray(mask, np.uint8)
+        T, H, W = mask.shape[:3]
+        if out is None:
+            out = np.empty((T, H, W, 3), np.float32)
+        cfg = default_config(**{**self.defaults, **job})
+        pr, dev = _ptr(rgb)
+        pm, _ = _ptr(mask)
+        po, _ = _ptr(out)
+        t = C.c_uint64(0)
+        st = self.lib.vi_server_submit(self.h, C.byref(cfg), pr, pm, W, H, T, dev, po, C.byref(t))
+        if st != VI_OK:
+            raise ViError(st, "vi_server_submit")
+        self._keep[t.value] = (rgb, mask, out)
+        return t.value
+
+    def poll(self, ticket):
+        d = C.c_int(0)
+        st = self.lib.vi_server_poll(self.h, ticket, C.byref(d))
+        if st != VI_OK:
+            raise ViError(st, "vi_server_poll")
+        return d.value
+
+    def wait(self, ticket, timeout=-1.0):
+        d = C.c_int(0)
+        st = self.lib.vi_server_wait(self.h, ticket, float(timeout), C.byref(d))
+        if st != VI_OK:
+            raise ViError(st, "vi_server_wait")
+        return d.value
+
+    def release(self, ticket):
+        """Returns the result array of a finished request and forgets it."""
+        buf = C.create_string_buffer(512)
+        st = self.lib.vi_server_release(self.h, ticket, buf, 512)
+        keep = self._keep.pop(ticket, None)
+        if st != VI_OK:
+            raise ViError(st, "request failed: " + buf.value.decode(errors="replace"))
+        return keep[2] if keep else None
+
+    def info(self):
+        q, r, b = C.c_int(0), C.c_int(0), C.c_size_t(0)
+        self.lib.vi_server_info(self.h, C.byref(q), C.byref(r), C.byref(b))
+        return dict(queued=q.value, running=r.value, bytes_in_use=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vi_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _rck(st, what):

@@ -77,3 +77,18 @@ def test_context_without_gpu_fails_loudly(lib):
     assert st == 7   # VI_ERR_NO_DEVICE
     with pytest.raises(vi.ViError):
         vi.Context()
+
+
+def test_server_arguments_and_no_gpu(lib):
+    import torch
+    h = ctypes.c_void_p()
+    assert lib.vi_server_create(0, 4, ctypes.byref(h)) == 1          # zero budget: VI_ERR_ARG
+    assert lib.vi_server_create(1 << 30, 0, ctypes.byref(h)) == 1    # no slots
+    assert lib.vi_server_create(1 << 30, 257, ctypes.byref(h)) == 1
+    d = ctypes.c_int(0)
+    assert lib.vi_server_poll(None, 1, ctypes.byref(d)) == 1
+    lib.vi_server_destroy(None)                                      # a no-op
+    if not torch.cuda.is_available():
+        assert lib.vi_server_create(1 << 30, 2, ctypes.byref(h)) == 7   # VI_ERR_NO_DEVICE
+        with pytest.raises(vi.ViError):
+            vi.Server(1 << 30, 2)
