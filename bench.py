@@ -51,7 +51,8 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # ncu capture (profiles/k_ann_step_layered_320x240x60.md), as a dict with
 # keys workload, storage, bytes, gathered_voxels. Applies to that workload and
 # storage only; None while the kernel has changed since the capture.
-NCU_STEP_TRAFFIC = None
+NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
+                    "bytes": (3053.4e6 + 9.85e6) / 330, "gathered_voxels": 67891553.6 / 20}
 
 
 def combine_ranks(values, dist=None, device="cpu"):

@@ -118,7 +118,7 @@ typedef struct {
     unsigned long long screened;       /* candidates screened on the FP16 copy */
     unsigned long long screen_passed;  /* of those, evaluated in FP32 */
     unsigned long long step_launches;  /* launches of the PatchMatch step kernel */
-    double step_ms;                    /* device time of those launches (profiling on) */
+    double step_ms;                    /* device time of those launches (profiling on, see vi_profile) */
     unsigned long long step_timed;     /* launches included in step_ms */
     int outer[16];                     /* search/reconstruction iterations run per level */
     int onion_layers;                  /* layers peeled by the initialisation */
@@ -290,8 +290,12 @@ vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n
  * are the input values. Synchronises when out is host memory. */
 vi_status vi_fetch_result(vi_ctx *ctx, float *rgb_out, int ptr_is_device);
 
-/* Device-time profiling of the PatchMatch step kernel: with enable = 1 every
- * launch is bracketed by CUDA events on the context's stream. */
+/* Device-time profiling of the PatchMatch step kernel: with enable = 1 each
+ * run of back-to-back step launches (the sweeps of one search, nothing else
+ * between them on the context's stream) is bracketed by one pair of CUDA
+ * events; step_ms sums those spans and step_timed counts the launches inside
+ * them. One pair per search instead of one per launch keeps the events from
+ * slowing the profiled run. */
 vi_status vi_profile(vi_ctx *ctx, int enable);
 
 /* The context's counters (synchronises to read event times). */

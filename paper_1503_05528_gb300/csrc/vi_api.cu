@@ -192,27 +192,40 @@ vi_status ensure_partials2(vi_ctx *ctx, int n_blocks)
     return VI_OK;
 }
 
-// One launch of the PatchMatch step kernel, bracketed by events when profiling.
+// One launch of the PatchMatch step kernel.
 vi_status step_launch(vi_ctx *ctx, const AnnArgs &a)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->profiling) {
-        if (ctx->events_used == ctx->events.size()) {
-            cudaEvent_t x, y;
-            CK(cudaEventCreate(&x));
-            CK(cudaEventCreate(&y));
-            ctx->events.emplace_back(x, y);
-        }
-        e0 = ctx->events[ctx->events_used].first;
-        e1 = ctx->events[ctx->events_used].second;
-        ++ctx->events_used;
-        CK(cudaEventRecord(e0, ctx->stream));
-    }
     launch_ann_step(a, ctx->c5, ctx->stream);
     CK_LAUNCH();
-    if (ctx->profiling)
-        CK(cudaEventRecord(e1, ctx->stream));
     ++ctx->step_launches;
+    return VI_OK;
+}
+
+// With profiling on, an event pair around a run of back-to-back step launches.
+vi_status profile_begin(vi_ctx *ctx, cudaEvent_t *e1)
+{
+    *e1 = nullptr;
+    if (!ctx->profiling)
+        return VI_OK;
+    if (ctx->events_used == ctx->events.size()) {
+        cudaEvent_t x, y;
+        CK(cudaEventCreate(&x));
+        CK(cudaEventCreate(&y));
+        ctx->events.emplace_back(x, y);
+        ctx->event_launches.push_back(0);
+    }
+    CK(cudaEventRecord(ctx->events[ctx->events_used].first, ctx->stream));
+    *e1 = ctx->events[ctx->events_used].second;
+    return VI_OK;
+}
+
+vi_status profile_end(vi_ctx *ctx, cudaEvent_t e1, int launches)
+{
+    if (!e1)
+        return VI_OK;
+    CK(cudaEventRecord(e1, ctx->stream));
+    ctx->event_launches[ctx->events_used] = launches;
+    ++ctx->events_used;
     return VI_OK;
 }
 
@@ -229,6 +242,8 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
                    ctx->cfg.lanes_per_target);
     CK_LAUNCH();
     const int rmax = std::max(l.W, std::max(l.H, l.T));
+    cudaEvent_t e1 = nullptr;
+    TRY(profile_begin(ctx, &e1));
     // launch s reads buffer s & 1 and writes the other one
     int s = 0;
     for (int k = 1; k <= ctx->cfg.n_pm; ++k) {
@@ -272,6 +287,7 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
             TRY(step_launch(ctx, a));
         }
     }
+    TRY(profile_end(ctx, e1, s));
     if (s & 1) {
         launch_copy_targets(targets, nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], ctx->stream);
         CK_LAUNCH();
@@ -289,7 +305,9 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
     a.n = l.nH;
     a.phi = l.phi[0];
     a.d2 = l.d2[0];
-    a.allowed = l.code;
+    // every patch covering a voxel of H is centred in H~ (the 5x5x5 dilation
+    // of H), so the vote needs no per-patch set test
+    a.allowed = nullptr;
     a.abit = CODE_TARGET;
     a.weighted = ctx->cfg.weighted;
     a.hp = nullptr;
@@ -1069,7 +1087,7 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
         float ms = 0.0f;
         CK(cudaEventElapsedTime(&ms, ctx->events[i].first, ctx->events[i].second));
         ctx->step_ms += ms;
-        ++ctx->step_timed;
+        ctx->step_timed += (unsigned long long)ctx->event_launches[i];
     }
     ctx->events_used = 0;
     out->evals = ev[0] + ev[1];

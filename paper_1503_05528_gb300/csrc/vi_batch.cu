@@ -337,7 +337,9 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
             v.n = l.nH;
             v.phi = l.phi[0];
             v.d2 = l.d2[0];
-            v.allowed = l.code;
+            // every patch covering a voxel of H is centred in H~ (the 5x5x5 dilation
+            // of H), so the vote needs no per-patch set test
+            v.allowed = nullptr;
             v.abit = CODE_TARGET;
             v.weighted = ctx->cfg.weighted;
             v.hp = nullptr;

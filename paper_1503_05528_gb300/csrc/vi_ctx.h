@@ -99,6 +99,7 @@ struct vi_ctx {
 
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    std::vector<int> event_launches;   // step launches inside each used event pair
     size_t events_used = 0;
     double step_ms = 0.0;
     unsigned long long step_timed = 0;

@@ -100,7 +100,7 @@ struct VoteArgs {
     int n;
     const Shift *phi;
     const float *d2;
-    const uint8_t *allowed;  // q contributes iff allowed[q] & abit
+    const uint8_t *allowed;  // q contributes iff allowed[q] & abit; null: every in-video q
     uint8_t abit;
     int weighted;
     uint8_t *hp;           // onion peel: cleared for filled voxels (nullable)

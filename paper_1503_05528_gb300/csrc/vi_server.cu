@@ -236,14 +236,20 @@ vi_status vi_server_wait(vi_server *s, uint64_t ticket, double timeout_s, int *d
     if (!s || !done)
         return VI_ERR_ARG;
     std::unique_lock<std::mutex> lock(s->mu);
-    auto it = s->jobs.find(ticket);
-    if (it == s->jobs.end())
+    if (s->jobs.find(ticket) == s->jobs.end())
         return VI_ERR_ARG;
-    auto finished = [&] { return it->second.state == JOB_DONE || it->second.state == JOB_FAILED; };
+    // looked up afresh on every wake-up: another thread may release the ticket meanwhile
+    auto finished = [&] {
+        auto f = s->jobs.find(ticket);
+        return f == s->jobs.end() || f->second.state == JOB_DONE || f->second.state == JOB_FAILED;
+    };
     if (timeout_s < 0)
         s->done_cv.wait(lock, finished);
     else
         s->done_cv.wait_for(lock, std::chrono::duration<double>(timeout_s), finished);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end())
+        return VI_ERR_ARG;
     const int st = it->second.state;
     *done = st == JOB_DONE ? 1 : (st == JOB_FAILED ? -1 : 0);
     return VI_OK;

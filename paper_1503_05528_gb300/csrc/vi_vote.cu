@@ -70,7 +70,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                           ot = (int)((o >> 16) & 0xFFu) - 2;
                 if (interior || inside(L, px + ox, py + oy, pt + ot)) {
                     const int q = p + ot * L.HW + oy * L.W + ox;
-                    if (a.allowed[q] & a.abit) {
+                    if (!a.allowed || (a.allowed[q] & a.abit)) {
                         const float d = a.d2[q];
                         const Shift f = a.phi[q];
                         // finite distance, and a source voxel p + phi(q) inside
