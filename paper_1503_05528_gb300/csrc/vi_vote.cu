@@ -92,39 +92,54 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
             if (a.weighted) {
                 // Radix select of the value of 0-based rank r over the bit
                 // patterns (non-negative finite floats order like their bits,
-                // all below 2^31). Invariant before bit b: the answer's bits
-                // above b are those of X (its bits <= b are 0), lo = #{v < X}
-                // and hi = #{v < X + 2^(b+1)}, so lo <= r < hi. Once a single
-                // value is left in [X, X + 2^(b+1)) it is the answer, and the
-                // search stops there: about log2(n) steps for distinct values
-                // instead of 31.
+                // all below 2^31; slots without a contributor hold 2^32 - 1,
+                // above all of them, so they never count). Invariant before
+                // bit b: the answer's bits above b are those of X (its bits
+                // <= b are 0), lo = #{v < X} and hi = #{v < X + 2^(b+1)}, so
+                // lo <= r < hi. The search starts at the highest bit where the
+                // smallest and largest values differ (every bit above it is
+                // shared by all values), and once a single value is left in
+                // [X, X + 2^(b+1)) it is the answer: about log2(n) steps for
+                // distinct values instead of 31.
                 const unsigned r = (unsigned)((3 * n + 3) / 4 - 1);   // 0-based nearest rank
-                unsigned X = 0, lo = 0, hi = (unsigned)n;
-                int b = 30;
-                for (; b >= 0 && hi - lo > 1; --b) {
-                    const unsigned Tt = X | (1u << b);
-                    unsigned c = 0;
+                unsigned u[4];
+                unsigned umin = 0xffffffffu, umax = 0u;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        c += ((okm >> m) & 1u) && (__float_as_uint(dq[m]) < Tt);
-                    c = __reduce_add_sync(0xffffffffu, c);
-                    if (c <= r) {
-                        X = Tt;
-                        lo = c;
-                    } else {
-                        hi = c;
-                    }
+                for (int m = 0; m < 4; ++m) {
+                    const bool ok = (okm >> m) & 1u;
+                    u[m] = ok ? __float_as_uint(dq[m]) : 0xffffffffu;
+                    umin = min(umin, u[m]);
+                    umax = max(umax, ok ? u[m] : 0u);
                 }
-                if (hi - lo == 1) {
-                    // the one value in [X, X + 2^(b+1)): the smallest v >= X
-                    unsigned mn = 0xffffffffu;
+                umin = __reduce_min_sync(0xffffffffu, umin);
+                umax = __reduce_max_sync(0xffffffffu, umax);
+                unsigned X = umin;
+                if (umin != umax) {
+                    int b = 31 - __clz(umin ^ umax);        // <= 30
+                    X = umin & ~((2u << b) - 1u);
+                    unsigned lo = 0, hi = (unsigned)n;
+                    for (; b >= 0 && hi - lo > 1; --b) {
+                        const unsigned Tt = X | (1u << b);
+                        unsigned c = 0;
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const unsigned u = __float_as_uint(dq[m]);
-                        if (((okm >> m) & 1u) && u >= X && u < mn)
-                            mn = u;
+                        for (int m = 0; m < 4; ++m)
+                            c += u[m] < Tt;
+                        c = __reduce_add_sync(0xffffffffu, c);
+                        if (c <= r) {
+                            X = Tt;
+                            lo = c;
+                        } else {
+                            hi = c;
+                        }
                     }
-                    X = __reduce_min_sync(0xffffffffu, mn);
+                    if (hi - lo == 1) {
+                        // the one value in [X, X + 2^(b+1)): the smallest v >= X
+                        unsigned mn = 0xffffffffu;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            mn = min(mn, u[m] >= X ? u[m] : 0xffffffffu);
+                        X = __reduce_min_sync(0xffffffffu, mn);
+                    }
                 }
                 sigma2 = __uint_as_float(X);
             }
