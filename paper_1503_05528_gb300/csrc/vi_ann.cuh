@@ -276,6 +276,215 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-shared lanes (lanes_per_target = 32). With one lane per target, a warp
+// spends each candidate's gathers on the lanes whose candidate needs them
+// (not rejected by a cheap test) while the others wait: at the largest
+// levels about 13 of 32 lanes were active on average. Here lane l still owns
+// target l of the warp's 32 (its state, counts and decisions), but every
+// candidate that needs a distance is evaluated by a group of G lanes, G
+// chosen per candidate round from how many lanes need one: the most lanes
+// (at most 8) that still serve them all at once. A target's candidates keep
+// their order (propagation from the three neighbours, then the random
+// search), each bounded by the best distance so far, and group_d2 adds the
+// slices in the same order for every G, so every decision and every output
+// is the same as with a fixed G.
+// ---------------------------------------------------------------------------
+
+// The pending candidates of mask M (owner lanes), G lanes each: group j
+// serves the owner holding the j-th set bit of M. Returns, on each owner
+// lane, its candidate's bounded distance (group_d2).
+template <bool C5, int G>
+__device__ __forceinline__ float warp_serve_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py,
+                                               int pt, int s, float best, unsigned &gathered)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int c = __popc(M);
+    const int j = lane / G;
+    const int o = j < c ? (int)__fns(M, 0, j + 1) : lane;
+    const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
+              opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
+    const float ob = __shfl_sync(FULL, best, o);
+    float dd = __int_as_float(0x7f800000);
+    if (j < c)
+        dd = group_d2<C5, G, false>(L, op, opx, opy, opt, os, nullptr, ob, lane & (G - 1), group_mask<G>(),
+                                    gathered);
+    const int r = __popc(M & ((1u << lane) - 1u));
+    return __shfl_sync(FULL, dd, (r * G) & 31);
+}
+
+template <bool C5>
+__device__ __forceinline__ float warp_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py, int pt,
+                                         int s, float best, unsigned &gathered)
+{
+    const int c = __popc(M);
+    if (c > 16)
+        return warp_serve_d2<C5, 1>(L, M, lane, p, px, py, pt, s, best, gathered);
+    if (c > 8)
+        return warp_serve_d2<C5, 2>(L, M, lane, p, px, py, pt, s, best, gathered);
+    if (c > 4)
+        return warp_serve_d2<C5, 4>(L, M, lane, p, px, py, pt, s, best, gathered);
+    return warp_serve_d2<C5, 8>(L, M, lane, p, px, py, pt, s, best, gathered);
+}
+
+// The FP16 screen (group_screen) of the pending candidates of M, the same way.
+template <bool C5, int G>
+__device__ __forceinline__ bool warp_serve_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
+                                                  int pt, int s, float best, float D, unsigned &gathered_h)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int c = __popc(M);
+    const int j = lane / G;
+    const int o = j < c ? (int)__fns(M, 0, j + 1) : lane;
+    const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
+              opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
+    const float ob = __shfl_sync(FULL, best, o);
+    int pass = 0;
+    if (j < c)
+        pass = group_screen<C5, G>(L, op, opx, opy, opt, os, ob, D, lane & (G - 1), group_mask<G>(), gathered_h);
+    const int r = __popc(M & ((1u << lane) - 1u));
+    return __shfl_sync(FULL, pass, (r * G) & 31) != 0;
+}
+
+template <bool C5>
+__device__ __forceinline__ bool warp_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
+                                            int pt, int s, float best, float D, unsigned &gathered_h)
+{
+    const int c = __popc(M);
+    if (c > 16)
+        return warp_serve_screen<C5, 1>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+    if (c > 8)
+        return warp_serve_screen<C5, 2>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+    if (c > 4)
+        return warp_serve_screen<C5, 4>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+    return warp_serve_screen<C5, 8>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+}
+
+// ann_one for the 32 targets [i0, i0 + 32) of a warp with warp-shared lanes
+// (the whole warp calls it; lanes past nT own no target). Stages 0..2 are the
+// propagation candidates, the rest the random search; each stage offers at
+// most one candidate per target, so a target's candidates are judged in the
+// same order and against the same running best as in ann_one.
+template <bool C5, bool F16>
+__device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int span, StepCount &n)
+{
+    const LevelView &L = a.L;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool active = i < a.nT;
+    const float D = F16 ? screen_d2bound(L) : 0.0f;
+    const float INF = __int_as_float(0x7f800000);
+    int p = 0, px = 0, py = 0, pt = 0;
+    Shift cur;
+    cur.dx = cur.dy = cur.dt = 0;
+    float d = INF;
+    Shift cn[3];
+    int sn[3] = {-1, -1, -1};
+    bool stale[3] = {false, false, false};
+    if (active) {
+        p = a.targets[i];
+        decode(p, L.W, L.HW, px, py, pt);
+        cur = a.phi_in[p];
+        d = a.d_in[p];
+        const int sg = (k & 1) ? 1 : -1;
+        const bool in0 = inside(L, px + sg, py, pt), in1 = inside(L, px, py + sg, pt),
+                   in2 = inside(L, px, py, pt + sg);
+        const int r0 = in0 ? p + sg : p, r1 = in1 ? p + sg * L.W : p, r2 = in2 ? p + sg * L.HW : p;
+        const bool t0 = in0 && (a.tmask[r0] & a.tbit), t1 = in1 && (a.tmask[r1] & a.tbit),
+                   t2 = in2 && (a.tmask[r2] & a.tbit);
+        cn[0] = a.phi_in[r0];
+        cn[1] = a.phi_in[r1];
+        cn[2] = a.phi_in[r2];
+        sn[0] = t0 ? source_of(L, px, py, pt, cn[0].dx, cn[0].dy, cn[0].dt) : -1;
+        sn[1] = t1 ? source_of(L, px, py, pt, cn[1].dx, cn[1].dy, cn[1].dt) : -1;
+        sn[2] = t2 ? source_of(L, px, py, pt, cn[2].dx, cn[2].dy, cn[2].dt) : -1;
+        // the change-flag rule of ann_one
+        const unsigned span_mask = a.chg_in != nullptr && span > 0 ? (1u << span) - 1u : 0u;
+        stale[0] = span_mask && t0 && (a.chg_in[r0] & span_mask) == 0;
+        stale[1] = span_mask && t1 && (a.chg_in[r1] & span_mask) == 0;
+        stale[2] = span_mask && t2 && (a.chg_in[r2] & span_mask) == 0;
+    }
+    Rejected rej;
+    const Shift start = cur;
+    const int stages = 3 + (a.do_random ? (a.rs_mode ? 31 : 1) : 0);
+#pragma unroll 1
+    for (int stage = 0; stage < stages; ++stage) {
+        int s = -1, cdx = 0, cdy = 0, cdt = 0;
+        bool skip = false;
+        if (stage < 3) {
+            // (a register array indexed by a loop variable would spill: select)
+            const Shift c = stage == 0 ? cn[0] : (stage == 1 ? cn[1] : cn[2]);
+            s = stage == 0 ? sn[0] : (stage == 1 ? sn[1] : sn[2]);
+            skip = stage == 0 ? stale[0] : (stage == 1 ? stale[1] : stale[2]);
+            cdx = c.dx;
+            cdy = c.dy;
+            cdt = c.dt;
+        } else {
+            const int ri = stage - 3;
+            const int sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
+            if (a.rs_mode && (sh > 30 || (a.rmax >> sh) < 1))
+                break;   // the same for every lane
+            if (active) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
+                                                         a.rs_mode ? (uint32_t)ri : 0u),
+                                              a.key0, a.key1);
+                cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
+                cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
+                cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
+                s = source_of(L, px, py, pt, cdx, cdy, cdt);
+            }
+        }
+        bool need = false;
+        unsigned long long key = 0;
+        if (active && s >= 0) {
+            ++n.evals;
+            if (!skip) {
+                key = shift_key(cdx, cdy, cdt);
+                need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
+            }
+        }
+        if (F16 && stage >= 3) {
+            const unsigned M = __ballot_sync(FULL, need);
+            if (M) {
+                const bool pass = warp_screen<C5>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                if (need) {
+                    ++n.screened;
+                    if (pass) {
+                        ++n.passed;
+                    } else {
+                        rej.add(key);
+                        need = false;
+                    }
+                }
+            }
+        }
+        const unsigned M = __ballot_sync(FULL, need);
+        if (M) {
+            const float dd = warp_d2<C5>(L, M, lane, p, px, py, pt, s, d, n.gathered);
+            if (need) {
+                if (dd < d) {
+                    d = dd;
+                    cur.dx = (short)cdx;
+                    cur.dy = (short)cdy;
+                    cur.dt = (short)cdt;
+                } else {
+                    rej.add(key);
+                }
+            }
+        }
+        if (stage >= 3 && !a.rs_mode)
+            break;
+    }
+    if (active) {
+        a.phi_out[p] = cur;
+        a.d_out[p] = d;
+        if (a.chg_out) {
+            const bool changed = cur.dx != start.dx || cur.dy != start.dy || cur.dt != start.dt;
+            a.chg_out[p] = (uint8_t)((changed ? 1u : 0u) | ((unsigned)a.chg_in[p] << 1));
+        }
+    }
+}
+
 // Adds a launch's per-lane counts to the counters ctr[0..4] = evaluations,
 // FP32 voxels, FP16 voxels, screened, passed (evaluations and candidate
 // counts once per group).
@@ -304,6 +513,16 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, PARTIAL>() * (2
     if (i < a.nT)
         ann_one<C5, G, PARTIAL, F16>(a, i, a.k, a.chg_span, sub, gmask, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, sub);
+}
+
+// One target per lane, candidates' gathers shared by the warp (lanes = 32).
+template <bool C5, bool F16>
+__global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK)) k_ann_step_warp(const AnnArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    StepCount n;
+    ann_one_warp<C5, F16>(a, i, a.k, a.chg_span, n);
+    flush_counts<F16>(a.evals, a.gathered, a.screen, n, 0);
 }
 
 // Batch form: the targets of n clips in one persistent launch. Clip c owns
@@ -345,6 +564,14 @@ void launch_ann_step_impl(const AnnArgs &a, bool c5, cudaStream_t st)
             launch_ann_step_g<true, 8, true, false>(a, st);
         else
             launch_ann_step_g<false, 8, true, false>(a, st);
+        return;
+    }
+    if (a.lanes == 32) {
+        const int grid = blocks_for(a.nT, STEP_BLOCK);
+        if (c5)
+            k_ann_step_warp<true, F16><<<grid, STEP_BLOCK, 0, st>>>(a);
+        else
+            k_ann_step_warp<false, F16><<<grid, STEP_BLOCK, 0, st>>>(a);
         return;
     }
     switch ((a.lanes > 0 ? a.lanes : pick_group(a.nT)) * 2 + (c5 ? 1 : 0)) {

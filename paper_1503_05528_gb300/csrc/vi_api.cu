@@ -155,7 +155,7 @@ vi_status check_config(vi_ctx *ctx, const vi_config *c)
         c->time_subsample < 0 || c->time_subsample > 1 ||
         c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
-          c->lanes_per_target == 4 || c->lanes_per_target == 8))
+          c->lanes_per_target == 4 || c->lanes_per_target == 8 || c->lanes_per_target == 32))
         return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
     // rho must be 2^-m, m >= 1
     int m = 0;
@@ -191,6 +191,10 @@ vi_status ensure_partials2(vi_ctx *ctx, int n_blocks)
     ctx->partials2_cap = n_blocks;
     return VI_OK;
 }
+
+// Lanes per target of the rescore kernels: the warp-shared form (32) exists
+// for the step only; the rescore then uses one lane per target.
+static int rescore_lanes(int lanes) { return lanes == 32 ? 1 : lanes; }
 
 // One launch of the PatchMatch step kernel.
 vi_status step_launch(vi_ctx *ctx, const AnnArgs &a)
@@ -239,7 +243,7 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
     Level &l = ctx->lv[level];
     const LevelView v = l.view();
     launch_rescore(v, targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream,
-                   ctx->cfg.lanes_per_target);
+                   rescore_lanes(ctx->cfg.lanes_per_target));
     CK_LAUNCH();
     const int rmax = std::max(l.W, std::max(l.H, l.T));
     cudaEvent_t e1 = nullptr;
@@ -745,7 +749,7 @@ vi_status vi_rescore(vi_ctx *ctx, int level)
         return fail(ctx, VI_ERR_ARG, "vi_rescore: bad level or no pyramid");
     Level &l = ctx->lv[level];
     launch_rescore(l.view(), l.targets, l.nT, l.phi[0], l.d2[0], nullptr, ctx->c5, ctx->evals_dev,
-                   ctx->stream, ctx->cfg.lanes_per_target);
+                   ctx->stream, rescore_lanes(ctx->cfg.lanes_per_target));
     CK_LAUNCH();
     return VI_OK;
 }

@@ -63,7 +63,7 @@ unsigned long long *tune_scratch()
 // issues one launch with lanes G and counters at scratch. Returns 0 when the
 // tuning could not run (the caller then uses pick_group).
 template <typename Launch>
-int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch)
+int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch, bool with_warp = false)
 {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -72,26 +72,28 @@ int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch)
     unsigned long long *scratch = tune_scratch();
     if (!scratch)
         return 0;
-    static const int Gs[4] = {1, 2, 4, 8};
-    cudaEvent_t ev[5];
-    for (int i = 0; i < 5; ++i)
+    // 32: the warp-shared form of the single-clip step (k_ann_step_warp)
+    static const int Gs[5] = {1, 2, 4, 8, 32};
+    const int nG = with_warp ? 5 : 4;
+    cudaEvent_t ev[6];
+    for (int i = 0; i <= nG; ++i)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) {
             for (int j = 0; j < i; ++j)
                 cudaEventDestroy(ev[j]);
             cudaGetLastError();
             return 0;
         }
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < nG; ++i)
         launch(Gs[i], scratch);
     cudaEventRecord(ev[0], st);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < nG; ++i) {
         launch(Gs[i], scratch);
         cudaEventRecord(ev[i + 1], st);
     }
     int best = 0;
-    if (cudaEventSynchronize(ev[4]) == cudaSuccess) {
+    if (cudaEventSynchronize(ev[nG]) == cudaSuccess) {
         float best_ms = 0.0f;
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < nG; ++i) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess && (best == 0 || ms < best_ms)) {
                 best = Gs[i];
@@ -99,7 +101,7 @@ int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch)
             }
         }
     }
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i <= nG; ++i)
         cudaEventDestroy(ev[i]);
     if (best)
         g_tuned[key] = best;
@@ -151,7 +153,7 @@ vi_status vi_tune_import(const char *text)
             break;
         if (std::sscanf(p, "%u %u %u %u %d %d%n", &dev, &fam, &c5, &f16, &bucket, &G, &used) != 6 ||
             dev >= 64 || fam > 3 || c5 > 1 || f16 > 1 || bucket < 0 || bucket > 0x3FFFFFFF ||
-            !(G == 1 || G == 2 || G == 4 || G == 8))
+            !(G == 1 || G == 2 || G == 4 || G == 8 || (G == 32 && fam == TUNE_STEP)))
             return VI_ERR_ARG;
         add[((uint64_t)dev << 40) | ((uint64_t)fam << 32) | ((uint64_t)c5 << 31) | ((uint64_t)f16 << 30) |
             (uint64_t)bucket] = G;
@@ -192,7 +194,7 @@ void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
         t.screen = scr + 2;
         VI_COUNT_LAUNCH();
         run(t);
-    });
+    }, true);
     run(b);
 }
 

@@ -33,11 +33,12 @@ CASES = {
 }
 
 
-def _make(case, seed, n_pm=10):
+def _make(case, seed, n_pm=10, lanes=0):
     spec = CASES[case]
     clip = spec["clip"]()
     pyr = O.build_pyramid(clip.rgb, clip.mask, spec["levels"], spec["tex"])
-    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=1)
+    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=1,
+                     lanes_per_target=lanes)
     ctx.upload(clip.rgb, clip.mask)
     ctx.build_pyramid()
     return clip, pyr, ctx
@@ -72,10 +73,13 @@ def _ann_check(ctx, lv, level, x, phi, d2, seed, n_pm, call):
     return {k: s1[k] - s0[k] for k in ("screened", "screen_passed", "step_gathered_h", "step_gathered")}
 
 
+@pytest.mark.parametrize("lanes", [0, 32])
 @pytest.mark.parametrize("case,n_pm,call", [("tiny_rgb", 10, 0), ("layered_tex", 10, 3),
                                             ("odd_sizes", 3, 17)])
-def test_ann_fp16_bit_exact(case, n_pm, call):
-    clip, pyr, ctx = _make(case, seed=31, n_pm=n_pm)
+def test_ann_fp16_bit_exact(case, n_pm, call, lanes):
+    # lanes 32: the warp-shared form screens and gathers with lane groups of
+    # the warp; the decisions are the same
+    clip, pyr, ctx = _make(case, seed=31, n_pm=n_pm, lanes=lanes)
     with ctx:
         for level, lv in enumerate(pyr):
             x, phi, d2 = _state(lv, level, 31)
