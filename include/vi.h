@@ -395,8 +395,10 @@ vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *a
                            int T, const double *to_ref, float *rgb_out, int ptr_is_device, void *cuda_stream);
 
 /* Lanes-per-target autotuning (no counterpart in the paper; speed only, never
- * a result). With lanes_per_target = 0 the first PatchMatch step or rescore
- * launch of a kernel family for a target count (per device, channels,
+ * a result). With lanes_per_target = 0 the first rescore launch, or the
+ * first PatchMatch step launch with the change-flag rule on (k >= 3; earlier
+ * sweeps skip no candidate and would favour other choices), of a kernel
+ * family for a target count (per device, channels,
  * storage, quarter-octave bucket of the count) is run once with every lane
  * group size in {1, 2, 4, 8} (and the warp-shared form, 32, for the
  * single-clip step), timed, and the fastest is kept for the

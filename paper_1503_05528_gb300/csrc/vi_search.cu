@@ -108,6 +108,14 @@ int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch, bool with_warp = f
     return best;
 }
 
+// The tuned G for key, or 0 when the table has none.
+int known_lanes(uint64_t key)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
 }  // namespace
 
 }  // namespace vi
@@ -185,8 +193,20 @@ void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
         run(a);
         return;
     }
+    const uint64_t key = tune_key(TUNE_STEP, c5, f16, a.nT);
     AnnArgs b = a;
-    b.lanes = tuned_lanes(tune_key(TUNE_STEP, c5, f16, a.nT), st, [&](int G, unsigned long long *scr) {
+    if (a.chg_span == 0) {
+        // The first sweeps of a search skip no stale neighbour, so every
+        // candidate needs a distance; the later ones skip most. Timing the
+        // lane choices on an early sweep favours the forms that do well
+        // without the skips, so the table is filled from the first sweep with
+        // the change-flag rule on; the sweeps before it use the table when it
+        // knows the bucket, else the size rule.
+        b.lanes = known_lanes(key);
+        run(b);
+        return;
+    }
+    b.lanes = tuned_lanes(key, st, [&](int G, unsigned long long *scr) {
         AnnArgs t = a;
         t.lanes = G;
         t.evals = scr;
@@ -210,12 +230,15 @@ void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, in
         else
             launch_ann_step_batch_impl<false>(clips, tprefix, n, total_targets, k, c5, c, G, st);
     };
-    if (lanes <= 0)
-        lanes = tuned_lanes(tune_key(TUNE_STEP_BATCH, c5, f16, total_targets), st,
-                            [&](int G, unsigned long long *scr) {
-                                VI_COUNT_LAUNCH();
-                                run(G, scr);
-                            });
+    if (lanes <= 0) {
+        const uint64_t key = tune_key(TUNE_STEP_BATCH, c5, f16, total_targets);
+        // as in launch_ann_step: tuned on the first sweep with the change-flag rule (k >= 3)
+        lanes = k < 3 ? known_lanes(key)
+                      : tuned_lanes(key, st, [&](int G, unsigned long long *scr) {
+                            VI_COUNT_LAUNCH();
+                            run(G, scr);
+                        });
+    }
     run(lanes, ctr);
 }
 
