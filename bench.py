@@ -52,7 +52,7 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # keys workload, storage, bytes, gathered_voxels. Applies to that workload and
 # storage only; None while the kernel has changed since the capture.
 NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
-                    "bytes": (3053.4e6 + 9.85e6) / 330, "gathered_voxels": 67891553.6 / 20}
+                    "bytes": (3433.98e6 + 25.16e6) / 330, "gathered_voxels": 71711827.8 / 20}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
