@@ -291,10 +291,27 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span
 // is the same as with a fixed G.
 // ---------------------------------------------------------------------------
 
+// The level view of lane o (a batch warp may hold targets of several clips):
+// the fields the distance and the screen read.
+__device__ __forceinline__ LevelView view_of_lane(const LevelView &L, int o)
+{
+    const unsigned FULL = 0xffffffffu;
+    LevelView v = L;
+    v.W = __shfl_sync(FULL, L.W, o);
+    v.H = __shfl_sync(FULL, L.H, o);
+    v.T = __shfl_sync(FULL, L.T, o);
+    v.HW = __shfl_sync(FULL, L.HW, o);
+    v.x4 = reinterpret_cast<float4 *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.x4), o));
+    v.x1 = reinterpret_cast<float *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.x1), o));
+    v.h4 = reinterpret_cast<uint2 *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.h4), o));
+    return v;
+}
+
 // The pending candidates of mask M (owner lanes), G lanes each: group j
-// serves the owner holding the j-th set bit of M. Returns, on each owner
-// lane, its candidate's bounded distance (group_d2).
-template <bool C5, int G>
+// serves the owner holding the j-th set bit of M, with the owner's target,
+// source, bound and (MIXED: targets of several clips in the warp) level.
+// Returns, on each owner lane, its candidate's bounded distance (group_d2).
+template <bool C5, int G, bool MIXED>
 __device__ __forceinline__ float warp_serve_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                                int pt, int s, float best, unsigned &gathered)
 {
@@ -305,30 +322,32 @@ __device__ __forceinline__ float warp_serve_d2(const LevelView &L, unsigned M, i
     const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
               opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
     const float ob = __shfl_sync(FULL, best, o);
+    const LevelView OL = MIXED ? view_of_lane(L, o) : L;
     float dd = __int_as_float(0x7f800000);
     if (j < c)
-        dd = group_d2<C5, G, false>(L, op, opx, opy, opt, os, nullptr, ob, lane & (G - 1), group_mask<G>(),
+        dd = group_d2<C5, G, false>(OL, op, opx, opy, opt, os, nullptr, ob, lane & (G - 1), group_mask<G>(),
                                     gathered);
     const int r = __popc(M & ((1u << lane) - 1u));
     return __shfl_sync(FULL, dd, (r * G) & 31);
 }
 
-template <bool C5>
+template <bool C5, bool MIXED>
 __device__ __forceinline__ float warp_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py, int pt,
                                          int s, float best, unsigned &gathered)
 {
     const int c = __popc(M);
     if (c > 16)
-        return warp_serve_d2<C5, 1>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 1, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
     if (c > 8)
-        return warp_serve_d2<C5, 2>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 2, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
     if (c > 4)
-        return warp_serve_d2<C5, 4>(L, M, lane, p, px, py, pt, s, best, gathered);
-    return warp_serve_d2<C5, 8>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 4, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
+    return warp_serve_d2<C5, 8, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
 }
 
-// The FP16 screen (group_screen) of the pending candidates of M, the same way.
-template <bool C5, int G>
+// The FP16 screen (group_screen) of the pending candidates of M, the same way
+// (the owner's magnitude bound D too).
+template <bool C5, int G, bool MIXED>
 __device__ __forceinline__ bool warp_serve_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                                   int pt, int s, float best, float D, unsigned &gathered_h)
 {
@@ -338,41 +357,44 @@ __device__ __forceinline__ bool warp_serve_screen(const LevelView &L, unsigned M
     const int o = j < c ? (int)__fns(M, 0, j + 1) : lane;
     const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
               opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
-    const float ob = __shfl_sync(FULL, best, o);
+    const float ob = __shfl_sync(FULL, best, o), oD = __shfl_sync(FULL, D, o);
+    const LevelView OL = MIXED ? view_of_lane(L, o) : L;
     int pass = 0;
     if (j < c)
-        pass = group_screen<C5, G>(L, op, opx, opy, opt, os, ob, D, lane & (G - 1), group_mask<G>(), gathered_h);
+        pass = group_screen<C5, G>(OL, op, opx, opy, opt, os, ob, oD, lane & (G - 1), group_mask<G>(), gathered_h);
     const int r = __popc(M & ((1u << lane) - 1u));
     return __shfl_sync(FULL, pass, (r * G) & 31) != 0;
 }
 
-template <bool C5>
+template <bool C5, bool MIXED>
 __device__ __forceinline__ bool warp_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                             int pt, int s, float best, float D, unsigned &gathered_h)
 {
     const int c = __popc(M);
     if (c > 16)
-        return warp_serve_screen<C5, 1>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 1, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
     if (c > 8)
-        return warp_serve_screen<C5, 2>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 2, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
     if (c > 4)
-        return warp_serve_screen<C5, 4>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
-    return warp_serve_screen<C5, 8>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 4, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+    return warp_serve_screen<C5, 8, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
 }
 
-// ann_one for the 32 targets [i0, i0 + 32) of a warp with warp-shared lanes
-// (the whole warp calls it; lanes past nT own no target). Stages 0..2 are the
-// propagation candidates, the rest the random search; each stage offers at
-// most one candidate per target, so a target's candidates are judged in the
-// same order and against the same running best as in ann_one.
-template <bool C5, bool F16>
-__device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int span, StepCount &n)
+// ann_one for the targets of a warp with warp-shared lanes: the whole warp
+// calls it, and lane l owns target i of the clip a describes when active (a
+// is only read when active; with MIXED the lanes may belong to different
+// clips of a batch). Stages 0..2 are the propagation candidates, the rest the
+// random search; each stage offers at most one candidate per target, so a
+// target's candidates are judged in the same order and against the same
+// running best as in ann_one. The warp leaves the stage loop together, when
+// no lane has a stage left.
+template <bool C5, bool F16, bool MIXED>
+__device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int i, int k, int span, StepCount &n)
 {
     const LevelView &L = a.L;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool active = i < a.nT;
-    const float D = F16 ? screen_d2bound(L) : 0.0f;
+    const float D = (F16 && active) ? screen_d2bound(L) : 0.0f;
     const float INF = __int_as_float(0x7f800000);
     int p = 0, px = 0, py = 0, pt = 0;
     Shift cur;
@@ -406,11 +428,20 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int
     }
     Rejected rej;
     const Shift start = cur;
-    const int stages = 3 + (a.do_random ? (a.rs_mode ? 31 : 1) : 0);
 #pragma unroll 1
-    for (int stage = 0; stage < stages; ++stage) {
+    for (int stage = 0;; ++stage) {
         int s = -1, cdx = 0, cdy = 0, cdt = 0;
         bool skip = false;
+        // does this lane's target have a candidate at this stage
+        bool mine = active;
+        int ri = 0, sh = 0;
+        if (stage >= 3 && active) {
+            ri = stage - 3;
+            sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
+            mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
+        }
+        if (!__any_sync(FULL, mine))
+            break;
         if (stage < 3) {
             // (a register array indexed by a loop variable would spill: select)
             const Shift c = stage == 0 ? cn[0] : (stage == 1 ? cn[1] : cn[2]);
@@ -419,20 +450,14 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int
             cdx = c.dx;
             cdy = c.dy;
             cdt = c.dt;
-        } else {
-            const int ri = stage - 3;
-            const int sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
-            if (a.rs_mode && (sh > 30 || (a.rmax >> sh) < 1))
-                break;   // the same for every lane
-            if (active) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
-                                                         a.rs_mode ? (uint32_t)ri : 0u),
-                                              a.key0, a.key1);
-                cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
-                cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
-                cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
-                s = source_of(L, px, py, pt, cdx, cdy, cdt);
-            }
+        } else if (mine) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
+                                                     a.rs_mode ? (uint32_t)ri : 0u),
+                                          a.key0, a.key1);
+            cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
+            cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
+            cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
+            s = source_of(L, px, py, pt, cdx, cdy, cdt);
         }
         bool need = false;
         unsigned long long key = 0;
@@ -446,7 +471,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int
         if (F16 && stage >= 3) {
             const unsigned M = __ballot_sync(FULL, need);
             if (M) {
-                const bool pass = warp_screen<C5>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
                 if (need) {
                     ++n.screened;
                     if (pass) {
@@ -460,7 +485,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int
         }
         const unsigned M = __ballot_sync(FULL, need);
         if (M) {
-            const float dd = warp_d2<C5>(L, M, lane, p, px, py, pt, s, d, n.gathered);
+            const float dd = warp_d2<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, n.gathered);
             if (need) {
                 if (dd < d) {
                     d = dd;
@@ -472,8 +497,6 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, int i, int k, int
                 }
             }
         }
-        if (stage >= 3 && !a.rs_mode)
-            break;
     }
     if (active) {
         a.phi_out[p] = cur;
@@ -521,7 +544,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK)) k_ann_step
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     StepCount n;
-    ann_one_warp<C5, F16>(a, i, a.k, a.chg_span, n);
+    ann_one_warp<C5, F16, false>(a, i < a.nT, i, a.k, a.chg_span, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, 0);
 }
 
@@ -547,6 +570,28 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256
         ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), k, k >= 3 ? 2 : 0, sub, gmask, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, sub);
+}
+
+// Batch form of the warp-shared step: warp w of the grid-stride loop takes
+// the global targets [32 w, 32 w + 32), which may belong to several clips.
+template <bool C5, bool F16>
+__global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
+    k_ann_step_batch_warp(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, int k,
+                          unsigned long long *ctr)
+{
+    const int total = __ldg(prefix + n);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x / 32);
+    StepCount cnt;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32; w * 32 < total; w += warps) {
+        const int g = w * 32 + lane;
+        const bool active = g < total;
+        const int c = active ? find_segment(prefix, n, g) : 0;
+        const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
+        // one sweep per iteration: the same neighbours were judged two sweeps ago
+        ann_one_warp<C5, F16, true>(a, active, active ? g - __ldg(prefix + c) : 0, k, k >= 3 ? 2 : 0, cnt);
+    }
+    flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, 0);
 }
 
 template <bool C5, int G, bool PARTIAL, bool F16>
@@ -599,6 +644,14 @@ template <bool F16>
 void launch_ann_step_batch_impl(const BatchClip *clips, const int *tprefix, int n, int total, int k, bool c5,
                                 unsigned long long *ctr, int lanes, cudaStream_t st)
 {
+    if (lanes == 32) {
+        const int grid = persistent_grid(total, 2 * (256 / STEP_BLOCK), STEP_BLOCK);
+        if (c5)
+            k_ann_step_batch_warp<true, F16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr);
+        else
+            k_ann_step_batch_warp<false, F16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr);
+        return;
+    }
     switch ((lanes > 0 ? lanes : pick_group(total)) * 2 + (c5 ? 1 : 0)) {
     case 2: launch_ann_step_batch_g<false, 1, F16>(clips, tprefix, n, total, k, ctr, st); break;
     case 3: launch_ann_step_batch_g<true, 1, F16>(clips, tprefix, n, total, k, ctr, st); break;

@@ -72,7 +72,7 @@ int tuned_lanes(uint64_t key, cudaStream_t st, Launch launch, bool with_warp = f
     unsigned long long *scratch = tune_scratch();
     if (!scratch)
         return 0;
-    // 32: the warp-shared form of the single-clip step (k_ann_step_warp)
+    // 32: the warp-shared form of the step (k_ann_step_warp, k_ann_step_batch_warp)
     static const int Gs[5] = {1, 2, 4, 8, 32};
     const int nG = with_warp ? 5 : 4;
     cudaEvent_t ev[6];
@@ -161,7 +161,7 @@ vi_status vi_tune_import(const char *text)
             break;
         if (std::sscanf(p, "%u %u %u %u %d %d%n", &dev, &fam, &c5, &f16, &bucket, &G, &used) != 6 ||
             dev >= 64 || fam > 3 || c5 > 1 || f16 > 1 || bucket < 0 || bucket > 0x3FFFFFFF ||
-            !(G == 1 || G == 2 || G == 4 || G == 8 || (G == 32 && fam == TUNE_STEP)))
+            !(G == 1 || G == 2 || G == 4 || G == 8 || (G == 32 && (fam == TUNE_STEP || fam == TUNE_STEP_BATCH))))
             return VI_ERR_ARG;
         add[((uint64_t)dev << 40) | ((uint64_t)fam << 32) | ((uint64_t)c5 << 31) | ((uint64_t)f16 << 30) |
             (uint64_t)bucket] = G;
@@ -234,10 +234,13 @@ void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, in
         const uint64_t key = tune_key(TUNE_STEP_BATCH, c5, f16, total_targets);
         // as in launch_ann_step: tuned on the first sweep with the change-flag rule (k >= 3)
         lanes = k < 3 ? known_lanes(key)
-                      : tuned_lanes(key, st, [&](int G, unsigned long long *scr) {
-                            VI_COUNT_LAUNCH();
-                            run(G, scr);
-                        });
+                      : tuned_lanes(
+                            key, st,
+                            [&](int G, unsigned long long *scr) {
+                                VI_COUNT_LAUNCH();
+                                run(G, scr);
+                            },
+                            true);
     }
     run(lanes, ctr);
 }

@@ -42,9 +42,11 @@ def _alone(clip, seed, tag, with_evals=False):
     return out, phi, st["outer"][:clip.levels]
 
 
-def test_batch_equals_alone():
+@pytest.mark.parametrize("lanes", [0, 32])
+def test_batch_equals_alone(lanes):
+    # lanes 32: the warp-shared step, whose warps straddle clip boundaries
     clips = [_clip(s) for s in SPECS]
-    with vi.Batch() as b:
+    with vi.Batch(lanes_per_target=lanes) as b:
         ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=100 + i, clip=i) for i, c in enumerate(clips)]
         b.run()
         alone_evals = 0
@@ -101,3 +103,20 @@ def test_batch_multi_radius_search_equals_alone():
             assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
         with pytest.raises(vi.ViError):
             b.add(clips[0].rgb, clips[0].mask, sub_sweeps=2)
+
+
+def test_warp_shared_batch_mixed_search_modes():
+    # clips with Eq. 3 and with the multi-radius search (different numbers of
+    # random candidates, different r_max) share warps of the warp-shared step
+    clips = [_clip(s) for s in SPECS[:5]]
+    modes = [1, 0, 1, 0, 1]
+    with vi.Batch(lanes_per_target=32) as b:
+        ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=400 + i, clip=i, rs_mode=m)
+               for i, (c, m) in enumerate(zip(clips, modes))]
+        b.run()
+        for i, (cid, c, m) in enumerate(zip(ids, clips, modes)):
+            with vi.Context(levels=c.levels, seed=400 + i, clip=i, rs_mode=m) as ctx:
+                ctx.upload(c.rgb, c.mask)
+                ctx.run()
+                want = ctx.fetch_result()
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
