@@ -83,11 +83,11 @@ typedef struct {
     uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
     int lanes_per_target; /* GPU lanes sharing one target in the search kernels:
                              0 = chosen per level from its size, or 1, 2, 4, 8;
-                             32, 64, 128 = warp-shared: in the PatchMatch
-                             step 32, 16 or 8 lanes of a warp own a target
-                             each and all 32 lanes are shared out among the
-                             candidates that need a distance (the rescore then
-                             uses 1); never changes a result, only the speed */
+                             32 = warp-shared: in the PatchMatch step each
+                             lane owns a target and the lanes of a warp are
+                             shared out among the candidates that need a
+                             distance (the rescore then uses 1); never changes
+                             a result, only the speed */
     int stream_priority; /* priority of the stream a context creates for itself
                             (vi_ctx_create with cuda_stream NULL): 0 default,
                             lower = scheduled first; clamped to the device's
@@ -400,8 +400,8 @@ vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *a
  * sweeps skip no candidate and would favour other choices), of a kernel
  * family for a target count (per device, channels,
  * storage, quarter-octave bucket of the count) is run once with every lane
- * group size in {1, 2, 4, 8} (and the warp-shared forms, 32, 64 and 128,
- * for the step kernels), timed, and the fastest is kept for the
+ * group size in {1, 2, 4, 8} (and the warp-shared form, 32, for the
+ * step kernels), timed, and the fastest is kept for the
  * process. vi_tune_export writes the table as text lines
  * "device family c5 fp16 bucket lanes" (family 0 step, 1 batch step, 2
  * rescore, 3 batch rescore) into buf (cap bytes, NUL-terminated, truncated

@@ -538,21 +538,15 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, PARTIAL>() * (2
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, sub);
 }
 
-// OWN targets per warp (lanes 0 .. OWN-1 own one each), candidates' gathers
-// shared by all 32 lanes (lanes_per_target = 32, 64, 128 for OWN = 32, 16, 8:
-// fewer owners per warp give small levels more warps).
-template <bool C5, bool F16, int OWN>
+// One target per lane, candidates' gathers shared by the warp (lanes = 32).
+template <bool C5, bool F16>
 __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK)) k_ann_step_warp(const AnnArgs a)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * OWN + lane;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     StepCount n;
-    ann_one_warp<C5, F16, false>(a, lane < OWN && i < a.nT, i, a.k, a.chg_span, n);
+    ann_one_warp<C5, F16, false>(a, i < a.nT, i, a.k, a.chg_span, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, 0);
 }
-
-// Targets per warp of a warp-shared lane code (32, 64, 128), else 0.
-inline int warp_owners(int lanes) { return lanes == 32 ? 32 : lanes == 64 ? 16 : lanes == 128 ? 8 : 0; }
 
 // Batch form: the targets of n clips in one persistent launch. Clip c owns
 // the global target indices [prefix[c], prefix[c+1]) and is described by
@@ -579,8 +573,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256
 }
 
 // Batch form of the warp-shared step: warp w of the grid-stride loop takes
-// the global targets [OWN w, OWN w + OWN), which may belong to several clips.
-template <bool C5, bool F16, int OWN>
+// the global targets [32 w, 32 w + 32), which may belong to several clips.
+template <bool C5, bool F16>
 __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
     k_ann_step_batch_warp(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, int k,
                           unsigned long long *ctr)
@@ -589,9 +583,9 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x / 32);
     StepCount cnt;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32; w * OWN < total; w += warps) {
-        const int g = w * OWN + lane;
-        const bool active = lane < OWN && g < total;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32; w * 32 < total; w += warps) {
+        const int g = w * 32 + lane;
+        const bool active = g < total;
         const int c = active ? find_segment(prefix, n, g) : 0;
         const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
         // one sweep per iteration: the same neighbours were judged two sweeps ago
@@ -617,16 +611,12 @@ void launch_ann_step_impl(const AnnArgs &a, bool c5, cudaStream_t st)
             launch_ann_step_g<false, 8, true, false>(a, st);
         return;
     }
-    if (const int own = warp_owners(a.lanes)) {
-        const int grid = blocks_for(((long long)a.nT + own - 1) / own * 32, STEP_BLOCK);
-        switch (own * 2 + (c5 ? 1 : 0)) {
-        case 64: k_ann_step_warp<false, F16, 32><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        case 65: k_ann_step_warp<true, F16, 32><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        case 32: k_ann_step_warp<false, F16, 16><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        case 33: k_ann_step_warp<true, F16, 16><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        case 16: k_ann_step_warp<false, F16, 8><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        default: k_ann_step_warp<true, F16, 8><<<grid, STEP_BLOCK, 0, st>>>(a); break;
-        }
+    if (a.lanes == 32) {
+        const int grid = blocks_for(a.nT, STEP_BLOCK);
+        if (c5)
+            k_ann_step_warp<true, F16><<<grid, STEP_BLOCK, 0, st>>>(a);
+        else
+            k_ann_step_warp<false, F16><<<grid, STEP_BLOCK, 0, st>>>(a);
         return;
     }
     switch ((a.lanes > 0 ? a.lanes : pick_group(a.nT)) * 2 + (c5 ? 1 : 0)) {
@@ -654,17 +644,12 @@ template <bool F16>
 void launch_ann_step_batch_impl(const BatchClip *clips, const int *tprefix, int n, int total, int k, bool c5,
                                 unsigned long long *ctr, int lanes, cudaStream_t st)
 {
-    if (const int own = warp_owners(lanes)) {
-        const int grid = persistent_grid(((long long)total + own - 1) / own * 32, 2 * (256 / STEP_BLOCK),
-                                         STEP_BLOCK);
-        switch (own * 2 + (c5 ? 1 : 0)) {
-        case 64: k_ann_step_batch_warp<false, F16, 32><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        case 65: k_ann_step_batch_warp<true, F16, 32><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        case 32: k_ann_step_batch_warp<false, F16, 16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        case 33: k_ann_step_batch_warp<true, F16, 16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        case 16: k_ann_step_batch_warp<false, F16, 8><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        default: k_ann_step_batch_warp<true, F16, 8><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr); break;
-        }
+    if (lanes == 32) {
+        const int grid = persistent_grid(total, 2 * (256 / STEP_BLOCK), STEP_BLOCK);
+        if (c5)
+            k_ann_step_batch_warp<true, F16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr);
+        else
+            k_ann_step_batch_warp<false, F16><<<grid, STEP_BLOCK, 0, st>>>(clips, tprefix, n, k, ctr);
         return;
     }
     switch ((lanes > 0 ? lanes : pick_group(total)) * 2 + (c5 ? 1 : 0)) {

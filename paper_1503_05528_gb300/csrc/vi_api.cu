@@ -155,8 +155,7 @@ vi_status check_config(vi_ctx *ctx, const vi_config *c)
         c->time_subsample < 0 || c->time_subsample > 1 ||
         c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
-          c->lanes_per_target == 4 || c->lanes_per_target == 8 || c->lanes_per_target == 32 ||
-          c->lanes_per_target == 64 || c->lanes_per_target == 128))
+          c->lanes_per_target == 4 || c->lanes_per_target == 8 || c->lanes_per_target == 32))
         return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
     // rho must be 2^-m, m >= 1
     int m = 0;
@@ -193,9 +192,9 @@ vi_status ensure_partials2(vi_ctx *ctx, int n_blocks)
     return VI_OK;
 }
 
-// Lanes per target of the rescore kernels: the warp-shared forms (32, 64,
-// 128) exist for the step only; the rescore then uses one lane per target.
-static int rescore_lanes(int lanes) { return lanes >= 32 ? 1 : lanes; }
+// Lanes per target of the rescore kernels: the warp-shared form (32) exists
+// for the step only; the rescore then uses one lane per target.
+static int rescore_lanes(int lanes) { return lanes == 32 ? 1 : lanes; }
 
 // One launch of the PatchMatch step kernel.
 vi_status step_launch(vi_ctx *ctx, const AnnArgs &a)

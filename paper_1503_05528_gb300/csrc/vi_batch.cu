@@ -352,10 +352,9 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
         BCK(cudaMemcpyAsync(b->d_prefix, b->h_prefix, sizeof(int) * 3 * (b->cap + 1), cudaMemcpyHostToDevice,
                             st));
         const int *tpre = b->d_prefix, *hpre = b->d_prefix + b->cap + 1, *cpre = b->d_prefix + 2 * (b->cap + 1);
-        // the warp-shared forms (32, 64, 128) exist for the step; the rescore
-        // then uses one lane per target
+        // the warp-shared form (32) exists for the step; the rescore then uses one lane per target
         const int lanes = b->cfg.lanes_per_target;
-        const int rescore_lanes = lanes >= 32 ? 1 : lanes;
+        const int rescore_lanes = lanes == 32 ? 1 : lanes;
         launch_rescore_batch(b->d_clips, tpre, n, (int)tot_t, c5, b->counters, rescore_lanes, st);
         for (int k = 1; k <= b->cfg.n_pm; ++k) {
             cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -42,10 +42,9 @@ def _alone(clip, seed, tag, with_evals=False):
     return out, phi, st["outer"][:clip.levels]
 
 
-@pytest.mark.parametrize("lanes", [0, 32, 128])
+@pytest.mark.parametrize("lanes", [0, 32])
 def test_batch_equals_alone(lanes):
-    # lanes 32 / 128: the warp-shared step (32 / 8 targets per warp), whose
-    # warps straddle clip boundaries
+    # lanes 32: the warp-shared step, whose warps straddle clip boundaries
     clips = [_clip(s) for s in SPECS]
     with vi.Batch(lanes_per_target=lanes) as b:
         ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=100 + i, clip=i) for i, c in enumerate(clips)]

@@ -113,12 +113,11 @@ def test_init_nnf_bit_exact(case):
             assert (gphi[m] == ophi[m]).all()
 
 
-@pytest.mark.parametrize("lanes", [0, 1, 8, 32, 64, 128])
+@pytest.mark.parametrize("lanes", [0, 1, 8, 32])
 @pytest.mark.parametrize("case,n_pm,call", [("tiny_rgb", 10, 0), ("layered_tex", 10, 3),
                                             ("odd_sizes", 3, 17), ("layered_tex", 1, 0)])
 def test_ann_bit_exact(case, n_pm, call, lanes):
-    # every lane choice (0: autotuned; 32, 64, 128: warp-shared with 32, 16, 8
-    # targets per warp) gives the oracle's result
+    # every lane choice (0: autotuned; 32: warp-shared) gives the oracle's result
     clip, pyr, ctx = _make(case, seed=31, n_pm=n_pm, lanes_per_target=lanes)
     with ctx:
         for level, lv in enumerate(pyr):
@@ -138,7 +137,7 @@ def test_ann_bit_exact(case, n_pm, call, lanes):
             assert g_evals == o_evals
 
 
-@pytest.mark.parametrize("lanes", [0, 32, 128])
+@pytest.mark.parametrize("lanes", [0, 32])
 @pytest.mark.parametrize("case,n_pm,rs_mode,sub_sweeps", [("tiny_rgb", 10, 1, 1), ("layered_tex", 4, 1, 3),
                                                          ("odd_sizes", 3, 0, 2), ("layered_tex", 5, 0, 4)])
 def test_ann_options_bit_exact(case, n_pm, rs_mode, sub_sweeps, lanes):
