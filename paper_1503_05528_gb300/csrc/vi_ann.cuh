@@ -79,12 +79,13 @@ inline int persistent_grid(long long threads, int blocks_per_sm = 8, int block =
     return (int)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
-// Threads per block of the step kernels. With 128 threads a block's warps
-// finish closer together than with 256 (a target's work varies a lot: a
-// rejected candidate costs one slice, an accepted one five), so the SM
-// refills sooner: 22.9 against 23.4 ms (320x240x60) and 261 against 276 ms
-// (1280x720x100) per inpainting.
-constexpr int STEP_BLOCK = 128;
+// Threads per block of the step kernels. Smaller blocks' warps finish closer
+// together (a target's work varies a lot: a rejected candidate costs one
+// slice, an accepted one five), so the SM refills sooner. Per inpainting,
+// 128 threads against 256: 22.9 against 23.4 ms (320x240x60) and 261
+// against 276 ms (1280x720x100); 64 against 128, with the warp-shared step:
+// 19.84 against 20.04 ms (320x240x60).
+constexpr int STEP_BLOCK = 64;
 
 // Resident blocks of 256 threads per SM the step kernels are compiled for
 // (twice as many of STEP_BLOCK): the register budget per thread is
