@@ -45,14 +45,15 @@ BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
 BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
 BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the FP16 copy
 
-# DRAM bytes (read + write) per launch of the PatchMatch step kernel, averaged
-# over the step launches of one inpainting of the default workload with FP32
-# storage, and the source voxels those launches gathered per launch, from one
-# ncu capture (profiles/k_ann_step_layered_320x240x60.md), as a dict with
-# keys workload, storage, bytes, gathered_voxels. Applies to that workload and
-# storage only; None while the kernel has changed since the capture.
-NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32",
-                    "bytes": (3433.98e6 + 25.16e6) / 330, "gathered_voxels": 71711827.8 / 20}
+# DRAM bytes (read + write) per launch of the PatchMatch step kernels,
+# averaged over the step launches of one inpainting of the default workload
+# in its default configuration (FP32 storage, Eq. 3 random search, one sweep
+# per iteration, autotuned lanes, no realignment), and the source voxels
+# those launches gathered per launch, from one ncu capture
+# (profiles/k_ann_step_layered_320x240x60.md). Applies to that configuration
+# only; None while the kernels have changed since the capture.
+NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32", "rs_mode": "eq3", "sub_sweeps": 1,
+                    "bytes": (3442.53e6 + 25.09e6) / 330, "gathered_voxels": 70003159.6 / 20}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
@@ -386,7 +387,8 @@ def run_gpu(args):
     achieved = gathered_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     traffic = None
     if (NCU_STEP_TRAFFIC and step_launches and NCU_STEP_TRAFFIC["workload"] == args.workload
-            and NCU_STEP_TRAFFIC["storage"] == args.storage):
+            and NCU_STEP_TRAFFIC["storage"] == args.storage and NCU_STEP_TRAFFIC["rs_mode"] == args.rs_mode
+            and NCU_STEP_TRAFFIC["sub_sweeps"] == args.sub_sweeps and not args.lanes and not args.realign):
         per_voxel = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["gathered_voxels"]
         traffic = per_voxel * step_gathered / step_launches
     line = {
