@@ -411,7 +411,7 @@ def run_gpu(args):
                        "pass_rate": passed / screened if screened else None,
                        "fp16_voxels": step_gathered_h, "fp32_voxels": step_gathered}
                       if storage else None),
-        "roofline": {"bound": "hbm", "kernel": "k_ann_step (PatchMatch propagation + random search)",
+        "roofline": {"bound": "hbm", "kernel": "k_ann_step + k_ann_step_warp (PatchMatch propagation + random search, every level)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": traffic,
@@ -563,7 +563,7 @@ def run_batch(args):
                              "inpainted_voxels_per_s": sm[2] / mx[3], "seconds": mx[3],
                              "note": "the same 48 clips one after another through vi_run; "
                                      "bit-identical results"},
-        "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
+        "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch + k_ann_step_batch_warp (PatchMatch step, all clips)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                      "traffic": None,
@@ -740,7 +740,7 @@ def run_serve(args):
                             "inpainted_voxels_per_s": sm[2] / mx[3],
                             "busy_s": float(sum(service)),
                             "note": "same arrivals, one request at a time through vi_run"},
-        "roofline": ({"bound": "hbm", "kernel": "k_ann_step_batch (PatchMatch step, all clips)",
+        "roofline": ({"bound": "hbm", "kernel": "k_ann_step_batch + k_ann_step_batch_warp (PatchMatch step, all clips)",
                       "achieved": achieved, "peak": peak, "unit": "GB/s",
                       "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                       "traffic": None,
