@@ -153,7 +153,9 @@ const char *vi_last_error(const vi_ctx *ctx);
 int vi_auto_levels(const uint8_t *mask_host, int W, int H, int T);
 
 /* Device bytes a context will hold for a W x H x T clip with the given
- * number of occluded voxels (an upper bound used for admission). */
+ * number of occluded voxels (an upper bound used for admission; the lists
+ * are bounded by the voxel count, so the bound does not depend on
+ * hole_voxels at present). */
 size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long hole_voxels);
 
 /* Copies a video and its occlusion mask into the context and allocates the
@@ -346,7 +348,8 @@ vi_status vi_server_release(vi_server *s, uint64_t ticket, char *err_buf, int er
 /* Requests waiting, requests running, footprint bytes admitted. Nullable. */
 vi_status vi_server_info(vi_server *s, int *queued, int *running, size_t *bytes_in_use);
 
-/* Lets running requests finish, fails the queued ones, joins the workers. */
+/* Lets running requests finish, fails the queued ones, joins the workers and
+ * frees the server. No other call on s may be in progress or follow. */
 void vi_server_destroy(vi_server *s);
 
 /* ---------------------------------------------------------------------------

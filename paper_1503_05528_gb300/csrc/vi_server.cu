@@ -80,7 +80,7 @@ void run_job(vi_server *s, Job &job)
     cfg.stream_priority = size_priority((long long)job.W * job.H * job.T);
     vi_ctx *ctx = nullptr;
     vi_status st = vi_ctx_create(&cfg, nullptr, &ctx);
-    std::string err;
+    const char *err = nullptr;
     if (st == VI_OK)
         st = vi_upload(ctx, job.rgb, job.mask, job.W, job.H, job.T, job.ptr_is_device);
     if (st == VI_OK)
@@ -92,13 +92,18 @@ void run_job(vi_server *s, Job &job)
         st = VI_ERR_CUDA;
         err = cudaGetErrorString(cudaGetLastError());
     } else if (st != VI_OK) {
-        err = ctx ? vi_last_error(ctx) : "vi_ctx_create failed: " + std::to_string((int)st);
+        err = ctx ? vi_last_error(ctx) : "vi_ctx_create failed";
+    }
+    std::string msg;
+    try {
+        msg = err ? err : "";   // copied before the context (which owns the text) goes
+    } catch (...) {             // no room for the message: the status still says what failed
     }
     if (ctx)
         vi_ctx_destroy(ctx);
     std::lock_guard<std::mutex> lock(s->mu);
     job.status = st;
-    job.err = err;
+    job.err.swap(msg);
     job.state = st == VI_OK ? JOB_DONE : JOB_FAILED;
 }
 
@@ -188,20 +193,24 @@ vi_status vi_server_submit(vi_server *s, const vi_config *cfg, const float *rgb,
         c = *cfg;
     else
         vi_config_default(&c);
-    long long holes = 0;
-    if (!ptr_is_device) {
-        const size_t V = (size_t)W * H * T;
-        for (size_t i = 0; i < V; ++i)
-            holes += mask[i] != 0;
-    }
-    const size_t fp = vi_footprint_bytes(&c, W, H, T, holes);
+    // the footprint bound does not depend on the hole size, so the mask is not scanned here
+    const size_t fp = vi_footprint_bytes(&c, W, H, T, 0);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop)
         return VI_ERR_STATE;
     if (fp > s->budget)
         return VI_ERR_TOO_LARGE;
-    const uint64_t t = s->next_ticket++;
-    Job &j = s->jobs[t];
+    const uint64_t t = s->next_ticket;
+    Job *jp = nullptr;
+    try {
+        jp = &s->jobs[t];
+        s->queue.push_back(t);
+    } catch (...) {
+        s->jobs.erase(t);
+        return VI_ERR_OOM;
+    }
+    ++s->next_ticket;
+    Job &j = *jp;
     j.ticket = t;
     j.cfg = c;
     j.rgb = rgb;
@@ -212,7 +221,6 @@ vi_status vi_server_submit(vi_server *s, const vi_config *cfg, const float *rgb,
     j.T = T;
     j.ptr_is_device = ptr_is_device;
     j.footprint = fp;
-    s->queue.push_back(t);
     *ticket = t;
     s->cv.notify_all();
     return VI_OK;
