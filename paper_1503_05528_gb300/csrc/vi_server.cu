@@ -139,12 +139,15 @@ void worker_loop(vi_server *s)
         s->queue.pop_front();
         Job &job = s->jobs[t];
         job.state = JOB_RUNNING;
-        s->used += job.footprint;
+        // once run_job marks the job finished, its owner may release it at
+        // any time, so nothing of it is read afterwards
+        const size_t fp = job.footprint;
+        s->used += fp;
         ++s->running;
         lock.unlock();
         run_job(s, job);
         lock.lock();
-        s->used -= job.footprint;
+        s->used -= fp;
         --s->running;
         s->cv.notify_all();
         s->done_cv.notify_all();
