@@ -73,7 +73,9 @@ struct vi_server {
 
 namespace {
 
-void run_job(vi_server *s, Job &job)
+// Runs one admitted job (footprint fp) and, in one critical section, marks it
+// finished and returns its memory and slot.
+void run_job(vi_server *s, Job &job, size_t fp)
 {
     cudaSetDevice(s->device);
     vi_config cfg = job.cfg;
@@ -105,6 +107,10 @@ void run_job(vi_server *s, Job &job)
     job.status = st;
     job.err.swap(msg);
     job.state = st == VI_OK ? JOB_DONE : JOB_FAILED;
+    s->used -= fp;
+    --s->running;
+    s->cv.notify_all();
+    s->done_cv.notify_all();
 }
 
 void worker_loop(vi_server *s)
@@ -130,7 +136,10 @@ void worker_loop(vi_server *s)
                 s->queue.pop_front();
                 j.state = JOB_FAILED;
                 j.status = VI_ERR_STATE;
-                j.err = "server destroyed";
+                try {
+                    j.err = "server destroyed";
+                } catch (...) {
+                }
             }
             s->done_cv.notify_all();
             return;
@@ -145,12 +154,8 @@ void worker_loop(vi_server *s)
         s->used += fp;
         ++s->running;
         lock.unlock();
-        run_job(s, job);
+        run_job(s, job, fp);
         lock.lock();
-        s->used -= fp;
-        --s->running;
-        s->cv.notify_all();
-        s->done_cv.notify_all();
     }
 }
 
