@@ -490,7 +490,7 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
     return total + (16u << 20);
 }
 
-vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
+static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
                     int ptr_is_device)
 {
     if (!ctx)
@@ -564,6 +564,17 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
     ctx->uploaded = true;
     ctx->err.clear();
     return VI_OK;
+}
+
+vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                    int ptr_is_device)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_upload_body(ctx, rgb, mask, W, H, T, ptr_is_device);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
 }
 
 vi_status vi_build_pyramid(vi_ctx *ctx)
@@ -947,7 +958,7 @@ vi_status vi_set_channels(vi_ctx *ctx, int level, const float *in, int ptr_is_de
     return VI_OK;
 }
 
-vi_status vi_get_nnf(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host)
+static vi_status vi_get_nnf_body(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host)
 {
     if (!ctx)
         return VI_ERR_ARG;
@@ -975,7 +986,17 @@ vi_status vi_get_nnf(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host)
     return VI_OK;
 }
 
-vi_status vi_set_nnf(vi_ctx *ctx, int level, const int32_t *phi_host, const float *d2_host)
+vi_status vi_get_nnf(vi_ctx *ctx, int level, int32_t *phi_host, float *d2_host)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_get_nnf_body(ctx, level, phi_host, d2_host);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_set_nnf_body(vi_ctx *ctx, int level, const int32_t *phi_host, const float *d2_host)
 {
     if (!ctx)
         return VI_ERR_ARG;
@@ -1002,6 +1023,16 @@ vi_status vi_set_nnf(vi_ctx *ctx, int level, const int32_t *phi_host, const floa
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return VI_OK;
+}
+
+vi_status vi_set_nnf(vi_ctx *ctx, int level, const int32_t *phi_host, const float *d2_host)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_set_nnf_body(ctx, level, phi_host, d2_host);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
 }
 
 vi_status vi_get_masks(vi_ctx *ctx, int level, uint8_t *code_host)

@@ -232,7 +232,7 @@ void vi_batch_destroy(vi_batch *b)
 
 const char *vi_batch_last_error(const vi_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
-vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, const uint8_t *mask, int W,
+static vi_status vi_batch_add_body(vi_batch *b, const vi_config *job_cfg, const float *rgb, const uint8_t *mask, int W,
                        int H, int T, int ptr_is_device, int *id_out)
 {
     if (!b || !id_out)
@@ -263,7 +263,18 @@ vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, 
     return advance(b, b->clips.back());
 }
 
-vi_status vi_batch_step(vi_batch *b, int *n_active)
+vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, const uint8_t *mask, int W,
+                       int H, int T, int ptr_is_device, int *id_out)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_batch_add_body(b, job_cfg, rgb, mask, W, H, T, ptr_is_device, id_out);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
 {
     if (!b)
         return VI_ERR_ARG;
@@ -405,6 +416,16 @@ vi_status vi_batch_step(vi_batch *b, int *n_active)
         *n_active = m;
     }
     return VI_OK;
+}
+
+vi_status vi_batch_step(vi_batch *b, int *n_active)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_batch_step_body(b, n_active);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
 }
 
 vi_status vi_batch_run(vi_batch *b)

@@ -493,7 +493,7 @@ int vi_affine_levels(int W, int H)
     return L;
 }
 
-vi_status vi_affine_estimate(const float *rgb, const uint8_t *mask, int W, int H, int T, int ptr_is_device,
+static vi_status vi_affine_estimate_body(const float *rgb, const uint8_t *mask, int W, int H, int T, int ptr_is_device,
                              int levels, int iters, double *theta_out, void *cuda_stream)
 {
     if (!rgb || !mask || !theta_out || !sizes_ok(W, H, T) || iters < 0 || iters > 1000 || levels < 0 ||
@@ -596,7 +596,18 @@ vi_status vi_affine_estimate(const float *rgb, const uint8_t *mask, int W, int H
     return VI_OK;
 }
 
-vi_status vi_affine_to_reference(const double *theta_pairs, int T, double *to_ref_out)
+vi_status vi_affine_estimate(const float *rgb, const uint8_t *mask, int W, int H, int T, int ptr_is_device,
+                             int levels, int iters, double *theta_out, void *cuda_stream)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_affine_estimate_body(rgb, mask, W, H, T, ptr_is_device, levels, iters, theta_out, cuda_stream);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_affine_to_reference_body(const double *theta_pairs, int T, double *to_ref_out)
 {
     if (!to_ref_out || T <= 0 || (T > 1 && !theta_pairs))
         return rfail(VI_ERR_ARG, "vi_affine_to_reference: bad argument");
@@ -613,7 +624,17 @@ vi_status vi_affine_to_reference(const double *theta_pairs, int T, double *to_re
     return VI_OK;
 }
 
-vi_status vi_affine_align(const float *rgb, const uint8_t *mask, int W, int H, int T, const double *to_ref,
+vi_status vi_affine_to_reference(const double *theta_pairs, int T, double *to_ref_out)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_affine_to_reference_body(theta_pairs, T, to_ref_out);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_affine_align_body(const float *rgb, const uint8_t *mask, int W, int H, int T, const double *to_ref,
                           float *rgb_out, uint8_t *mask_out, int ptr_is_device, void *cuda_stream)
 {
     if (!rgb || !mask || !to_ref || !rgb_out || !mask_out || !sizes_ok(W, H, T))
@@ -649,7 +670,18 @@ vi_status vi_affine_align(const float *rgb, const uint8_t *mask, int W, int H, i
     return VI_OK;
 }
 
-vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *aligned_result, int W, int H,
+vi_status vi_affine_align(const float *rgb, const uint8_t *mask, int W, int H, int T, const double *to_ref,
+                          float *rgb_out, uint8_t *mask_out, int ptr_is_device, void *cuda_stream)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_affine_align_body(rgb, mask, W, H, T, to_ref, rgb_out, mask_out, ptr_is_device, cuda_stream);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_affine_unwarp_body(const float *rgb, const uint8_t *mask, const float *aligned_result, int W, int H,
                            int T, const double *to_ref, float *rgb_out, int ptr_is_device, void *cuda_stream)
 {
     if (!rgb || !mask || !aligned_result || !to_ref || !rgb_out || !sizes_ok(W, H, T))
@@ -684,6 +716,17 @@ vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *a
         RCK(cudaMemcpyAsync(rgb_out, dout, V * 3 * sizeof(float), cudaMemcpyDeviceToHost, st));
     RCK(cudaStreamSynchronize(st));
     return VI_OK;
+}
+
+vi_status vi_affine_unwarp(const float *rgb, const uint8_t *mask, const float *aligned_result, int W, int H,
+                           int T, const double *to_ref, float *rgb_out, int ptr_is_device, void *cuda_stream)
+{
+    // host allocations proportional to the clip may throw; no exception crosses the C ABI
+    try {
+        return vi_affine_unwarp_body(rgb, mask, aligned_result, W, H, T, to_ref, rgb_out, ptr_is_device, cuda_stream);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
 }
 
 }  // extern "C"
