@@ -58,13 +58,13 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
         decode(p, L.W, L.HW, px, py, pt);
         const bool interior = px >= 2 && px < L.W - 2 && py >= 2 && py < L.H - 2 && pt >= 2 && pt < L.T - 2;
         float dq[4];
-        int sv[4];   // source voxel p + phi(q) of each contributor
+        int qv[4];
         unsigned okm = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const unsigned o = vl.off[m];
             dq[m] = 0.0f;
-            sv[m] = 0;
+            qv[m] = 0;
             if (o) {
                 const int ox = (int)(o & 0xFFu) - 2, oy = (int)((o >> 8) & 0xFFu) - 2,
                           ot = (int)((o >> 16) & 0xFFu) - 2;
@@ -79,7 +79,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                         if (d < __int_as_float(0x7f800000) &&
                             inside(L, px + f.dx, py + f.dy, pt + f.dt)) {
                             dq[m] = d;
-                            sv[m] = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
+                            qv[m] = q;
                             okm |= 1u << m;
                         }
                     }
@@ -156,7 +156,8 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                     w = dq[m] > 0.0f ? expf(-(dq[m] * inv2s)) : 1.0f;   // inv2s may be +inf
                 else
                     w = (dq[m] == 0.0f) ? 1.0f : 0.0f;
-                const int s = sv[m];
+                const Shift f = a.phi[qv[m]];
+                const int s = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
                 const float4 v = L.x4[s];
                 n0 = fmaf(w, v.x, n0);
                 n1 = fmaf(w, v.y, n1);
@@ -173,32 +174,15 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
             if (C5)
                 n4 = warp_sum(n4);
             den = warp_sum(den);
-            // Lane c < 4 (and lane 4 with C5) divides and writes channel c of
-            // lane 0's totals, so the five divisions run side by side; lane 0
-            // adds the colour changes in R, G, B order.
-            const unsigned FULL = 0xffffffffu;
-            const float b0 = __shfl_sync(FULL, n0, 0), b1 = __shfl_sync(FULL, n1, 0),
-                        b2 = __shfl_sync(FULL, n2, 0), b3 = __shfl_sync(FULL, n3, 0),
-                        b4 = C5 ? __shfl_sync(FULL, n4, 0) : 0.0f, bden = __shfl_sync(FULL, den, 0);
-            const float num = lane == 0 ? b0 : lane == 1 ? b1 : lane == 2 ? b2 : lane == 3 ? b3 : b4;
-            float nw = 0.0f, dc = 0.0f;
-            if (lane < 4) {
-                float *xp = reinterpret_cast<float *>(L.x4 + p) + lane;
-                nw = num / bden;
-                dc = fabsf(nw - *xp);
-                *xp = nw;
-            } else if (C5 && lane == 4) {
-                L.x1[p] = num / bden;
-            }
-            const float d1 = __shfl_sync(FULL, dc, 1), d2c = __shfl_sync(FULL, dc, 2);
-            if (L.h4) {
-                const float nw1 = __shfl_sync(FULL, nw, 1), nw2 = __shfl_sync(FULL, nw, 2),
-                            nw3 = __shfl_sync(FULL, nw, 3);
-                if (lane == 0)
-                    shadow_store_raise(L, p, make_float4(nw, nw1, nw2, nw3));
-            }
             if (lane == 0) {
-                change = dc + d1 + d2c;
+                const float4 old = L.x4[p];
+                const float4 nw = make_float4(n0 / den, n1 / den, n2 / den, n3 / den);
+                change = fabsf(nw.x - old.x) + fabsf(nw.y - old.y) + fabsf(nw.z - old.z);
+                L.x4[p] = nw;
+                if (C5)
+                    L.x1[p] = n4 / den;
+                if (L.h4)
+                    shadow_store_raise(L, p, nw);
                 if (a.hp)
                     a.hp[p] = 0;
             }
