@@ -758,6 +758,70 @@ def run_serve(args):
     return 0
 
 
+def run_slabs(args):
+    """One clip's whole inpainting split by frames over --slabs contexts on
+    this GPU (vi_run_slabs): the decomposition a multi-GPU run of one clip
+    would use, with its boundary copies made on one device. Reports the
+    evaluation rate, the bytes exchanged per step and the same clip's time
+    through vi_run, measured in the same process; the results are identical
+    (checked here, bit for bit)."""
+    import numpy as np
+    import torch
+
+    from paper_1503_05528_gb300 import vi
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    vi.load(build_if_missing=True)
+    _tune_load(args, vi)
+    clip = make_clip(rank, args.workload)
+    rgb_d = torch.from_numpy(clip.rgb).cuda()
+    mask_d = torch.from_numpy(clip.mask).cuda()
+    out_d, ref_d = torch.empty_like(rgb_d), torch.empty_like(rgb_d)
+    stream = torch.cuda.current_stream()
+    cfg = dict(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank, lanes_per_target=args.lanes,
+               rs_mode=1 if args.rs_mode == "multi" else 0, sub_sweeps=args.sub_sweeps)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = [fn() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, out[-1]
+
+    ms, (_, st, nbytes) = timed(lambda: vi.run_slabs(rgb_d, mask_d, args.slabs, out=out_d,
+                                                     stream=stream.cuda_stream, **cfg))
+    evals = st["evals"]
+
+    def alone():
+        with vi.Context(stream=stream.cuda_stream, **cfg) as ctx:
+            ctx.upload(rgb_d, mask_d)
+            ctx.run()
+            ctx.fetch_result(ref_d)
+            return ctx.stats()["evals"]
+
+    ms1, evals1 = timed(alone)
+    torch.cuda.synchronize()
+    same = bool((out_d.view(torch.int32) == ref_d.view(torch.int32)).all().item()) and evals == evals1
+    assert same, "slab result differs from vi_run"
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "levels": clip.levels, "slabs": args.slabs,
+                       "slab_devices": "all on this GPU, one stream"},
+            "exchanged_bytes_per_step": nbytes, "identical_to_vi_run": same,
+            "vi_run": {"ms_per_step": ms1, "value": evals1 / (ms1 / 1e3), "unit": UNIT},
+            "roofline": None, "note": "the coarsest level runs in every slab's context"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -768,6 +832,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVE_WORKLOAD])
+    ap.add_argument("--slabs", type=int, default=1,
+                    help="split one clip by frames over this many contexts on this GPU (vi_run_slabs)")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: mean arrivals per second")
     ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
@@ -794,6 +860,8 @@ def main():
         return run_batch(args)
     if args.workload == SERVE_WORKLOAD:
         return run_serve(args)
+    if args.slabs > 1:
+        return run_slabs(args)
     return run_gpu(args)
 
 

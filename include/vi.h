@@ -353,6 +353,34 @@ vi_status vi_server_info(vi_server *s, int *queued, int *running, size_t *bytes_
 void vi_server_destroy(vi_server *s);
 
 /* ---------------------------------------------------------------------------
+ * Time slabs (no counterpart in the paper, whose program is not parallel):
+ * the whole inpainting of one clip, as vi_run, with the targets and occluded
+ * voxels of every level but the coarsest split by frames into n_slabs
+ * contiguous ranges (slab r: frames [r T / n, (r + 1) T / n)), each searched
+ * and reconstructed by a context of its own that holds the whole clip. The
+ * coarsest level (onion peel and its iterations) runs alike in every
+ * context. What a slab reads across its boundary is copied between the
+ * contexts: after every Jacobi sweep the shifts and change flags of the frame
+ * on each side; after a search the shifts and distances of the two frames on
+ * each side; after every vote the channels of every slab to every context;
+ * and the per-voxel changes into context 0, which sums e over the whole list
+ * in vi_run's order. The output, the iteration counts and the evaluation
+ * count are identical to vi_run's. All contexts run on the current device on
+ * one stream (cuda_stream, or one context 0 creates; NULL), which orders the
+ * copies: this is the decomposition a multi-GPU run would use, exchanging
+ * with peer copies instead. rgb, mask, rgb_out as in vi_upload /
+ * vi_fetch_result (ptr_is_device); stats_out (nullable) receives context 0's
+ * counters with every slab's evaluations; exchanged_bytes (nullable) the
+ * bytes copied between contexts. Errors: VI_ERR_ARG (n_slabs outside
+ * 1 .. min(16, T), FP16 storage, temporal subsampling; text in
+ * vi_slabs_last_error), others as vi_run.
+ * ------------------------------------------------------------------------- */
+vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                       int ptr_is_device, int n_slabs, float *rgb_out, vi_stats *stats_out,
+                       unsigned long long *exchanged_bytes, void *cuda_stream);
+const char *vi_slabs_last_error(void);
+
+/* ---------------------------------------------------------------------------
  * Affine realignment: Sec. 3.4, Algorithm 2 (AlignVideo) and the UnwarpVideo
  * step that ends Algorithm 4. The paper estimates the dominant affine motion
  * between successive frames with the robust method of Odobez and Bouthemy;

@@ -233,6 +233,51 @@ vi_status profile_end(vi_ctx *ctx, cudaEvent_t e1, int launches)
     return VI_OK;
 }
 
+// The arguments of sweep s of a search over a target list: iteration k,
+// sub-sweep j; sweep s reads buffer s & 1 and writes the other one.
+AnnArgs sweep_args(vi_ctx *ctx, int level, const int *targets, int nT, const uint8_t *tmask, uint8_t tbit,
+                   const uint8_t *excl, uint32_t tag, int k, int j, int s)
+{
+    Level &l = ctx->lv[level];
+    AnnArgs a;
+    a.L = l.view();
+    a.targets = targets;
+    a.nT = nT;
+    a.phi_in = l.phi[s & 1];
+    a.d_in = l.d2[s & 1];
+    a.phi_out = l.phi[(s + 1) & 1];
+    a.d_out = l.d2[(s + 1) & 1];
+    a.tmask = tmask;
+    a.tbit = tbit;
+    a.excl = excl;
+    a.k = k;
+    a.rmax = std::max(l.W, std::max(l.H, l.T));
+    a.rho_log2 = ctx->rho_log2;
+    a.key0 = (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull);
+    a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
+    a.tag = tag;
+    a.clip = ctx->cfg.clip;
+    a.evals = ctx->evals_dev + 1;
+    a.gathered = ctx->evals_dev + 2;
+    a.screen = ctx->evals_dev + 3;
+    a.lanes = ctx->cfg.lanes_per_target;
+    a.rs_mode = ctx->cfg.rs_mode;
+    a.do_random = j == ctx->cfg.sub_sweeps - 1;
+    // sweeps since the same targets judged the same neighbours in the same
+    // direction: the previous sub-sweep, or at the first sub-sweep of
+    // iteration k >= 3 the last of iteration k - 2
+    const int J = ctx->cfg.sub_sweeps;
+    int span = 0;
+    if (j > 0)
+        span = 1;
+    else if (k >= 3 && J + 1 <= 8)
+        span = J + 1;
+    a.chg_in = l.chg[s & 1];
+    a.chg_out = l.chg[(s + 1) & 1];
+    a.chg_span = span;
+    return a;
+}
+
 // Distances, then n_pm Jacobi sweeps (Algorithm 1) over a target list. The
 // current shift map is buffer 0; sweep k reads buffer (k-1)&1 and writes k&1,
 // so only target entries are ever read from buffer 1; after an odd count the
@@ -241,56 +286,15 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
                   uint8_t tbit, const uint8_t *excl, uint32_t tag)
 {
     Level &l = ctx->lv[level];
-    const LevelView v = l.view();
-    launch_rescore(v, targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream,
+    launch_rescore(l.view(), targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream,
                    rescore_lanes(ctx->cfg.lanes_per_target));
     CK_LAUNCH();
-    const int rmax = std::max(l.W, std::max(l.H, l.T));
     cudaEvent_t e1 = nullptr;
     TRY(profile_begin(ctx, &e1));
-    // launch s reads buffer s & 1 and writes the other one
     int s = 0;
-    for (int k = 1; k <= ctx->cfg.n_pm; ++k) {
-        for (int j = 0; j < ctx->cfg.sub_sweeps; ++j, ++s) {
-            AnnArgs a;
-            a.L = v;
-            a.targets = targets;
-            a.nT = nT;
-            a.phi_in = l.phi[s & 1];
-            a.d_in = l.d2[s & 1];
-            a.phi_out = l.phi[(s + 1) & 1];
-            a.d_out = l.d2[(s + 1) & 1];
-            a.tmask = tmask;
-            a.tbit = tbit;
-            a.excl = excl;
-            a.k = k;
-            a.rmax = rmax;
-            a.rho_log2 = ctx->rho_log2;
-            a.key0 = (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull);
-            a.key1 = (uint32_t)(ctx->cfg.seed >> 32);
-            a.tag = tag;
-            a.clip = ctx->cfg.clip;
-            a.evals = ctx->evals_dev + 1;
-            a.gathered = ctx->evals_dev + 2;
-            a.screen = ctx->evals_dev + 3;
-            a.lanes = ctx->cfg.lanes_per_target;
-            a.rs_mode = ctx->cfg.rs_mode;
-            a.do_random = j == ctx->cfg.sub_sweeps - 1;
-            // sweeps since the same targets judged the same neighbours in the
-            // same direction: the previous sub-sweep, or at the first
-            // sub-sweep of iteration k >= 3 the last of iteration k - 2
-            const int J = ctx->cfg.sub_sweeps;
-            int span = 0;
-            if (j > 0)
-                span = 1;
-            else if (k >= 3 && J + 1 <= 8)
-                span = J + 1;
-            a.chg_in = l.chg[s & 1];
-            a.chg_out = l.chg[(s + 1) & 1];
-            a.chg_span = span;
-            TRY(step_launch(ctx, a));
-        }
-    }
+    for (int k = 1; k <= ctx->cfg.n_pm; ++k)
+        for (int j = 0; j < ctx->cfg.sub_sweeps; ++j, ++s)
+            TRY(step_launch(ctx, sweep_args(ctx, level, targets, nT, tmask, tbit, excl, tag, k, j, s)));
     TRY(profile_end(ctx, e1, s));
     if (s & 1) {
         launch_copy_targets(targets, nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], ctx->stream);
@@ -299,14 +303,16 @@ vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint
     return VI_OK;
 }
 
-vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
+// The vote of the occluded voxels [off, off + n) of the level's list; their
+// changes go to partials[off .. off + n).
+vi_status vote_range(vi_ctx *ctx, int level, int off, int n)
 {
     Level &l = ctx->lv[level];
     TRY(ensure_partials(ctx, std::max(l.nH, 1)));
     VoteArgs a;
     a.L = l.view();
-    a.list = l.holes;
-    a.n = l.nH;
+    a.list = l.holes + off;
+    a.n = n;
     a.phi = l.phi[0];
     a.d2 = l.d2[0];
     // every patch covering a voxel of H is centred in H~ (the 5x5x5 dilation
@@ -315,20 +321,34 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
     a.abit = CODE_TARGET;
     a.weighted = ctx->cfg.weighted;
     a.hp = nullptr;
-    a.partials = ctx->partials;
+    a.partials = ctx->partials + off;
     launch_vote(a, ctx->c5, ctx->stream);
     CK_LAUNCH();
-    if (change_dev) {
-        const int nc = std::max(sum_chunks(l.nH), 1);
-        if (nc > ctx->chunks_cap) {
-            dfree(ctx, ctx->chunks);
-            ctx->chunks_cap = 0;
-            TRY(dalloc(ctx, &ctx->chunks, sizeof(double) * (size_t)nc));
-            ctx->chunks_cap = nc;
-        }
-        launch_sum_partials(ctx->partials, l.nH, ctx->chunks, change_dev, ctx->stream);
-        CK_LAUNCH();
+    return VI_OK;
+}
+
+// e's numerator of Sec. 3.7 (the per-voxel changes of the whole list summed
+// in the fixed two-stage order) into change_dev.
+vi_status sum_changes(vi_ctx *ctx, int level, double *change_dev)
+{
+    const int nH = ctx->lv[level].nH;
+    const int nc = std::max(sum_chunks(nH), 1);
+    if (nc > ctx->chunks_cap) {
+        dfree(ctx, ctx->chunks);
+        ctx->chunks_cap = 0;
+        TRY(dalloc(ctx, &ctx->chunks, sizeof(double) * (size_t)nc));
+        ctx->chunks_cap = nc;
     }
+    launch_sum_partials(ctx->partials, nH, ctx->chunks, change_dev, ctx->stream);
+    CK_LAUNCH();
+    return VI_OK;
+}
+
+vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
+{
+    TRY(vote_range(ctx, level, 0, ctx->lv[level].nH));
+    if (change_dev)
+        TRY(sum_changes(ctx, level, change_dev));
     return VI_OK;
 }
 
@@ -1140,6 +1160,326 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
     out->levels = ctx->L;
     out->launches = g_launch_count.load();
     return VI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Time slabs. One clip's inpainting split by frames over n contexts, each
+// holding the whole clip: context r owns the targets and occluded voxels of
+// frames [t0_r, t1_r) at every level but the coarsest (which, with the onion
+// peel, every context computes alike). Each context searches and votes only
+// what it owns; the reads that cross a slab boundary are served by copies:
+//  - after every Jacobi sweep, the shifts and change flags of the frame on
+//    each side (propagation in t reads the neighbour at t +- 1);
+//  - after a search, the shifts and distances of the two frames on each side
+//    (the vote reads the patches q in N_p, up to two frames away);
+//  - after every vote or provisional fill, every slab's channels to every
+//    other context (the random search and the patches read anywhere);
+//  - the per-voxel changes of every slab into context 0, which sums e over
+//    the whole list in the single-context order.
+// So every decision, shift, distance and voxel is the same as vi_run's. All
+// contexts share one stream on the current device, which orders the copies;
+// a multi-device form would use peer copies and events instead.
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_slab_err;
+
+struct Slab {
+    vi_ctx *ctx = nullptr;
+    int t0 = 0, t1 = 0;                   // frames owned
+    std::vector<int> tOff, tN, hOff, hN;  // per level: ranges of the target and occluded-voxel lists
+};
+
+int slab_of(const std::vector<Slab> &S, int t)
+{
+    for (size_t r = 0; r + 1 < S.size(); ++r)
+        if (t < S[r].t1)
+            return (int)r;
+    return (int)S.size() - 1;
+}
+
+// Frames [ta, tb) of a per-voxel array of one context into another's.
+template <typename E>
+vi_status copy_frames(vi_ctx *ctx, E *dst, const E *src, int HW, int ta, int tb, unsigned long long &bytes)
+{
+    if (tb <= ta || dst == src || !dst || !src)
+        return VI_OK;
+    const size_t n = (size_t)(tb - ta) * HW * sizeof(E);
+    CK(cudaMemcpyAsync(dst + (size_t)ta * HW, src + (size_t)ta * HW, n, cudaMemcpyDeviceToDevice, ctx->stream));
+    bytes += n;
+    return VI_OK;
+}
+
+// Every slab receives the frames within w of its range from their owners:
+// shift buffer b, change-flag buffer b and distance buffer b as selected.
+vi_status exchange_halo(std::vector<Slab> &S, int level, int w, int b, bool phi, bool chg, bool d2,
+                        unsigned long long &bytes)
+{
+    const int T = S[0].ctx->lv[level].T, HW = S[0].ctx->lv[level].W * S[0].ctx->lv[level].H;
+    for (Slab &dst : S) {
+        for (int t = std::max(dst.t0 - w, 0); t < std::min(dst.t1 + w, T); ++t) {
+            if (t >= dst.t0 && t < dst.t1)
+                continue;
+            vi_ctx *src = S[slab_of(S, t)].ctx;
+            Level &ld = dst.ctx->lv[level], &ls = src->lv[level];
+            if (phi)
+                TRY(copy_frames(dst.ctx, ld.phi[b], ls.phi[b], HW, t, t + 1, bytes));
+            if (chg)
+                TRY(copy_frames(dst.ctx, ld.chg[b], ls.chg[b], HW, t, t + 1, bytes));
+            if (d2)
+                TRY(copy_frames(dst.ctx, ld.d2[b], ls.d2[b], HW, t, t + 1, bytes));
+        }
+    }
+    return VI_OK;
+}
+
+// Every context receives the channels of every other slab's frames.
+vi_status allgather_channels(std::vector<Slab> &S, int level, unsigned long long &bytes)
+{
+    const int HW = S[0].ctx->lv[level].W * S[0].ctx->lv[level].H;
+    for (Slab &dst : S)
+        for (Slab &src : S) {
+            if (&dst == &src)
+                continue;
+            Level &ld = dst.ctx->lv[level], &ls = src.ctx->lv[level];
+            TRY(copy_frames(dst.ctx, ld.x4, ls.x4, HW, src.t0, src.t1, bytes));
+            TRY(copy_frames(dst.ctx, ld.x1, ls.x1, HW, src.t0, src.t1, bytes));
+        }
+    return VI_OK;
+}
+
+// The search of one iteration (call) at a sharded level: rescore, n_pm
+// sweeps with the halo exchanged after each, copy-back, halo for the vote.
+vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long &bytes)
+{
+    const uint32_t tag = make_tag(PURPOSE_SEARCH, level, call);
+    for (Slab &r : S) {
+        vi_ctx *ctx = r.ctx;
+        Level &l = ctx->lv[level];
+        launch_rescore(l.view(), l.targets + r.tOff[level], r.tN[level], l.phi[0], l.d2[0], nullptr, ctx->c5,
+                       ctx->evals_dev, ctx->stream, rescore_lanes(ctx->cfg.lanes_per_target));
+        CK_LAUNCH();
+    }
+    vi_ctx *c0 = S[0].ctx;
+    int s = 0;
+    for (int k = 1; k <= c0->cfg.n_pm; ++k)
+        for (int j = 0; j < c0->cfg.sub_sweeps; ++j, ++s) {
+            for (Slab &r : S) {
+                Level &l = r.ctx->lv[level];
+                TRY(step_launch(r.ctx, sweep_args(r.ctx, level, l.targets + r.tOff[level], r.tN[level], l.code,
+                                                  CODE_TARGET, nullptr, tag, k, j, s)));
+            }
+            TRY(exchange_halo(S, level, 1, (s + 1) & 1, true, true, false, bytes));
+        }
+    if (s & 1)
+        for (Slab &r : S) {
+            vi_ctx *ctx = r.ctx;
+            Level &l = ctx->lv[level];
+            launch_copy_targets(l.targets + r.tOff[level], r.tN[level], l.phi[1], l.d2[1], l.phi[0], l.d2[0],
+                                ctx->stream);
+            CK_LAUNCH();
+        }
+    return exchange_halo(S, level, 2, 0, true, false, true, bytes);
+}
+
+// Votes of every slab, then e over the whole list on context 0 (returned in
+// *e when e is not null), then the channels to every context.
+vi_status slab_vote(std::vector<Slab> &S, int level, float *e, unsigned long long &bytes)
+{
+    for (Slab &r : S)
+        TRY(vote_range(r.ctx, level, r.hOff[level], r.hN[level]));
+    vi_ctx *ctx = S[0].ctx;
+    if (e) {
+        for (size_t i = 1; i < S.size(); ++i) {
+            const size_t n = (size_t)S[i].hN[level] * sizeof(float);
+            if (n) {
+                CK(cudaMemcpyAsync(ctx->partials + S[i].hOff[level], S[i].ctx->partials + S[i].hOff[level], n,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+                bytes += n;
+            }
+        }
+        TRY(sum_changes(ctx, level, ctx->scal));
+    }
+    TRY(allgather_channels(S, level, bytes));
+    if (e) {
+        CK(cudaMemcpyAsync(ctx->host_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int nH = ctx->lv[level].nH;
+        *e = nH ? (float)(ctx->host_scal[0] / (3.0 * nH)) : 0.0f;
+    }
+    return VI_OK;
+}
+
+// Level transition (vi_next_level) into sharded level `level` from level + 1.
+vi_status slab_next_level(std::vector<Slab> &S, int level, unsigned long long &bytes)
+{
+    for (Slab &r : S) {
+        vi_ctx *ctx = r.ctx;
+        Level &c = ctx->lv[level + 1], &f = ctx->lv[level];
+        launch_upsample_nnf(c.view(), c.phi[0], f.view(), false, f.targets + r.tOff[level], r.tN[level], f.sources,
+                            f.nS, f.phi[0], (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull),
+                            (uint32_t)(ctx->cfg.seed >> 32), make_tag(PURPOSE_UPSAMPLE, level, 0), ctx->cfg.clip,
+                            ctx->stream);
+        CK_LAUNCH();
+        launch_provisional_fill(c.view(), f.view(), f.holes + r.hOff[level], r.hN[level], ctx->c5, false,
+                                ctx->stream);
+        CK_LAUNCH();
+    }
+    TRY(allgather_channels(S, level, bytes));
+    for (Slab &r : S) {
+        vi_ctx *ctx = r.ctx;
+        Level &f = ctx->lv[level];
+        launch_rescore(f.view(), f.targets + r.tOff[level], r.tN[level], f.phi[0], f.d2[0], nullptr, ctx->c5,
+                       ctx->evals_dev, ctx->stream, rescore_lanes(ctx->cfg.lanes_per_target));
+        CK_LAUNCH();
+    }
+    TRY(exchange_halo(S, level, 2, 0, true, false, true, bytes));
+    return slab_vote(S, level, nullptr, bytes);
+}
+
+// List ranges of every slab at every level (the lists are raster ordered, so
+// a slab's entries are contiguous).
+vi_status slab_ranges(std::vector<Slab> &S)
+{
+    vi_ctx *ctx = S[0].ctx;
+    for (Slab &r : S) {
+        r.tOff.assign(ctx->L, 0);
+        r.tN.assign(ctx->L, 0);
+        r.hOff.assign(ctx->L, 0);
+        r.hN.assign(ctx->L, 0);
+    }
+    for (int l = 0; l < ctx->L; ++l) {
+        Level &lv = ctx->lv[l];
+        const int HW = lv.W * lv.H;
+        std::vector<int> tl((size_t)lv.nT), hl((size_t)lv.nH);
+        if (lv.nT)
+            CK(cudaMemcpyAsync(tl.data(), lv.targets, sizeof(int) * tl.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        if (lv.nH)
+            CK(cudaMemcpyAsync(hl.data(), lv.holes, sizeof(int) * hl.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (Slab &r : S) {
+            const auto t_a = std::lower_bound(tl.begin(), tl.end(), r.t0 * HW);
+            const auto t_b = std::lower_bound(tl.begin(), tl.end(), r.t1 * HW);
+            const auto h_a = std::lower_bound(hl.begin(), hl.end(), r.t0 * HW);
+            const auto h_b = std::lower_bound(hl.begin(), hl.end(), r.t1 * HW);
+            r.tOff[l] = (int)(t_a - tl.begin());
+            r.tN[l] = (int)(t_b - t_a);
+            r.hOff[l] = (int)(h_a - hl.begin());
+            r.hN[l] = (int)(h_b - h_a);
+        }
+    }
+    return VI_OK;
+}
+
+vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                    int ptr_is_device, float *rgb_out, vi_stats *stats_out, unsigned long long &bytes)
+{
+    const int n = (int)S.size();
+    for (Slab &r : S) {
+        TRY(vi_upload(r.ctx, rgb, mask, W, H, T, ptr_is_device));
+        // pyramid, initialisation and onion peel, then the coarsest level's
+        // iterations: the same on every context
+        TRY(vi_prepare(r.ctx));
+        TRY(vi_iterate(r.ctx, r.ctx->L - 1, -1, 0, nullptr, nullptr));
+    }
+    vi_ctx *ctx = S[0].ctx;
+    const int L = ctx->L;
+    std::vector<unsigned long long> before((size_t)n, 0);
+    for (int i = 1; i < n; ++i) {
+        vi_stats st;
+        TRY(vi_get_stats(S[i].ctx, &st));
+        before[(size_t)i] = st.evals;
+    }
+    TRY(slab_ranges(S));
+    for (int l = L - 2; l >= 0; --l) {
+        TRY(slab_next_level(S, l, bytes));
+        int k = 0;
+        float e = INFINITY;
+        while (e > ctx->cfg.stop && k < ctx->cfg.max_outer) {
+            TRY(slab_ann(S, l, k, bytes));
+            TRY(slab_vote(S, l, &e, bytes));
+            ++k;
+        }
+        if (l < 16)
+            ctx->outer[l] += k;
+    }
+    if (L == 1) {
+        TRY(vi_final(ctx));
+    } else {
+        Level &l0 = ctx->lv[0];
+        const int HW = l0.W * l0.H;
+        for (Slab &r : S) {
+            Level &l = r.ctx->lv[0];
+            launch_final(l.view(), l.holes + r.hOff[0], r.hN[0], l.phi[0], l.d2[0], r.ctx->c5, r.ctx->stream);
+            CK_LAUNCH();
+        }
+        for (int i = 1; i < n; ++i)
+            TRY(copy_frames(ctx, l0.x4, S[i].ctx->lv[0].x4, HW, S[i].t0, S[i].t1, bytes));
+    }
+    TRY(vi_fetch_result(ctx, rgb_out, ptr_is_device));
+    if (stats_out) {
+        TRY(vi_get_stats(ctx, stats_out));
+        for (int i = 1; i < n; ++i) {
+            vi_stats st;
+            TRY(vi_get_stats(S[i].ctx, &st));
+            stats_out->evals += st.evals - before[(size_t)i];
+        }
+    }
+    return VI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vi_slabs_last_error(void) { return g_slab_err.c_str(); }
+
+vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *mask, int W, int H, int T,
+                       int ptr_is_device, int n_slabs, float *rgb_out, vi_stats *stats_out,
+                       unsigned long long *exchanged_bytes, void *cuda_stream)
+{
+    g_slab_err.clear();
+    vi_config c;
+    if (cfg)
+        c = *cfg;
+    else
+        vi_config_default(&c);
+    if (!rgb || !mask || !rgb_out || n_slabs < 1 || n_slabs > 16 || T < n_slabs || c.storage != 0 ||
+        c.time_subsample != 0) {
+        g_slab_err = "vi_run_slabs: bad arguments (1 <= n_slabs <= min(16, T); FP32 storage; no temporal "
+                     "subsampling)";
+        return VI_ERR_ARG;
+    }
+    std::vector<Slab> S;
+    vi_status st = VI_OK;
+    unsigned long long bytes = 0;
+    try {
+        S.resize((size_t)n_slabs);
+        for (int r = 0; r < n_slabs && st == VI_OK; ++r) {
+            S[(size_t)r].t0 = (int)((long long)r * T / n_slabs);
+            S[(size_t)r].t1 = (int)((long long)(r + 1) * T / n_slabs);
+            // all contexts share one stream: the caller's, else context 0's own
+            st = vi_ctx_create(&c, r ? (void *)S[0].ctx->stream : cuda_stream, &S[(size_t)r].ctx);
+        }
+        if (st == VI_OK)
+            st = run_slabs(S, rgb, mask, W, H, T, ptr_is_device, rgb_out, stats_out, bytes);
+    } catch (...) {
+        st = VI_ERR_OOM;
+    }
+    if (st != VI_OK) {
+        for (const Slab &r : S)
+            if (r.ctx && !r.ctx->err.empty()) {
+                g_slab_err = r.ctx->err;
+                break;
+            }
+    }
+    if (exchanged_bytes)
+        *exchanged_bytes = bytes;
+    for (size_t r = S.size(); r-- > 0;)
+        vi_ctx_destroy(S[r].ctx);   // context 0 (the stream's owner) last
+    return st;
 }
 
 }  // extern "C"

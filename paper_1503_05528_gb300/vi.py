@@ -31,7 +31,7 @@ EXPORTS = [
     "vi_realign_last_error", "vi_affine_levels", "vi_affine_estimate", "vi_affine_to_reference",
     "vi_affine_align", "vi_affine_unwarp",
     "vi_server_create", "vi_server_submit", "vi_server_poll", "vi_server_wait", "vi_server_release",
-    "vi_server_info", "vi_server_destroy",
+    "vi_server_info", "vi_server_destroy", "vi_run_slabs", "vi_slabs_last_error",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -137,6 +137,9 @@ def _declare(L):
     L.vi_affine_to_reference.argtypes = [vp, i, vp]
     L.vi_affine_align.argtypes = [vp, vp, i, i, i, vp, vp, vp, i, vp]
     L.vi_affine_unwarp.argtypes = [vp, vp, vp, i, i, i, vp, vp, i, vp]
+    L.vi_run_slabs.argtypes = [P(ViConfig), vp, vp, i, i, i, i, i, vp, P(ViStats), P(C.c_ulonglong), vp]
+    L.vi_slabs_last_error.argtypes = []
+    L.vi_slabs_last_error.restype = C.c_char_p
     ull = C.c_ulonglong
     L.vi_batch_create.argtypes = [P(ViConfig), vp, P(vp)]
     L.vi_batch_destroy.argtypes = [vp]
@@ -602,6 +605,31 @@ def auto_levels(mask):
     mask = np.ascontiguousarray(mask, np.uint8)
     T, H, W = mask.shape
     return load().vi_auto_levels(mask.ctypes.data, W, H, T)
+
+
+def run_slabs(rgb, mask, n_slabs, out=None, stream=None, **cfg):
+    """The whole inpainting with the finer levels split by frames over
+    n_slabs contexts (vi_run_slabs). Returns (result, stats dict, bytes
+    exchanged between the contexts)."""
+    lib = load()
+    if isinstance(rgb, np.ndarray):
+        rgb = np.ascontiguousarray(rgb, np.float32)
+    if isinstance(mask, np.ndarray):
+        mask = np.ascontiguousarray(mask, np.uint8)
+    T, H, W = mask.shape[:3]
+    if out is None:
+        out = np.empty((T, H, W, 3), np.float32)
+    pr, dev = _ptr(rgb)
+    pm, _ = _ptr(mask)
+    po, _ = _ptr(out)
+    cfgs = default_config(**cfg)
+    st = ViStats()
+    nbytes = C.c_ulonglong(0)
+    r = lib.vi_run_slabs(C.byref(cfgs), pr, pm, W, H, T, dev, int(n_slabs), po, C.byref(st), C.byref(nbytes),
+                         C.c_void_p(stream) if stream else None)
+    if r != VI_OK:
+        raise ViError(r, "vi_run_slabs: " + (lib.vi_slabs_last_error() or b"").decode(errors="replace"))
+    return out, _stats_dict(st), nbytes.value
 
 
 def inpaint(rgb, mask, realign=False, **cfg):

@@ -92,3 +92,14 @@ def test_server_arguments_and_no_gpu(lib):
         assert lib.vi_server_create(1 << 30, 2, ctypes.byref(h)) == 7   # VI_ERR_NO_DEVICE
         with pytest.raises(vi.ViError):
             vi.Server(1 << 30, 2)
+
+
+def test_slabs_argument_errors_need_no_gpu(lib):
+    cfg = vi.default_config()
+    rgb = np.zeros((4, 8, 8, 3), np.float32)
+    mask = np.zeros((4, 8, 8), np.uint8)
+    out = np.empty_like(rgb)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    for n in (0, 5, 17):   # n_slabs outside 1 .. min(16, T)
+        assert lib.vi_run_slabs(ctypes.byref(cfg), p(rgb), p(mask), 8, 8, 4, 0, n, p(out), None, None, None) == 1
+    assert b"n_slabs" in lib.vi_slabs_last_error()
