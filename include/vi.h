@@ -362,8 +362,9 @@ void vi_server_destroy(vi_server *s);
  * context. What a slab reads across its boundary is copied between the
  * contexts: after every Jacobi sweep the shifts and change flags of the frame
  * on each side; after a search the shifts and distances of the two frames on
- * each side; after every vote the channels of every slab to every context;
- * and the per-voxel changes into context 0, which sums e over the whole list
+ * each side; after every vote or provisional fill the channels of every
+ * slab's occluded voxels to every context; and the per-voxel changes into
+ * context 0, which sums e over the whole list
  * in vi_run's order. The output, the iteration counts and the evaluation
  * count are identical to vi_run's. All contexts run on the current device on
  * one stream (cuda_stream, or one context 0 creates; NULL), which orders the

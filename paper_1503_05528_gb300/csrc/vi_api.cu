@@ -1174,8 +1174,9 @@ vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out)
 //    each side (propagation in t reads the neighbour at t +- 1);
 //  - after a search, the shifts and distances of the two frames on each side
 //    (the vote reads the patches q in N_p, up to two frames away);
-//  - after every vote or provisional fill, every slab's channels to every
-//    other context (the random search and the patches read anywhere);
+//  - after every vote or provisional fill, the channels of every slab's
+//    occluded voxels to every other context (the random search and the
+//    patches read anywhere);
 //  - the per-voxel changes of every slab into context 0, which sums e over
 //    the whole list in the single-context order.
 // So every decision, shift, distance and voxel is the same as vi_run's. All
@@ -1190,6 +1191,8 @@ struct Slab {
     vi_ctx *ctx = nullptr;
     int t0 = 0, t1 = 0;                   // frames owned
     std::vector<int> tOff, tN, hOff, hN;  // per level: ranges of the target and occluded-voxel lists
+    float4 *buf4 = nullptr;               // channels of occluded voxels, indexed like the level's list
+    float *buf1 = nullptr;
 };
 
 int slab_of(const std::vector<Slab> &S, int t)
@@ -1235,18 +1238,36 @@ vi_status exchange_halo(std::vector<Slab> &S, int level, int w, int b, bool phi,
     return VI_OK;
 }
 
-// Every context receives the channels of every other slab's frames.
-vi_status allgather_channels(std::vector<Slab> &S, int level, unsigned long long &bytes)
+// The channels of every slab's occluded voxels (the only voxels a vote or a
+// provisional fill writes) into every other context (all_dst), or into
+// context 0 only: packed by the owner, copied, unpacked by the receiver.
+vi_status gather_holes(std::vector<Slab> &S, int level, bool all_dst, unsigned long long &bytes)
 {
-    const int HW = S[0].ctx->lv[level].W * S[0].ctx->lv[level].H;
-    for (Slab &dst : S)
-        for (Slab &src : S) {
-            if (&dst == &src)
+    for (Slab &src : S) {
+        vi_ctx *ctx = src.ctx;
+        Level &l = ctx->lv[level];
+        const int off = src.hOff[level], n = src.hN[level];
+        if (!n)
+            continue;
+        launch_pack_voxels(l.view(), l.holes + off, n, src.buf4 + off, src.buf1 + off, false, ctx->stream);
+        CK_LAUNCH();
+        for (Slab &dst : S) {
+            if (&dst == &src || (!all_dst && &dst != &S[0]))
                 continue;
-            Level &ld = dst.ctx->lv[level], &ls = src.ctx->lv[level];
-            TRY(copy_frames(dst.ctx, ld.x4, ls.x4, HW, src.t0, src.t1, bytes));
-            TRY(copy_frames(dst.ctx, ld.x1, ls.x1, HW, src.t0, src.t1, bytes));
+            vi_ctx *dctx = dst.ctx;
+            Level &ld = dctx->lv[level];
+            CK(cudaMemcpyAsync(dst.buf4 + off, src.buf4 + off, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice,
+                               dctx->stream));
+            bytes += sizeof(float4) * (size_t)n;
+            if (l.x1) {
+                CK(cudaMemcpyAsync(dst.buf1 + off, src.buf1 + off, sizeof(float) * (size_t)n,
+                                   cudaMemcpyDeviceToDevice, dctx->stream));
+                bytes += sizeof(float) * (size_t)n;
+            }
+            launch_pack_voxels(ld.view(), ld.holes + off, n, dst.buf4 + off, dst.buf1 + off, true, dctx->stream);
+            CK_LAUNCH();
         }
+    }
     return VI_OK;
 }
 
@@ -1302,7 +1323,7 @@ vi_status slab_vote(std::vector<Slab> &S, int level, float *e, unsigned long lon
         }
         TRY(sum_changes(ctx, level, ctx->scal));
     }
-    TRY(allgather_channels(S, level, bytes));
+    TRY(gather_holes(S, level, true, bytes));
     if (e) {
         CK(cudaMemcpyAsync(ctx->host_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1327,7 +1348,7 @@ vi_status slab_next_level(std::vector<Slab> &S, int level, unsigned long long &b
                                 ctx->stream);
         CK_LAUNCH();
     }
-    TRY(allgather_channels(S, level, bytes));
+    TRY(gather_holes(S, level, true, bytes));
     for (Slab &r : S) {
         vi_ctx *ctx = r.ctx;
         Level &f = ctx->lv[level];
@@ -1393,6 +1414,14 @@ vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask,
         before[(size_t)i] = st.evals;
     }
     TRY(slab_ranges(S));
+    int max_h = 1;
+    for (int l = 0; l < L; ++l)
+        max_h = std::max(max_h, ctx->lv[l].nH);
+    for (Slab &r : S) {
+        vi_ctx *rc = r.ctx;
+        TRY(dalloc(rc, &r.buf4, sizeof(float4) * (size_t)max_h));
+        TRY(dalloc(rc, &r.buf1, sizeof(float) * (size_t)max_h));
+    }
     for (int l = L - 2; l >= 0; --l) {
         TRY(slab_next_level(S, l, bytes));
         int k = 0;
@@ -1408,15 +1437,12 @@ vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask,
     if (L == 1) {
         TRY(vi_final(ctx));
     } else {
-        Level &l0 = ctx->lv[0];
-        const int HW = l0.W * l0.H;
         for (Slab &r : S) {
             Level &l = r.ctx->lv[0];
             launch_final(l.view(), l.holes + r.hOff[0], r.hN[0], l.phi[0], l.d2[0], r.ctx->c5, r.ctx->stream);
             CK_LAUNCH();
         }
-        for (int i = 1; i < n; ++i)
-            TRY(copy_frames(ctx, l0.x4, S[i].ctx->lv[0].x4, HW, S[i].t0, S[i].t1, bytes));
+        TRY(gather_holes(S, 0, false, bytes));
     }
     TRY(vi_fetch_result(ctx, rgb_out, ptr_is_device));
     if (stats_out) {
@@ -1477,8 +1503,13 @@ vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *ma
     }
     if (exchanged_bytes)
         *exchanged_bytes = bytes;
-    for (size_t r = S.size(); r-- > 0;)
+    for (size_t r = S.size(); r-- > 0;) {
+        if (S[r].ctx) {
+            dfree(S[r].ctx, S[r].buf4);
+            dfree(S[r].ctx, S[r].buf1);
+        }
         vi_ctx_destroy(S[r].ctx);   // context 0 (the stream's owner) last
+    }
     return st;
 }
 

@@ -153,6 +153,8 @@ void launch_onion_targets(LevelView L, const uint8_t *hp, const uint8_t *layer, 
 void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st);
 // Packing helpers between the library layout and the ABI layout.
 void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st);
+void launch_pack_voxels(LevelView L, const int *list, int n, float4 *buf4, float *buf1, bool unpack,
+                        cudaStream_t st);
 void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st);
 void launch_set_channels(LevelView L, const float *in, int C, cudaStream_t st);
 // FP16 copies of channels c0..c3 of every voxel of a level (no-op for FP32

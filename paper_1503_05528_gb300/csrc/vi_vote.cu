@@ -578,6 +578,34 @@ void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st)
     k_pack_rgb<<<blocks_for(L.V, 256), 256, 0, st>>>(L, rgb);
 }
 
+// The channels of list[0 .. n) packed into buf4[0 .. n) (c0..c3) and
+// buf1[0 .. n) (c4), or (unpack) written back from there.
+__global__ void k_pack_voxels(LevelView L, const int *__restrict__ list, int n, float4 *buf4, float *buf1,
+                              bool unpack)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int v = list[i];
+        if (unpack) {
+            L.x4[v] = buf4[i];
+            if (L.x1)
+                L.x1[v] = buf1[i];
+        } else {
+            buf4[i] = L.x4[v];
+            if (L.x1)
+                buf1[i] = L.x1[v];
+        }
+    }
+}
+
+void launch_pack_voxels(LevelView L, const int *list, int n, float4 *buf4, float *buf1, bool unpack,
+                        cudaStream_t st)
+{
+    if (n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    k_pack_voxels<<<blocks_for(n, 256), 256, 0, st>>>(L, list, n, buf4, buf1, unpack);
+}
+
 __global__ void k_get_channels(LevelView L, float *__restrict__ out, int C)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
