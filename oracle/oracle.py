@@ -112,6 +112,11 @@ def _declare(L):
     L.vio_ann2.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p, i, i, i, d,
                            u32, u32, u32, u32, i, i]
     L.vio_ann2.restype = C.c_longlong
+    L.vio_rescore.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p]
+    L.vio_rescore.restype = C.c_longlong
+    L.vio_ann_iteration.argtypes = [_f32p, i, i, i, i, _u8p, _OptU8, _u8p, _OptU8, _i32p, _f32p, i, i, d,
+                                    u32, u32, u32, u32, i, i]
+    L.vio_ann_iteration.restype = C.c_longlong
     L.vio_bruteforce_nn.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p]
     L.vio_vote.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _u8p, _i32p, _f32p, i, i, _OptU8]
     L.vio_vote.restype = d
@@ -265,6 +270,42 @@ def ann(x, target, dtilde, phi, d2, n_pm=10, schedule="JAC", rmax=None, rho=0.5,
                           phi.reshape(-1), d2.reshape(-1), int(n_pm), sched, int(rmax),
                           float(rho), key[0], key[1], int(tag_base), int(clip), int(rs_mode),
                           int(sub_sweeps))
+
+
+def rescore(x, target, dtilde, phi, d2, excl=None):
+    """The first step of ann (JAC): every target's distance to its current
+    correspondent, in place in d2. Returns the evaluations."""
+    x = _c(x, np.float32)
+    T, H, W, Cn = x.shape
+    assert phi.dtype == np.int32 and phi.flags.c_contiguous
+    assert d2.dtype == np.float32 and d2.flags.c_contiguous
+    return lib().vio_rescore(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
+                             _c(dtilde, np.uint8).reshape(-1),
+                             None if excl is None else _c(excl, np.uint8).reshape(-1),
+                             phi.reshape(-1), d2.reshape(-1))
+
+
+def ann_iteration(x, target, dtilde, phi, d2, k, rmax=None, rho=0.5, key=(0, 0), tag_base=0, clip=0,
+                  excl=None, rs_mode=0, sub_sweeps=1, own=None):
+    """Iteration k of ann with the Jacobi schedule, in place, for the targets
+    in own (None: all of target; target still says which neighbours hold a
+    shift). rescore then ann_iteration for k = 1 .. n_pm is
+    ann(schedule="JAC"). Returns the evaluations."""
+    x = _c(x, np.float32)
+    T, H, W, Cn = x.shape
+    assert phi.dtype == np.int32 and phi.flags.c_contiguous
+    assert d2.dtype == np.float32 and d2.flags.c_contiguous
+    if rmax is None:
+        rmax = max(W, H, T)
+    n = lib().vio_ann_iteration(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
+                                None if own is None else _c(own, np.uint8).reshape(-1),
+                                _c(dtilde, np.uint8).reshape(-1),
+                                None if excl is None else _c(excl, np.uint8).reshape(-1),
+                                phi.reshape(-1), d2.reshape(-1), int(k), int(rmax), float(rho), key[0], key[1],
+                                int(tag_base), int(clip), int(rs_mode), int(sub_sweeps))
+    if n < 0:
+        raise MemoryError("vio_ann_iteration")
+    return n
 
 
 def bruteforce_nn(x, target, dtilde, excl=None):

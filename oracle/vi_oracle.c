@@ -637,6 +637,59 @@ long long vio_ann2(const float *x, int W, int H, int T, int C,
     return a.evals;
 }
 
+/* The two parts of vio_ann2's Jacobi schedule on their own, so that ranks
+ * holding different targets can exchange shifts between iterations: the
+ * distance of every target to its current correspondent (+inf where that is
+ * not in D~), and one iteration k (sub_sweeps Jacobi propagation sweeps, then
+ * the random search) for the targets marked in own (NULL: every target),
+ * where target still says which neighbours hold a shift. vio_rescore
+ * followed by vio_ann_iteration for k = 1 .. n_pm is vio_ann2 with schedule
+ * 1, step for step. Each returns its evaluations. */
+long long vio_rescore(const float *x, int W, int H, int T, int C, const uint8_t *target,
+                      const uint8_t *dtilde, const uint8_t *excl, const int32_t *phi, float *d2)
+{
+    size_t V = (size_t)W * H * T;
+    long long evals = 0;
+    for (size_t p = 0; p < V; ++p) {
+        if (!target[p])
+            continue;
+        int px, py, pt;
+        coords(p, W, H, &px, &py, &pt);
+        int sx = px + phi[3 * p], sy = py + phi[3 * p + 1], st = pt + phi[3 * p + 2];
+        if (inside(sx, sy, st, W, H, T) && dtilde[vidx(sx, sy, st, W, H)]) {
+            d2[p] = vio_dist_f32(x, W, H, T, C, px, py, pt, sx, sy, st, excl);
+            evals++;
+        } else {
+            d2[p] = INFINITY;
+        }
+    }
+    return evals;
+}
+
+long long vio_ann_iteration(const float *x, int W, int H, int T, int C, const uint8_t *target,
+                            const uint8_t *own, const uint8_t *dtilde, const uint8_t *excl, int32_t *phi,
+                            float *d2, int k, int rmax, double rho, uint32_t key0, uint32_t key1,
+                            uint32_t tag_base, uint32_t clip, int rs_mode, int sub_sweeps)
+{
+    size_t V = (size_t)W * H * T;
+    ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0};
+    const uint8_t *mine = own ? own : target;
+    int32_t *phi_old = (int32_t *)malloc(V * 3 * sizeof(int32_t));
+    if (!phi_old)
+        return -1;
+    for (int j = 0; j < sub_sweeps; ++j) {
+        memcpy(phi_old, phi, V * 3 * sizeof(int32_t));
+        for (size_t p = 0; p < V; ++p)
+            if (mine[p])
+                propagate_one(&a, p, k, phi_old, phi, d2);
+    }
+    for (size_t p = 0; p < V; ++p)
+        if (mine[p])
+            random_search_one(&a, p, k, rmax, rho, rs_mode, key0, key1, tag_base, clip, phi, d2);
+    free(phi_old);
+    return a.evals;
+}
+
 long long vio_ann(const float *x, int W, int H, int T, int C,
                   const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
                   int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,

@@ -265,3 +265,22 @@ def test_multi_radius_and_sub_sweeps_keep_validity_and_monotonicity(schedule):
         assert _valid(phi, ht, dt)
         assert (d2[ht == 1] <= prev[ht == 1]).all()
         prev = d2.copy()
+
+
+@pytest.mark.parametrize("rs_mode,sub_sweeps", [(0, 1), (1, 1), (0, 2)])
+def test_rescore_then_iterations_is_the_jacobi_search(rs_mode, sub_sweeps):
+    # rescore followed by ann_iteration for k = 1 .. n_pm (the split the rank
+    # harness of the time slabs exchanges between) is ann's Jacobi schedule
+    x, hole, ht, dt, phi0 = _setup(seed=9)
+    a, b = phi0.copy(), phi0.copy()
+    da = np.full(hole.shape, np.inf, np.float32)
+    db = da.copy()
+    ea = O.ann(x, ht, dt, a, da, n_pm=5, schedule="JAC", key=(4, 1), tag_base=77, rs_mode=rs_mode,
+               sub_sweeps=sub_sweeps)
+    eb = O.rescore(x, ht, dt, b, db)
+    for k in range(1, 6):
+        eb += O.ann_iteration(x, ht, dt, b, db, k, key=(4, 1), tag_base=77, rs_mode=rs_mode,
+                              sub_sweeps=sub_sweeps)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(da.view(np.uint32), db.view(np.uint32))
+    assert ea == eb
