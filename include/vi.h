@@ -216,7 +216,9 @@ vi_status vi_reconstruct(vi_ctx *ctx, int level, float *e_host);
  * n_outer >= 0 runs exactly that many iterations; n_outer < 0 applies the
  * stopping rule of Sec. 3.7 (stop when e <= cfg.stop or after cfg.max_outer
  * iterations; synchronises once per iteration). n_done_host and e_last_host
- * are nullable. The call index of the k-th iteration is first_call + k. */
+ * are nullable. The call index of the k-th iteration is first_call + k, and
+ * with the rule the cap counts from call 0 (first_call + k < cfg.max_outer),
+ * so a loop resumed at call first_call stops where the whole loop would. */
 vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n_done_host,
                      float *e_last_host);
 
@@ -306,6 +308,39 @@ vi_status vi_profile(vi_ctx *ctx, int enable);
 
 /* The context's counters (synchronises to read event times). */
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
+
+/* ---------------------------------------------------------------------------
+ * Checkpoint and resume (no counterpart in the paper). Between two
+ * iterations of Algorithm 4's inner loop a level carries forward its channels
+ * (u and the texture features of Eq. 7-9), its shift map and its distances;
+ * every random draw depends only on (level, call, voxel). So a context that
+ * uploaded the same clip with the same configuration and built its pyramid
+ * can load a level's saved state and go on: the result is bit-identical to
+ * the uninterrupted run, as long as that run went on past the saved
+ * iteration. Host buffers, owned by the caller. Layout: 16 int32 of header
+ * (magic "VICK", version 1, level, W, H, T, channels, zeros), then the
+ * level's V x 4 channels c0..c3 (float), V x c4 (float, with texture), V x 3
+ * shift components (int32 dx, dy, dt) and V distances (float), raster order.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of a saved state of `level` (0 for a bad level or no pyramid). */
+size_t vi_state_bytes(vi_ctx *ctx, int level);
+
+/* Saves the state of `level` into buf (cap >= vi_state_bytes). Synchronises.
+ * Errors: VI_ERR_ARG. */
+vi_status vi_save_state(vi_ctx *ctx, int level, void *buf, size_t cap);
+
+/* Loads a saved state of `level` (same level, sizes and channels; size must
+ * be exactly vi_state_bytes). With FP16 storage the copies are rebuilt.
+ * Synchronises. Errors: VI_ERR_ARG (other level, clip or configuration; a
+ * shift beyond 16 bits). */
+vi_status vi_load_state(vi_ctx *ctx, int level, const void *buf, size_t size);
+
+/* The rest of Algorithm 4 from call first_call of `level` (the iterations
+ * there with the stopping rule, the finer levels, Eq. 6): with the state of
+ * `level` saved after first_call iterations, vi_load_state + vi_resume gives
+ * vi_run's result. */
+vi_status vi_resume(vi_ctx *ctx, int level, int first_call);
 
 /* ---------------------------------------------------------------------------
  * Serving (no counterpart in the paper, which runs one clip at a time). A

@@ -482,7 +482,10 @@ def _outer_count(prm, idx_from_coarsest):
 def iterate_level(lv, prm, level_index, n_outer=None, start_call=0):
     """The inner loop of Algorithm 4 at one level: ANN search, then
     reconstruction of u and T, until e <= stop or max_outer iterations
-    (or exactly n_outer iterations when given)."""
+    (or exactly n_outer iterations when given). Iteration k uses call index
+    start_call + k, and the cap of Sec. 3.7 counts the level's iterations
+    from call 0, so a loop resumed at start_call stops where the whole loop
+    would."""
     nH = int(lv.hole.sum())
     k = 0
     e = math.inf
@@ -492,7 +495,7 @@ def iterate_level(lv, prm, level_index, n_outer=None, start_call=0):
         if n_outer is not None:
             if k >= n_outer:
                 break
-        elif not (e > prm.stop and k < prm.max_outer):
+        elif not (e > prm.stop and start_call + k < prm.max_outer):
             break
         evals += ann(lv.x, lv.htilde, lv.dtilde, lv.phi, lv.d2, n_pm=prm.n_pm,
                      schedule=prm.schedule, rho=prm.rho, key=prm.key,

@@ -285,6 +285,7 @@ AnnArgs sweep_args(vi_ctx *ctx, int level, const int *targets, int nT, const uin
 vi_status run_ann(vi_ctx *ctx, int level, const int *targets, int nT, const uint8_t *tmask,
                   uint8_t tbit, const uint8_t *excl, uint32_t tag)
 {
+    const Phase ph("search L%d", level);
     Level &l = ctx->lv[level];
     launch_rescore(l.view(), targets, nT, l.phi[0], l.d2[0], excl, ctx->c5, ctx->evals_dev, ctx->stream,
                    rescore_lanes(ctx->cfg.lanes_per_target));
@@ -346,6 +347,7 @@ vi_status sum_changes(vi_ctx *ctx, int level, double *change_dev)
 
 vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
 {
+    const Phase ph("vote L%d", level);
     TRY(vote_range(ctx, level, 0, ctx->lv[level].nH));
     if (change_dev)
         TRY(sum_changes(ctx, level, change_dev));
@@ -599,6 +601,7 @@ vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, i
 
 vi_status vi_build_pyramid(vi_ctx *ctx)
 {
+    const Phase ph("pyramid");
     if (!ctx)
         return VI_ERR_ARG;
     if (!ctx->uploaded)
@@ -702,6 +705,7 @@ vi_status vi_init_nnf(vi_ctx *ctx, int level)
 
 vi_status vi_onion_peel(vi_ctx *ctx)
 {
+    const Phase ph("onion peel");
     if (!ctx)
         return VI_ERR_ARG;
     if (!ctx->built)
@@ -819,10 +823,14 @@ vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n
         return VI_ERR_ARG;
     if (!level_ok(ctx, level) || first_call < 0)
         return fail(ctx, VI_ERR_ARG, "vi_iterate: bad level or no pyramid");
+    const Phase ph("level %d", level);
     int k = 0;
     float e = INFINITY;
     const bool rule = n_outer < 0;
-    while (rule ? (e > ctx->cfg.stop && k < ctx->cfg.max_outer) : (k < n_outer)) {
+    // with the rule, the cap counts the iterations from call 0, so a run
+    // resumed at call first_call stops where the uninterrupted run would
+    while (rule ? (e > ctx->cfg.stop && first_call + k < ctx->cfg.max_outer) : (k < n_outer)) {
+        const Phase it("L%d iteration %d", level, first_call + k);
         TRY(vi_ann(ctx, level, first_call + k));
         TRY(vi_reconstruct(ctx, level, (rule || e_last_host) ? &e : nullptr));
         ++k;
@@ -838,6 +846,7 @@ vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n
 
 vi_status vi_next_level(vi_ctx *ctx, int level)
 {
+    const Phase ph("transition L%d to L%d", level, level - 1);
     if (!ctx)
         return VI_ERR_ARG;
     if (!level_ok(ctx, level) || level == 0)
@@ -857,6 +866,7 @@ vi_status vi_next_level(vi_ctx *ctx, int level)
 
 vi_status vi_final(vi_ctx *ctx)
 {
+    const Phase ph("final (Eq. 6)");
     if (!ctx)
         return VI_ERR_ARG;
     if (!level_ok(ctx, 0))
@@ -867,8 +877,155 @@ vi_status vi_final(vi_ctx *ctx)
     return VI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint and resume. Between two iterations of Algorithm 4's inner loop
+// the state a level carries forward is its channels (u and the texture
+// features, known voxels from the pyramid and the occluded ones as last
+// voted), its shift map and its distances; every random draw depends only on
+// (level, call, voxel), so a run resumed from a saved state draws the same.
+// Layout: a header of 16 int32 (magic, version, level, W, H, T, C, then 0),
+// then the level's x4 (V float4), x1 (V float, with texture channels), shift
+// map (V x 3 int32: dx, dy, dt) and distances (V float).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int32_t STATE_MAGIC = 0x4B434956;   // "VICK"
+
+size_t state_bytes(vi_ctx *ctx, int level)
+{
+    const size_t V = (size_t)ctx->lv[level].V;
+    return 16 * sizeof(int32_t) + V * (sizeof(float4) + (ctx->c5 ? sizeof(float) : 0) + 3 * sizeof(int32_t) +
+                                       sizeof(float));
+}
+
+}  // namespace
+
+size_t vi_state_bytes(vi_ctx *ctx, int level)
+{
+    if (!ctx || !level_ok(ctx, level))
+        return 0;
+    return state_bytes(ctx, level);
+}
+
+static vi_status vi_save_state_body(vi_ctx *ctx, int level, void *buf, size_t cap)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || !buf || cap < state_bytes(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_save_state: bad level, no pyramid or buffer too small");
+    Level &l = ctx->lv[level];
+    const size_t V = (size_t)l.V;
+    int32_t *hdr = static_cast<int32_t *>(buf);
+    std::memset(hdr, 0, 16 * sizeof(int32_t));
+    hdr[0] = STATE_MAGIC;
+    hdr[1] = 1;
+    hdr[2] = level;
+    hdr[3] = l.W;
+    hdr[4] = l.H;
+    hdr[5] = l.T;
+    hdr[6] = ctx->c5 ? 5 : 4;
+    char *p = static_cast<char *>(buf) + 16 * sizeof(int32_t);
+    CK(cudaMemcpyAsync(p, l.x4, V * sizeof(float4), cudaMemcpyDeviceToHost, ctx->stream));
+    p += V * sizeof(float4);
+    if (ctx->c5) {
+        CK(cudaMemcpyAsync(p, l.x1, V * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        p += V * sizeof(float);
+    }
+    std::vector<Shift> ph(V);
+    CK(cudaMemcpyAsync(ph.data(), l.phi[0], V * sizeof(Shift), cudaMemcpyDeviceToHost, ctx->stream));
+    char *phi_at = p;
+    p += V * 3 * sizeof(int32_t);
+    CK(cudaMemcpyAsync(p, l.d2[0], V * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int32_t *phi = reinterpret_cast<int32_t *>(phi_at);
+    for (size_t v = 0; v < V; ++v) {
+        phi[3 * v] = ph[v].dx;
+        phi[3 * v + 1] = ph[v].dy;
+        phi[3 * v + 2] = ph[v].dt;
+    }
+    return VI_OK;
+}
+
+vi_status vi_save_state(vi_ctx *ctx, int level, void *buf, size_t cap)
+{
+    try {
+        return vi_save_state_body(ctx, level, buf, cap);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+static vi_status vi_load_state_body(vi_ctx *ctx, int level, const void *buf, size_t size)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || !buf || size < 16 * sizeof(int32_t))
+        return fail(ctx, VI_ERR_ARG, "vi_load_state: bad level, no pyramid or no buffer");
+    Level &l = ctx->lv[level];
+    const size_t V = (size_t)l.V;
+    const int32_t *hdr = static_cast<const int32_t *>(buf);
+    if (hdr[0] != STATE_MAGIC || hdr[1] != 1 || hdr[2] != level || hdr[3] != l.W || hdr[4] != l.H ||
+        hdr[5] != l.T || hdr[6] != (ctx->c5 ? 5 : 4) || size != state_bytes(ctx, level))
+        return fail(ctx, VI_ERR_ARG, "vi_load_state: the state is of another level, clip or configuration");
+    const char *p = static_cast<const char *>(buf) + 16 * sizeof(int32_t);
+    CK(cudaMemcpyAsync(l.x4, p, V * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    p += V * sizeof(float4);
+    if (ctx->c5) {
+        CK(cudaMemcpyAsync(l.x1, p, V * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        p += V * sizeof(float);
+    }
+    const int32_t *phi = reinterpret_cast<const int32_t *>(p);
+    std::vector<Shift> ph(V);
+    for (size_t v = 0; v < V; ++v) {
+        if (phi[3 * v] < -32768 || phi[3 * v] > 32767 || phi[3 * v + 1] < -32768 || phi[3 * v + 1] > 32767 ||
+            phi[3 * v + 2] < -32768 || phi[3 * v + 2] > 32767)
+            return fail(ctx, VI_ERR_ARG, "vi_load_state: shift out of range");
+        ph[v].dx = (short)phi[3 * v];
+        ph[v].dy = (short)phi[3 * v + 1];
+        ph[v].dt = (short)phi[3 * v + 2];
+    }
+    p += V * 3 * sizeof(int32_t);
+    CK(cudaMemcpyAsync(l.phi[0], ph.data(), V * sizeof(Shift), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(l.d2[0], p, V * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->cfg.storage == 1) {
+        // the FP16 copies and their magnitude bounds follow the loaded channels
+        CK(cudaMemsetAsync(l.hmax, 0, 8 * sizeof(unsigned), ctx->stream));
+        launch_shadow_all(l.view(), ctx->stream);
+        CK_LAUNCH();
+    }
+    CK(cudaStreamSynchronize(ctx->stream));   // the host copy of the shifts is released on return
+    return VI_OK;
+}
+
+vi_status vi_load_state(vi_ctx *ctx, int level, const void *buf, size_t size)
+{
+    try {
+        return vi_load_state_body(ctx, level, buf, size);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+vi_status vi_resume(vi_ctx *ctx, int level, int first_call)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!level_ok(ctx, level) || first_call < 0)
+        return fail(ctx, VI_ERR_ARG, "vi_resume: bad level or no pyramid");
+    TRY(vi_iterate(ctx, level, -1, first_call, nullptr, nullptr));
+    if (level > 0)
+        TRY(vi_next_level(ctx, level));
+    for (int l = level - 1; l >= 0; --l) {
+        TRY(vi_iterate(ctx, l, -1, 0, nullptr, nullptr));
+        if (l > 0)
+            TRY(vi_next_level(ctx, l));
+    }
+    return vi_final(ctx);
+}
+
 vi_status vi_run(vi_ctx *ctx)
 {
+    const Phase ph("inpainting");
     if (!ctx)
         return VI_ERR_ARG;
     TRY(vi_prepare(ctx));
@@ -1275,6 +1432,7 @@ vi_status gather_holes(std::vector<Slab> &S, int level, bool all_dst, unsigned l
 // sweeps with the halo exchanged after each, copy-back, halo for the vote.
 vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long &bytes)
 {
+    const Phase ph("slab search L%d call %d", level, call);
     const uint32_t tag = make_tag(PURPOSE_SEARCH, level, call);
     for (Slab &r : S) {
         vi_ctx *ctx = r.ctx;
@@ -1309,6 +1467,7 @@ vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long
 // *e when e is not null), then the channels to every context.
 vi_status slab_vote(std::vector<Slab> &S, int level, float *e, unsigned long long &bytes)
 {
+    const Phase ph("slab vote L%d", level);
     for (Slab &r : S)
         TRY(vote_range(r.ctx, level, r.hOff[level], r.hN[level]));
     vi_ctx *ctx = S[0].ctx;

@@ -276,6 +276,7 @@ vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, 
 
 static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
 {
+    const vi::Phase ph("batch round");
     if (!b)
         return VI_ERR_ARG;
     std::vector<Entry *> act;

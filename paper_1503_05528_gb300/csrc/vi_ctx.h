@@ -9,10 +9,29 @@
 #include <utility>
 #include <vector>
 
+#include <cstdio>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "vi.h"
 #include "vi_launch.h"
 
 namespace vi {
+
+// A named NVTX range for the lifetime of the object (phases of the method in
+// a profiler's timeline; a no-op unless a tool is attached). The name is
+// formatted like printf.
+struct Phase {
+    explicit Phase(const char *fmt, int a = 0, int b = 0)
+    {
+        char name[64];
+        std::snprintf(name, sizeof(name), fmt, a, b);
+        nvtxRangePushA(name);
+    }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
+};
 
 // Philox tag word: purpose (4 bits) | level (4) | call (16) | k (8).
 enum : uint32_t { PURPOSE_INIT = 1, PURPOSE_SEARCH = 2, PURPOSE_UPSAMPLE = 3, PURPOSE_ONION = 4 };

@@ -32,6 +32,7 @@ EXPORTS = [
     "vi_affine_align", "vi_affine_unwarp",
     "vi_server_create", "vi_server_submit", "vi_server_poll", "vi_server_wait", "vi_server_release",
     "vi_server_info", "vi_server_destroy", "vi_run_slabs", "vi_slabs_last_error",
+    "vi_state_bytes", "vi_save_state", "vi_load_state", "vi_resume",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -137,6 +138,11 @@ def _declare(L):
     L.vi_affine_to_reference.argtypes = [vp, i, vp]
     L.vi_affine_align.argtypes = [vp, vp, i, i, i, vp, vp, vp, i, vp]
     L.vi_affine_unwarp.argtypes = [vp, vp, vp, i, i, i, vp, vp, i, vp]
+    L.vi_state_bytes.argtypes = [vp, i]
+    L.vi_state_bytes.restype = C.c_size_t
+    L.vi_save_state.argtypes = [vp, i, vp, C.c_size_t]
+    L.vi_load_state.argtypes = [vp, i, vp, C.c_size_t]
+    L.vi_resume.argtypes = [vp, i, i]
     L.vi_run_slabs.argtypes = [P(ViConfig), vp, vp, i, i, i, i, i, vp, P(ViStats), P(C.c_ulonglong), vp]
     L.vi_slabs_last_error.argtypes = []
     L.vi_slabs_last_error.restype = C.c_char_p
@@ -325,6 +331,23 @@ class Context:
         p, dev = _ptr(out)
         self._ck(self.lib.vi_fetch_result(self.h, p, dev))
         return out
+
+    def save_state(self, level):
+        """The level's state between two iterations (vi_save_state), as bytes."""
+        n = self.lib.vi_state_bytes(self.h, level)
+        if n == 0:
+            raise ViError(1, "vi_state_bytes: bad level or no pyramid")
+        buf = C.create_string_buffer(n)
+        self._ck(self.lib.vi_save_state(self.h, level, buf, n))
+        return buf.raw
+
+    def load_state(self, level, state):
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._ck(self.lib.vi_load_state(self.h, level, buf, len(state)))
+
+    def resume(self, level, first_call):
+        """The rest of Algorithm 4 from call first_call of level (vi_resume)."""
+        self._ck(self.lib.vi_resume(self.h, level, first_call))
 
     def profile(self, enable=True):
         self._ck(self.lib.vi_profile(self.h, 1 if enable else 0))

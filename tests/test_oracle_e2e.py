@@ -128,3 +128,17 @@ def test_multilevel_with_texture_runs():
     assert np.isfinite(out).all()
     assert pyr[1].stats["onion_layers"] >= 1
     assert pyr[0].stats["outer"] == [2] and pyr[1].stats["outer"] == [3]
+
+
+def test_iteration_cap_counts_from_call_zero():
+    # Sec. 3.7's cap of max_outer iterations per level counts the level's
+    # iterations from call 0: a loop resumed at call start_call runs at most
+    # max_outer - start_call more
+    from paper_1503_05528_gb300 import synth as S
+    c = S.small_layered(W=40, H=32, T=10, levels=1, seed=1903)
+    lv = O.build_pyramid(c.rgb, c.mask, 1, True)[0]
+    lv.phi = O.init_nnf(lv.htilde, lv.dtilde, (1, 1), O.tag(O.PURPOSE_INIT, 0))
+    lv.d2 = np.full(lv.hole.shape, np.inf, np.float32)
+    prm = O.Params(seed=5, stop=0.0, max_outer=4)      # stop 0: only the cap ends the loop
+    assert O.iterate_level(lv, prm, 0, start_call=2) == 2
+    assert O.iterate_level(lv, prm, 0, start_call=4) == 0
