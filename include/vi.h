@@ -306,6 +306,12 @@ vi_status vi_fetch_result(vi_ctx *ctx, float *rgb_out, int ptr_is_device);
  * slowing the profiled run. */
 vi_status vi_profile(vi_ctx *ctx, int enable);
 
+/* The iterations run since the last upload that computed e (vi_iterate with
+ * the stopping rule or with e_last_host): for record i < cap its level, call
+ * index, e (Sec. 3.7) and the context's evaluation count after it, into the
+ * nullable arrays. Returns the number of records (-1 for a null context). */
+int vi_iteration_log(vi_ctx *ctx, int cap, int *level, int *call, float *e, unsigned long long *evals);
+
 /* The context's counters (synchronises to read event times). */
 vi_status vi_get_stats(vi_ctx *ctx, vi_stats *out);
 

@@ -582,6 +582,7 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
     // evaluation / launch / time counters accumulate over the context's life;
     // the per-run counters restart with every upload
     ctx->onion_layers = 0;
+    ctx->iter_log.clear();
     std::memset(ctx->outer, 0, sizeof(ctx->outer));
     ctx->uploaded = true;
     ctx->err.clear();
@@ -809,6 +810,8 @@ vi_status vi_reconstruct(vi_ctx *ctx, int level, float *e_host)
     TRY(vote_level(ctx, level, e_host ? ctx->scal : nullptr));
     if (e_host) {
         CK(cudaMemcpyAsync(ctx->host_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->host_evals, ctx->evals_dev, sizeof(ctx->host_evals), cudaMemcpyDeviceToHost,
+                           ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         const int nH = ctx->lv[level].nH;
         *e_host = nH ? (float)(ctx->host_scal[0] / (3.0 * nH)) : 0.0f;
@@ -832,7 +835,14 @@ vi_status vi_iterate(vi_ctx *ctx, int level, int n_outer, int first_call, int *n
     while (rule ? (e > ctx->cfg.stop && first_call + k < ctx->cfg.max_outer) : (k < n_outer)) {
         const Phase it("L%d iteration %d", level, first_call + k);
         TRY(vi_ann(ctx, level, first_call + k));
-        TRY(vi_reconstruct(ctx, level, (rule || e_last_host) ? &e : nullptr));
+        const bool want_e = rule || e_last_host;
+        TRY(vi_reconstruct(ctx, level, want_e ? &e : nullptr));
+        if (want_e) {
+            try {
+                ctx->iter_log.push_back({level, first_call + k, e, ctx->host_evals[0] + ctx->host_evals[1]});
+            } catch (...) {   // the log is a convenience: a full host heap only shortens it
+            }
+        }
         ++k;
     }
     if (level < 16)
@@ -899,6 +909,25 @@ size_t state_bytes(vi_ctx *ctx, int level)
 }
 
 }  // namespace
+
+int vi_iteration_log(vi_ctx *ctx, int cap, int *level, int *call, float *e, unsigned long long *evals)
+{
+    if (!ctx)
+        return -1;
+    const int n = (int)ctx->iter_log.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        const auto &r = ctx->iter_log[(size_t)i];
+        if (level)
+            level[i] = r.level;
+        if (call)
+            call[i] = r.call;
+        if (e)
+            e[i] = r.e;
+        if (evals)
+            evals[i] = r.evals;
+    }
+    return n;
+}
 
 size_t vi_state_bytes(vi_ctx *ctx, int level)
 {

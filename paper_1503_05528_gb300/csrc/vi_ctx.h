@@ -104,6 +104,13 @@ struct vi_ctx {
     double *scal = nullptr;        // device scalars
     double host_scal[8] = {0};     // host copies of scal (read after a stream synchronisation)
     int host_counts[64] = {0};     // host copies of count_dev
+    unsigned long long host_evals[6] = {0};   // host copy of evals_dev, read with e
+    struct IterRecord {
+        int level, call;
+        float e;
+        unsigned long long evals;   // evaluations of the context so far
+    };
+    std::vector<IterRecord> iter_log;   // one record per iteration that computed e (since the upload)
     // [0] rescore evals, [1] step evals, [2] FP32 voxels gathered by the step,
     // [3] FP16 voxels gathered, [4] candidates screened, [5] screened and passed
     unsigned long long *evals_dev = nullptr;

@@ -32,7 +32,7 @@ EXPORTS = [
     "vi_affine_align", "vi_affine_unwarp",
     "vi_server_create", "vi_server_submit", "vi_server_poll", "vi_server_wait", "vi_server_release",
     "vi_server_info", "vi_server_destroy", "vi_run_slabs", "vi_slabs_last_error",
-    "vi_state_bytes", "vi_save_state", "vi_load_state", "vi_resume",
+    "vi_state_bytes", "vi_save_state", "vi_load_state", "vi_resume", "vi_iteration_log",
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
@@ -138,6 +138,8 @@ def _declare(L):
     L.vi_affine_to_reference.argtypes = [vp, i, vp]
     L.vi_affine_align.argtypes = [vp, vp, i, i, i, vp, vp, vp, i, vp]
     L.vi_affine_unwarp.argtypes = [vp, vp, vp, i, i, i, vp, vp, i, vp]
+    L.vi_iteration_log.argtypes = [vp, i, P(i), P(i), P(C.c_float), P(C.c_ulonglong)]
+    L.vi_iteration_log.restype = i
     L.vi_state_bytes.argtypes = [vp, i]
     L.vi_state_bytes.restype = C.c_size_t
     L.vi_save_state.argtypes = [vp, i, vp, C.c_size_t]
@@ -331,6 +333,15 @@ class Context:
         p, dev = _ptr(out)
         self._ck(self.lib.vi_fetch_result(self.h, p, dev))
         return out
+
+    def iteration_log(self):
+        """Per iteration that computed e: level, call, e and the evaluation
+        count after it (vi_iteration_log)."""
+        n = self.lib.vi_iteration_log(self.h, 0, None, None, None, None)
+        lv, ca = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+        e, ev = (C.c_float * max(n, 1))(), (C.c_ulonglong * max(n, 1))()
+        self.lib.vi_iteration_log(self.h, n, lv, ca, e, ev)
+        return [dict(level=lv[i], call=ca[i], e=e[i], evals=ev[i]) for i in range(n)]
 
     def save_state(self, level):
         """The level's state between two iterations (vi_save_state), as bytes."""

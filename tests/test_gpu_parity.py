@@ -335,6 +335,35 @@ def test_end_to_end_energy_layered_two_levels():
     assert e_gpu <= 1.02 * es["SEQ"], (e_gpu, es)
 
 
+def test_iteration_log_follows_the_stopping_rule():
+    # vi_iteration_log: one record per iteration of the stopping rule, in
+    # level order with call indices 0, 1, ...; a level ends at e <= stop or
+    # at the cap; the evaluation count grows; and the first iteration of the
+    # coarsest level has the oracle's e (its state before that iteration is
+    # the oracle's, bit for bit, up to the vote's rounding)
+    clip = synth.small_layered(W=72, H=56, T=14, levels=2, seed=1517)
+    with vi.Context(levels=2, use_texture=1, seed=68) as ctx:
+        ctx.upload(clip.rgb, clip.mask)
+        ctx.run()
+        log = ctx.iteration_log()
+        outer = ctx.stats()["outer"][:2]
+        cfg = vi.default_config()
+    assert len(log) == sum(outer)
+    i = 0
+    for level in (1, 0):
+        recs = log[i:i + outer[level]]
+        i += outer[level]
+        assert [r["level"] for r in recs] == [level] * outer[level]
+        assert [r["call"] for r in recs] == list(range(outer[level]))
+        assert all(r["e"] > cfg.stop for r in recs[:-1])
+        assert recs[-1]["e"] <= cfg.stop or outer[level] == cfg.max_outer
+    assert all(a["evals"] < b["evals"] for a, b in zip(log, log[1:]))
+    prm = O.Params(seed=68)
+    _, pyr, _ = O.inpaint(clip.rgb, clip.mask, 2, use_texture=True, prm=prm, return_levels=True)
+    e_oracle = pyr[1].stats["e"][0]
+    assert abs(log[0]["e"] - e_oracle) <= 1e-3 * e_oracle
+
+
 def test_run_is_deterministic_and_keeps_known_voxels():
     clip = synth.small_layered(W=72, H=56, T=14, levels=2, seed=1516)
     outs = []
