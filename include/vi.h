@@ -107,6 +107,12 @@ typedef struct {
                             every level also halves the frames (2x2x2 means,
                             occlusion by OR, features sampled at (2^l x, 2^l y,
                             2^l t), shifts upsampled with dt doubled) */
+    size_t mem_limit;    /* device bytes a context may hold at once (0: no
+                            limit); an allocation beyond it fails with
+                            VI_ERR_OOM as if the device were full, so the
+                            failure paths can be exercised without
+                            exhausting the GPU. vi_footprint_bytes is a
+                            limit every run stays within. */
 } vi_config;
 
 /* Per-context counters. evals, step_*: since vi_ctx_create; outer and

@@ -68,6 +68,10 @@ vi_status dalloc(vi_ctx *ctx, P **ptr, size_t bytes)
     *ptr = nullptr;
     if (bytes == 0)
         bytes = 16;
+    if (ctx->cfg.mem_limit && ctx->held + bytes > ctx->cfg.mem_limit)
+        return fail(ctx, VI_ERR_OOM,
+                    "allocation of " + std::to_string(bytes) + " bytes beyond the context's memory limit (" +
+                        std::to_string(ctx->held) + " of " + std::to_string(ctx->cfg.mem_limit) + " held)");
     cudaError_t e = cudaMallocAsync((void **)ptr, bytes, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -75,14 +79,28 @@ vi_status dalloc(vi_ctx *ctx, P **ptr, size_t bytes)
         return fail(ctx, e == cudaErrorMemoryAllocation ? VI_ERR_OOM : VI_ERR_CUDA,
                     std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
+    try {
+        ctx->sizes[(const void *)*ptr] = bytes;
+    } catch (...) {
+        cudaFreeAsync((void *)*ptr, ctx->stream);
+        *ptr = nullptr;
+        return fail(ctx, VI_ERR_OOM, "host allocation");
+    }
+    ctx->held += bytes;
     return VI_OK;
 }
 
 template <typename P>
 void dfree(vi_ctx *ctx, P *&ptr)
 {
-    if (ptr)
+    if (ptr) {
+        auto it = ctx->sizes.find((const void *)ptr);
+        if (it != ctx->sizes.end()) {
+            ctx->held -= it->second;
+            ctx->sizes.erase(it);
+        }
         cudaFreeAsync((void *)ptr, ctx->stream);
+    }
     ptr = nullptr;
 }
 
@@ -414,6 +432,7 @@ void vi_config_default(vi_config *cfg)
     cfg->rs_mode = 0;
     cfg->sub_sweeps = 1;
     cfg->time_subsample = 0;
+    cfg->mem_limit = 0;
 }
 
 vi_status vi_ctx_create(const vi_config *cfg, void *cuda_stream, vi_ctx **out)

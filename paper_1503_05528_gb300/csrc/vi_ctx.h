@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -111,6 +112,8 @@ struct vi_ctx {
         unsigned long long evals;   // evaluations of the context so far
     };
     std::vector<IterRecord> iter_log;   // one record per iteration that computed e (since the upload)
+    size_t held = 0;                    // device bytes held (checked against cfg.mem_limit)
+    std::unordered_map<const void *, size_t> sizes;   // bytes of each allocation
     // [0] rescore evals, [1] step evals, [2] FP32 voxels gathered by the step,
     // [3] FP16 voxels gathered, [4] candidates screened, [5] screened and passed
     unsigned long long *evals_dev = nullptr;

@@ -45,7 +45,7 @@ class ViConfig(C.Structure):
                 ("weighted", C.c_int), ("use_texture", C.c_int), ("storage", C.c_int),
                 ("seed", C.c_uint64), ("clip", C.c_uint32), ("lanes_per_target", C.c_int),
                 ("stream_priority", C.c_int), ("rs_mode", C.c_int), ("sub_sweeps", C.c_int),
-                ("time_subsample", C.c_int)]
+                ("time_subsample", C.c_int), ("mem_limit", C.c_size_t)]
 
 
 class ViStats(C.Structure):
