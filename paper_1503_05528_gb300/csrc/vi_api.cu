@@ -566,7 +566,21 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
     CK(cudaMemcpyAsync(ctx->mask, mask, V0, kind, ctx->stream));
     TRY(dalloc(ctx, &ctx->tmpA, V0));
     TRY(dalloc(ctx, &ctx->tmpB, V0));
-    TRY(dalloc(ctx, &ctx->block_counts, sizeof(int) * (size_t)(compact_blocks(ctx->V0) + 1)));
+    {
+        // the per-block counts of every level's three lists (kept from the
+        // sizing pass to the writing pass), or of one level-0 list
+        size_t n = 0;
+        int w = W, h = H, tl = T;
+        for (int l = 0; l < L; ++l) {
+            n += 3 * (size_t)(compact_blocks(w * h * tl) + 1);
+            w = (w + 1) / 2;
+            h = (h + 1) / 2;
+            if (ctx->cfg.time_subsample)
+                tl = (tl + 1) / 2;
+        }
+        n = std::max(n, (size_t)compact_blocks(ctx->V0) + 1);
+        TRY(dalloc(ctx, &ctx->block_counts, sizeof(int) * n));
+    }
 
     ctx->lv.assign(L, Level());
     int w = W, h = H, tl = T;
@@ -669,12 +683,14 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         launch_shadow_all(ctx->lv[l].view(), st);
         CK_LAUNCH();
     }
-    // list sizes (one synchronisation), then the lists
+    // list sizes of every level (one synchronisation), then the lists
+    const uchar3 sets = make_uchar3(CODE_TARGET, CODE_HOLE, CODE_SOURCE);
+    std::vector<size_t> base((size_t)ctx->L, 0);
     for (int l = 0; l < ctx->L; ++l) {
         Level &lv = ctx->lv[l];
-        launch_compact(lv.code, CODE_TARGET, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l, st);
-        launch_compact(lv.code, CODE_HOLE, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l + 1, st);
-        launch_compact(lv.code, CODE_SOURCE, lv.V, ctx->block_counts, nullptr, ctx->count_dev + 3 * l + 2, st);
+        if (l > 0)
+            base[(size_t)l] = base[(size_t)l - 1] + 3 * (size_t)(compact_blocks(ctx->lv[l - 1].V) + 1);
+        launch_compact3_count(lv.code, sets, lv.V, ctx->block_counts + base[(size_t)l], ctx->count_dev + 3 * l, st);
         CK_LAUNCH();
     }
     CK(cudaMemcpyAsync(ctx->host_counts, ctx->count_dev, sizeof(int) * 3 * ctx->L, cudaMemcpyDeviceToHost, st));
@@ -694,9 +710,8 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         TRY(dalloc(ctx, &lv.targets, sizeof(int) * (size_t)std::max(lv.nT, 1)));
         TRY(dalloc(ctx, &lv.holes, sizeof(int) * (size_t)std::max(lv.nH, 1)));
         TRY(dalloc(ctx, &lv.sources, sizeof(int) * (size_t)std::max(lv.nS, 1)));
-        launch_compact(lv.code, CODE_TARGET, lv.V, ctx->block_counts, lv.targets, ctx->count_dev, st);
-        launch_compact(lv.code, CODE_HOLE, lv.V, ctx->block_counts, lv.holes, ctx->count_dev, st);
-        launch_compact(lv.code, CODE_SOURCE, lv.V, ctx->block_counts, lv.sources, ctx->count_dev, st);
+        launch_compact3_write(lv.code, sets, lv.V, ctx->block_counts + base[(size_t)l], lv.targets, lv.holes,
+                              lv.sources, st);
         CK_LAUNCH();
         max_list = std::max(max_list, lv.nH);
         max_t = std::max(max_t, lv.nT);

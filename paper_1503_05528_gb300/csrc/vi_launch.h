@@ -37,6 +37,12 @@ void launch_codes(LevelView L, uint8_t *tmp_a, uint8_t *tmp_b, cudaStream_t st);
 // Raster-ordered compaction of {v : (flags[v] & bits) != 0} into list.
 // block_counts needs compact_blocks(V) + 1 ints; *count_dev receives the size.
 int compact_blocks(int V);
+// Three lists at once: block_counts needs 3 * (compact_blocks(V) + 1) ints,
+// which the write pass reads again; count_dev[0..2] receive the sizes.
+void launch_compact3_count(const uint8_t *flags, uchar3 bits, int V, int *block_counts, int *count_dev,
+                           cudaStream_t st);
+void launch_compact3_write(const uint8_t *flags, uchar3 bits, int V, const int *block_counts, int *l0, int *l1,
+                           int *l2, cudaStream_t st);
 void launch_compact(const uint8_t *flags, uint8_t bits, int V, int *block_counts, int *list,
                     int *count_dev, cudaStream_t st);
 

@@ -299,8 +299,11 @@ __global__ void k_compact_count(const uint8_t *__restrict__ flags, uint8_t bits,
 }
 
 // Exclusive scan of counts[0..nb) in place; counts[nb] and *total get the sum.
-__global__ void k_compact_scan(int *counts, int nb, int *total)
+// Block j of the grid scans the array at counts + j * stride into total[j].
+__global__ void k_compact_scan(int *counts, int nb, int *total, int stride)
 {
+    counts += blockIdx.x * stride;
+    total += blockIdx.x;
     __shared__ int warp_tot[32];
     __shared__ int carry;
     if (threadIdx.x == 0)
@@ -371,10 +374,78 @@ void launch_compact(const uint8_t *flags, uint8_t bits, int V, int *block_counts
     VI_COUNT_LAUNCH();
     k_compact_count<<<nb, CB, 0, st>>>(flags, bits, V, block_counts);
     VI_COUNT_LAUNCH();
-    k_compact_scan<<<1, 1024, 0, st>>>(block_counts, nb, count_dev);
+    k_compact_scan<<<1, 1024, 0, st>>>(block_counts, nb, count_dev, 0);
     VI_COUNT_LAUNCH();
     if (list)
         k_compact_write<<<nb, CB, 0, st>>>(flags, bits, V, block_counts, list);
+}
+
+// The three lists of a level's set codes at once (bits b.x, b.y, b.z of
+// flags): one pass counts all three per block (counts j at
+// block_counts[j * (nb + 1) ..]), one launch scans the three arrays (sizes to
+// count_dev[0..2]), and after the caller has read the sizes and allocated
+// the lists, one pass writes all three, raster ordered, from the same
+// offsets.
+__global__ void k_compact_count3(const uint8_t *__restrict__ flags, uchar3 b, int V, int nb, int *counts)
+{
+    const int v = blockIdx.x * CB + threadIdx.x;
+    const unsigned f = v < V ? flags[v] : 0u;
+    const int c0 = __syncthreads_count(f & b.x);
+    const int c1 = __syncthreads_count(f & b.y);
+    const int c2 = __syncthreads_count(f & b.z);
+    if (threadIdx.x == 0) {
+        counts[blockIdx.x] = c0;
+        counts[(nb + 1) + blockIdx.x] = c1;
+        counts[2 * (nb + 1) + blockIdx.x] = c2;
+    }
+}
+
+__global__ void k_compact_write3(const uint8_t *__restrict__ flags, uchar3 b, int V, int nb,
+                                 const int *__restrict__ offsets, int *__restrict__ l0, int *__restrict__ l1,
+                                 int *__restrict__ l2)
+{
+    __shared__ int warp_cnt[3][CB / 32];
+    const int v = blockIdx.x * CB + threadIdx.x;
+    const unsigned f = v < V ? flags[v] : 0u;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned bits[3] = {b.x, b.y, b.z};
+    unsigned ballot[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        ballot[j] = __ballot_sync(0xffffffffu, (f & bits[j]) != 0u);
+        if (lane == 0)
+            warp_cnt[j][wid] = __popc(ballot[j]);
+    }
+    __syncthreads();
+    int *lists[3] = {l0, l1, l2};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (f & bits[j]) {
+            int before = 0;
+            for (int w = 0; w < wid; ++w)
+                before += warp_cnt[j][w];
+            before += __popc(ballot[j] & ((1u << lane) - 1u));
+            lists[j][offsets[j * (nb + 1) + blockIdx.x] + before] = v;
+        }
+    }
+}
+
+void launch_compact3_count(const uint8_t *flags, uchar3 bits, int V, int *block_counts, int *count_dev,
+                           cudaStream_t st)
+{
+    const int nb = compact_blocks(V);
+    VI_COUNT_LAUNCH();
+    k_compact_count3<<<nb, CB, 0, st>>>(flags, bits, V, nb, block_counts);
+    VI_COUNT_LAUNCH();
+    k_compact_scan<<<3, 1024, 0, st>>>(block_counts, nb, count_dev, nb + 1);
+}
+
+void launch_compact3_write(const uint8_t *flags, uchar3 bits, int V, const int *block_counts, int *l0, int *l1,
+                           int *l2, cudaStream_t st)
+{
+    const int nb = compact_blocks(V);
+    VI_COUNT_LAUNCH();
+    k_compact_write3<<<nb, CB, 0, st>>>(flags, bits, V, nb, block_counts, l0, l1, l2);
 }
 
 }  // namespace vi
