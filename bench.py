@@ -839,7 +839,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=16, help="serving: distinct clips")
     ap.add_argument("--hbm-budget-gb", type=float, default=96.0, help="serving: admission budget")
     ap.add_argument("--slots", type=int, default=32, help="serving: most requests admitted at once")
-    ap.add_argument("--serve-backend", default="streams", choices=["streams", "batch", "native"],
+    ap.add_argument("--serve-backend", default="native", choices=["streams", "batch", "native"],
                     help="serving: one stream per request by size priority (Python front), one shared batch, "
                          "or the library server (vi_server_*)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
