@@ -504,67 +504,62 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
     }
     Rejected rej;
     const Shift start = cur;
-    // Propagation, single clip: the three neighbours' candidates are gathered
-    // together, each bounded by the distance the target had before them, and
-    // then decided in order against the running best. A gather the bound
-    // stopped is at or above every later best, and a completed one has the
-    // exact distance, so the decisions are those of judging them one by one.
-    // A candidate equal to the current shift, or to an earlier candidate of
-    // the same target that is gathered, is decided by that one. (320x240x60:
-    // 18.5 against 19.9 ms per inpainting. In a batch, whose warps mix clips
-    // and need the level of every pair's owner, it measured slower, 1,392
-    // against 1,286 ms for 48 clips, so there the candidates go one by one.)
-    if (!MIXED) {
-        bool need[3] = {false, false, false};
-        unsigned long long key[3] = {0ull, 0ull, 0ull};
-        if (active) {
-            const unsigned long long k_cur = shift_key(cur.dx, cur.dy, cur.dt);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (sn[j] < 0)
-                    continue;
-                ++n.evals;
-                if (stale[j])
-                    continue;
-                key[j] = shift_key(cn[j].dx, cn[j].dy, cn[j].dt);
-                bool nj = key[j] != k_cur;
-#pragma unroll
-                for (int i = 0; i < j; ++i)
-                    nj = nj && !(need[i] && key[i] == key[j]);
-                need[j] = nj;
-            }
-        }
-        const unsigned M0 = __ballot_sync(FULL, need[0]), M1 = __ballot_sync(FULL, need[1]),
-                       M2 = __ballot_sync(FULL, need[2]);
-        if (M0 | M1 | M2) {
-            float dist[3] = {INF, INF, INF};
-            warp_d2_multi<C5, MIXED>(L, M0, M1, M2, lane, p, px, py, pt, sn[0], sn[1], sn[2], d, dist, n.gathered);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (!need[j])
-                    continue;
-                if (dist[j] < d) {
-                    d = dist[j];
-                    cur = cn[j];
-                } else {
-                    rej.add(key[j]);
-                }
-            }
-        }
-    } else {
+    if (MIXED) {
+        // batch: every candidate judged one stage at a time (the single-clip
+        // form below measured slower where warps mix clips)
 #pragma unroll 1
-        for (int j = 0; j < 3; ++j) {
-            // (a register array indexed by a loop variable would spill: select)
-            const Shift c = j == 0 ? cn[0] : (j == 1 ? cn[1] : cn[2]);
-            const int s = j == 0 ? sn[0] : (j == 1 ? sn[1] : sn[2]);
-            const bool skip = j == 0 ? stale[0] : (j == 1 ? stale[1] : stale[2]);
+        for (int stage = 0;; ++stage) {
+            int s = -1, cdx = 0, cdy = 0, cdt = 0;
+            bool skip = false;
+            // does this lane's target have a candidate at this stage
+            bool mine = active;
+            int ri = 0, sh = 0;
+            if (stage >= 3 && active) {
+                ri = stage - 3;
+                sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
+                mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
+            }
+            if (!__any_sync(FULL, mine))
+                break;
+            if (stage < 3) {
+                // (a register array indexed by a loop variable would spill: select)
+                const Shift c = stage == 0 ? cn[0] : (stage == 1 ? cn[1] : cn[2]);
+                s = stage == 0 ? sn[0] : (stage == 1 ? sn[1] : sn[2]);
+                skip = stage == 0 ? stale[0] : (stage == 1 ? stale[1] : stale[2]);
+                cdx = c.dx;
+                cdy = c.dy;
+                cdt = c.dt;
+            } else if (mine) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
+                                                         a.rs_mode ? (uint32_t)ri : 0u),
+                                              a.key0, a.key1);
+                cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
+                cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
+                cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
+                s = source_of(L, px, py, pt, cdx, cdy, cdt);
+            }
             bool need = false;
             unsigned long long key = 0;
             if (active && s >= 0) {
                 ++n.evals;
                 if (!skip) {
-                    key = shift_key(c.dx, c.dy, c.dt);
+                    key = shift_key(cdx, cdy, cdt);
                     need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
+                }
+            }
+            if (F16 && stage >= 3) {
+                const unsigned M = __ballot_sync(FULL, need);
+                if (M) {
+                    const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                    if (need) {
+                        ++n.screened;
+                        if (pass) {
+                            ++n.passed;
+                        } else {
+                            rej.add(key);
+                            need = false;
+                        }
+                    }
                 }
             }
             const unsigned M = __ballot_sync(FULL, need);
@@ -573,70 +568,121 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
                 if (need) {
                     if (dd < d) {
                         d = dd;
-                        cur = c;
+                        cur.dx = (short)cdx;
+                        cur.dy = (short)cdy;
+                        cur.dt = (short)cdt;
                     } else {
                         rej.add(key);
                     }
                 }
             }
         }
-    }
-    // random search
+    } else {
+        // Propagation, single clip: the three neighbours' candidates are gathered
+        // together, each bounded by the distance the target had before them, and
+        // then decided in order against the running best. A gather the bound
+        // stopped is at or above every later best, and a completed one has the
+        // exact distance, so the decisions are those of judging them one by one.
+        // A candidate equal to the current shift, or to an earlier candidate of
+        // the same target that is gathered, is decided by that one. (320x240x60:
+        // 18.5 against 19.9 ms per inpainting. In a batch, whose warps mix clips
+        // and need the level of every pair's owner, it measured slower, 1,392
+        // against 1,286 ms for 48 clips, so there the candidates go one by one.)
+        {
+            bool need[3] = {false, false, false};
+            unsigned long long key[3] = {0ull, 0ull, 0ull};
+            if (active) {
+                const unsigned long long k_cur = shift_key(cur.dx, cur.dy, cur.dt);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (sn[j] < 0)
+                        continue;
+                    ++n.evals;
+                    if (stale[j])
+                        continue;
+                    key[j] = shift_key(cn[j].dx, cn[j].dy, cn[j].dt);
+                    bool nj = key[j] != k_cur;
+#pragma unroll
+                    for (int i = 0; i < j; ++i)
+                        nj = nj && !(need[i] && key[i] == key[j]);
+                    need[j] = nj;
+                }
+            }
+            const unsigned M0 = __ballot_sync(FULL, need[0]), M1 = __ballot_sync(FULL, need[1]),
+                           M2 = __ballot_sync(FULL, need[2]);
+            if (M0 | M1 | M2) {
+                float dist[3] = {INF, INF, INF};
+                warp_d2_multi<C5, MIXED>(L, M0, M1, M2, lane, p, px, py, pt, sn[0], sn[1], sn[2], d, dist, n.gathered);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (!need[j])
+                        continue;
+                    if (dist[j] < d) {
+                        d = dist[j];
+                        cur = cn[j];
+                    } else {
+                        rej.add(key[j]);
+                    }
+                }
+            }
+        }
+        // random search
 #pragma unroll 1
-    for (int stage = 3;; ++stage) {
-        int s = -1, cdx = 0, cdy = 0, cdt = 0;
-        // does this lane's target have a candidate at this stage
-        bool mine = false;
-        int ri = 0, sh = 0;
-        if (active) {
-            ri = stage - 3;
-            sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
-            mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
-        }
-        if (!__any_sync(FULL, mine))
-            break;
-        if (mine) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
-                                                     a.rs_mode ? (uint32_t)ri : 0u),
-                                          a.key0, a.key1);
-            cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
-            cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
-            cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
-            s = source_of(L, px, py, pt, cdx, cdy, cdt);
-        }
-        bool need = false;
-        unsigned long long key = 0;
-        if (active && s >= 0) {
-            ++n.evals;
-            key = shift_key(cdx, cdy, cdt);
-            need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
-        }
-        if (F16) {
+        for (int stage = 3;; ++stage) {
+            int s = -1, cdx = 0, cdy = 0, cdt = 0;
+            // does this lane's target have a candidate at this stage
+            bool mine = false;
+            int ri = 0, sh = 0;
+            if (active) {
+                ri = stage - 3;
+                sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
+                mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
+            }
+            if (!__any_sync(FULL, mine))
+                break;
+            if (mine) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
+                                                         a.rs_mode ? (uint32_t)ri : 0u),
+                                              a.key0, a.key1);
+                cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
+                cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
+                cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
+                s = source_of(L, px, py, pt, cdx, cdy, cdt);
+            }
+            bool need = false;
+            unsigned long long key = 0;
+            if (active && s >= 0) {
+                ++n.evals;
+                key = shift_key(cdx, cdy, cdt);
+                need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
+            }
+            if (F16) {
+                const unsigned M = __ballot_sync(FULL, need);
+                if (M) {
+                    const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                    if (need) {
+                        ++n.screened;
+                        if (pass) {
+                            ++n.passed;
+                        } else {
+                            rej.add(key);
+                            need = false;
+                        }
+                    }
+                }
+            }
             const unsigned M = __ballot_sync(FULL, need);
             if (M) {
-                const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                const float dd = warp_d2<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, n.gathered);
                 if (need) {
-                    ++n.screened;
-                    if (pass) {
-                        ++n.passed;
+                    if (dd < d) {
+                        d = dd;
+                        cur.dx = (short)cdx;
+                        cur.dy = (short)cdy;
+                        cur.dt = (short)cdt;
                     } else {
                         rej.add(key);
-                        need = false;
                     }
-                }
-            }
-        }
-        const unsigned M = __ballot_sync(FULL, need);
-        if (M) {
-            const float dd = warp_d2<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, n.gathered);
-            if (need) {
-                if (dd < d) {
-                    d = dd;
-                    cur.dx = (short)cdx;
-                    cur.dy = (short)cdy;
-                    cur.dt = (short)cdt;
-                } else {
-                    rej.add(key);
                 }
             }
         }
