@@ -53,7 +53,7 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # (profiles/k_ann_step_layered_320x240x60.md). Applies to that configuration
 # only; None while the kernels have changed since the capture.
 NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32", "rs_mode": "eq3", "sub_sweeps": 1,
-                    "bytes": (3442.53e6 + 25.09e6) / 330, "gathered_voxels": 70003159.6 / 20}
+                    "bytes": (3634.43e6 + 38.00e6) / 330, "gathered_voxels": 68953343.0 / 20}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
