@@ -176,3 +176,75 @@ def test_stream_priority_by_size():
     p = [StreamBackend.priority(v) for v in (1, 1_999_999, 2_000_000, 7_999_999, 8_000_000, 31_999_999,
                                              32_000_000, 10 ** 9)]
     assert p == [-3, -3, -2, -2, -1, -1, 0, 0]
+
+
+class FakeNativeServer:
+    """Stands in for vi.Server (the library's server): every request finishes
+    after a number of polls; a request with fail=True ends in the failed
+    state and its release raises."""
+
+    def __init__(self, hbm_budget, max_slots=8, **defaults):
+        self.jobs = {}
+        self.next = 1
+        self.closed = False
+
+    def submit(self, rgb, mask, out=None, **job):
+        t = self.next
+        self.next += 1
+        self.jobs[t] = {"left": job.get("polls", 1), "fail": job.get("fail", False), "rgb": rgb}
+        return t
+
+    def poll(self, t):
+        j = self.jobs[t]
+        if j["left"] > 0:
+            j["left"] -= 1
+            return 0
+        return -1 if j["fail"] else 1
+
+    def wait(self, t, timeout=-1.0):
+        j = self.jobs[t]
+        return 0 if j["left"] > 0 else (-1 if j["fail"] else 1)
+
+    def release(self, t):
+        j = self.jobs.pop(t)
+        if j["fail"]:
+            from paper_1503_05528_gb300 import vi
+            raise vi.ViError(6, "request failed: planted")
+        return ("result", j["rgb"])
+
+    def info(self):
+        return dict(queued=0, running=sum(1 for j in self.jobs.values() if j["left"] > 0), bytes_in_use=0)
+
+    def close(self):
+        self.closed = True
+
+
+def test_native_front_bookkeeping(monkeypatch):
+    # NativeServer (the submit/step front over vi_server_*): tickets numbered
+    # from 0 in arrival order, results handed back with their latency,
+    # failures recorded with the library's message, the server closed
+    from paper_1503_05528_gb300 import serve, vi
+    monkeypatch.setattr(vi, "Server", FakeNativeServer)
+
+    class Clock:
+        t = 0.0
+
+        def __call__(self):
+            return self.t
+
+    clock = Clock()
+    srv = serve.NativeServer(1 << 30, 4, clock=clock)
+    t0 = srv.submit("a", None, arrival=0.0, polls=2)
+    t1 = srv.submit("b", None, arrival=0.5, polls=0, fail=True)
+    t2 = srv.submit("c", None, arrival=1.0, polls=1)
+    assert (t0, t1, t2) == (0, 1, 2)
+    clock.t = 2.0
+    while srv.step():
+        clock.t += 1.0
+    assert srv.pending() == 0 and set(srv.done) == {0, 1, 2}
+    assert srv.done[0].result == ("result", "a") and srv.done[2].result == ("result", "c")
+    assert srv.done[1].info.get("failed") and "planted" in srv.done[1].info["error"]
+    # finished at the step that saw them done: t = 2 (failed), 3, 4
+    assert {t: r.latency for t, r in srv.done.items()} == {0: 4.0, 1: 1.5, 2: 2.0}
+    srv.close()
+    assert srv.srv.closed
