@@ -413,19 +413,24 @@ void vi_server_destroy(vi_server *s);
  * slab's occluded voxels to every context; and the per-voxel changes into
  * context 0, which sums e over the whole list
  * in vi_run's order. The output, the iteration counts and the evaluation
- * count are identical to vi_run's. All contexts run on the current device on
- * one stream (cuda_stream, or one context 0 creates; NULL), which orders the
- * copies: this is the decomposition a multi-GPU run would use, exchanging
- * with peer copies instead. rgb, mask, rgb_out as in vi_upload /
+ * count are identical to vi_run's. With devices NULL all contexts run on the
+ * current device on one stream (cuda_stream, or one context 0 creates),
+ * which orders the copies. With devices (n_slabs entries; cuda_stream must
+ * be NULL) slab r's context runs on device devices[r] on a stream of its
+ * own, the copies are peer copies, and events order them: every exchange
+ * waits for all work issued on every stream before it, and the next step
+ * for the exchange (with device buffers devices[0] must be the current
+ * device, where rgb_out lives). The result is the same either way. rgb,
+ * mask, rgb_out as in vi_upload /
  * vi_fetch_result (ptr_is_device); stats_out (nullable) receives context 0's
  * counters with every slab's evaluations; exchanged_bytes (nullable) the
  * bytes copied between contexts. Errors: VI_ERR_ARG (n_slabs outside
- * 1 .. min(16, T), FP16 storage, temporal subsampling; text in
- * vi_slabs_last_error), others as vi_run.
+ * 1 .. min(16, T), FP16 storage, temporal subsampling, a stream with devices,
+ * a bad device; text in vi_slabs_last_error), others as vi_run.
  * ------------------------------------------------------------------------- */
 vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *mask, int W, int H, int T,
                        int ptr_is_device, int n_slabs, float *rgb_out, vi_stats *stats_out,
-                       unsigned long long *exchanged_bytes, void *cuda_stream);
+                       unsigned long long *exchanged_bytes, void *cuda_stream, const int *devices);
 const char *vi_slabs_last_error(void);
 
 /* ---------------------------------------------------------------------------

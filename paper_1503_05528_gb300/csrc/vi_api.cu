@@ -1409,6 +1409,8 @@ thread_local std::string g_slab_err;
 
 struct Slab {
     vi_ctx *ctx = nullptr;
+    int dev = 0;                          // device of the context
+    cudaEvent_t ev = nullptr;             // with a stream per slab: marks its progress for the others
     int t0 = 0, t1 = 0;                   // frames owned
     std::vector<int> tOff, tN, hOff, hN;  // per level: ranges of the target and occluded-voxel lists
     float4 *buf4 = nullptr;               // channels of occluded voxels, indexed like the level's list
@@ -1423,16 +1425,48 @@ int slab_of(const std::vector<Slab> &S, int t)
     return (int)S.size() - 1;
 }
 
-// Frames [ta, tb) of a per-voxel array of one context into another's.
-template <typename E>
-vi_status copy_frames(vi_ctx *ctx, E *dst, const E *src, int HW, int ta, int tb, unsigned long long &bytes)
+// With a stream per slab (possibly on different devices), every stream waits
+// for all work issued so far on every other one; with one shared stream,
+// stream order already does it.
+vi_status barrier(std::vector<Slab> &S)
 {
-    if (tb <= ta || dst == src || !dst || !src)
+    if (!S[0].ev)
         return VI_OK;
-    const size_t n = (size_t)(tb - ta) * HW * sizeof(E);
-    CK(cudaMemcpyAsync(dst + (size_t)ta * HW, src + (size_t)ta * HW, n, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (Slab &r : S) {
+        vi_ctx *ctx = r.ctx;
+        CK(cudaSetDevice(r.dev));
+        CK(cudaEventRecord(r.ev, ctx->stream));
+    }
+    for (Slab &dst : S) {
+        vi_ctx *ctx = dst.ctx;
+        CK(cudaSetDevice(dst.dev));
+        for (Slab &src : S)
+            if (&src != &dst)
+                CK(cudaStreamWaitEvent(ctx->stream, src.ev, 0));
+    }
+    return VI_OK;
+}
+
+// n bytes at src (slab from's device) to dst (slab to's device), on to's stream.
+vi_status copy_between(Slab &to, Slab &from, void *dst, const void *src, size_t n, unsigned long long &bytes)
+{
+    vi_ctx *ctx = to.ctx;
+    if (!n || dst == src || !dst || !src)
+        return VI_OK;
+    CK(cudaSetDevice(to.dev));
+    CK(cudaMemcpyPeerAsync(dst, to.dev, src, from.dev, n, ctx->stream));
     bytes += n;
     return VI_OK;
+}
+
+// Frames [ta, tb) of a per-voxel array of one context into another's.
+template <typename E>
+vi_status copy_frames(Slab &to, Slab &from, E *dst, const E *src, int HW, int ta, int tb, unsigned long long &bytes)
+{
+    if (tb <= ta)
+        return VI_OK;
+    return copy_between(to, from, dst + (size_t)ta * HW, src + (size_t)ta * HW, (size_t)(tb - ta) * HW * sizeof(E),
+                        bytes);
 }
 
 // Every slab receives the frames within w of its range from their owners:
@@ -1441,21 +1475,22 @@ vi_status exchange_halo(std::vector<Slab> &S, int level, int w, int b, bool phi,
                         unsigned long long &bytes)
 {
     const int T = S[0].ctx->lv[level].T, HW = S[0].ctx->lv[level].W * S[0].ctx->lv[level].H;
+    TRY(barrier(S));
     for (Slab &dst : S) {
         for (int t = std::max(dst.t0 - w, 0); t < std::min(dst.t1 + w, T); ++t) {
             if (t >= dst.t0 && t < dst.t1)
                 continue;
-            vi_ctx *src = S[slab_of(S, t)].ctx;
-            Level &ld = dst.ctx->lv[level], &ls = src->lv[level];
+            Slab &src = S[slab_of(S, t)];
+            Level &ld = dst.ctx->lv[level], &ls = src.ctx->lv[level];
             if (phi)
-                TRY(copy_frames(dst.ctx, ld.phi[b], ls.phi[b], HW, t, t + 1, bytes));
+                TRY(copy_frames(dst, src, ld.phi[b], ls.phi[b], HW, t, t + 1, bytes));
             if (chg)
-                TRY(copy_frames(dst.ctx, ld.chg[b], ls.chg[b], HW, t, t + 1, bytes));
+                TRY(copy_frames(dst, src, ld.chg[b], ls.chg[b], HW, t, t + 1, bytes));
             if (d2)
-                TRY(copy_frames(dst.ctx, ld.d2[b], ls.d2[b], HW, t, t + 1, bytes));
+                TRY(copy_frames(dst, src, ld.d2[b], ls.d2[b], HW, t, t + 1, bytes));
         }
     }
-    return VI_OK;
+    return barrier(S);
 }
 
 // The channels of every slab's occluded voxels (the only voxels a vote or a
@@ -1469,26 +1504,30 @@ vi_status gather_holes(std::vector<Slab> &S, int level, bool all_dst, unsigned l
         const int off = src.hOff[level], n = src.hN[level];
         if (!n)
             continue;
+        CK(cudaSetDevice(src.dev));
         launch_pack_voxels(l.view(), l.holes + off, n, src.buf4 + off, src.buf1 + off, false, ctx->stream);
         CK_LAUNCH();
+    }
+    TRY(barrier(S));
+    for (Slab &src : S) {
+        const int off = src.hOff[level], n = src.hN[level];
+        if (!n)
+            continue;
+        const bool c5 = src.ctx->lv[level].x1 != nullptr;
         for (Slab &dst : S) {
             if (&dst == &src || (!all_dst && &dst != &S[0]))
                 continue;
-            vi_ctx *dctx = dst.ctx;
-            Level &ld = dctx->lv[level];
-            CK(cudaMemcpyAsync(dst.buf4 + off, src.buf4 + off, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice,
-                               dctx->stream));
-            bytes += sizeof(float4) * (size_t)n;
-            if (l.x1) {
-                CK(cudaMemcpyAsync(dst.buf1 + off, src.buf1 + off, sizeof(float) * (size_t)n,
-                                   cudaMemcpyDeviceToDevice, dctx->stream));
-                bytes += sizeof(float) * (size_t)n;
-            }
-            launch_pack_voxels(ld.view(), ld.holes + off, n, dst.buf4 + off, dst.buf1 + off, true, dctx->stream);
+            vi_ctx *ctx = dst.ctx;
+            Level &ld = ctx->lv[level];
+            TRY(copy_between(dst, src, dst.buf4 + off, src.buf4 + off, sizeof(float4) * (size_t)n, bytes));
+            if (c5)
+                TRY(copy_between(dst, src, dst.buf1 + off, src.buf1 + off, sizeof(float) * (size_t)n, bytes));
+            CK(cudaSetDevice(dst.dev));
+            launch_pack_voxels(ld.view(), ld.holes + off, n, dst.buf4 + off, dst.buf1 + off, true, ctx->stream);
             CK_LAUNCH();
         }
     }
-    return VI_OK;
+    return barrier(S);
 }
 
 // The search of one iteration (call) at a sharded level: rescore, n_pm
@@ -1500,6 +1539,7 @@ vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long
     for (Slab &r : S) {
         vi_ctx *ctx = r.ctx;
         Level &l = ctx->lv[level];
+        CK(cudaSetDevice(r.dev));
         launch_rescore(l.view(), l.targets + r.tOff[level], r.tN[level], l.phi[0], l.d2[0], nullptr, ctx->c5,
                        ctx->evals_dev, ctx->stream, rescore_lanes(ctx->cfg.lanes_per_target));
         CK_LAUNCH();
@@ -1509,9 +1549,11 @@ vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long
     for (int k = 1; k <= c0->cfg.n_pm; ++k)
         for (int j = 0; j < c0->cfg.sub_sweeps; ++j, ++s) {
             for (Slab &r : S) {
-                Level &l = r.ctx->lv[level];
-                TRY(step_launch(r.ctx, sweep_args(r.ctx, level, l.targets + r.tOff[level], r.tN[level], l.code,
-                                                  CODE_TARGET, nullptr, tag, k, j, s)));
+                vi_ctx *ctx = r.ctx;
+                Level &l = ctx->lv[level];
+                CK(cudaSetDevice(r.dev));
+                TRY(step_launch(ctx, sweep_args(ctx, level, l.targets + r.tOff[level], r.tN[level], l.code,
+                                                CODE_TARGET, nullptr, tag, k, j, s)));
             }
             TRY(exchange_halo(S, level, 1, (s + 1) & 1, true, true, false, bytes));
         }
@@ -1519,6 +1561,7 @@ vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long
         for (Slab &r : S) {
             vi_ctx *ctx = r.ctx;
             Level &l = ctx->lv[level];
+            CK(cudaSetDevice(r.dev));
             launch_copy_targets(l.targets + r.tOff[level], r.tN[level], l.phi[1], l.d2[1], l.phi[0], l.d2[0],
                                 ctx->stream);
             CK_LAUNCH();
@@ -1531,22 +1574,23 @@ vi_status slab_ann(std::vector<Slab> &S, int level, int call, unsigned long long
 vi_status slab_vote(std::vector<Slab> &S, int level, float *e, unsigned long long &bytes)
 {
     const Phase ph("slab vote L%d", level);
-    for (Slab &r : S)
-        TRY(vote_range(r.ctx, level, r.hOff[level], r.hN[level]));
+    for (Slab &r : S) {
+        vi_ctx *ctx = r.ctx;
+        CK(cudaSetDevice(r.dev));
+        TRY(vote_range(ctx, level, r.hOff[level], r.hN[level]));
+    }
     vi_ctx *ctx = S[0].ctx;
     if (e) {
-        for (size_t i = 1; i < S.size(); ++i) {
-            const size_t n = (size_t)S[i].hN[level] * sizeof(float);
-            if (n) {
-                CK(cudaMemcpyAsync(ctx->partials + S[i].hOff[level], S[i].ctx->partials + S[i].hOff[level], n,
-                                   cudaMemcpyDeviceToDevice, ctx->stream));
-                bytes += n;
-            }
-        }
+        TRY(barrier(S));
+        for (size_t i = 1; i < S.size(); ++i)
+            TRY(copy_between(S[0], S[i], ctx->partials + S[i].hOff[level], S[i].ctx->partials + S[i].hOff[level],
+                             (size_t)S[i].hN[level] * sizeof(float), bytes));
+        CK(cudaSetDevice(S[0].dev));
         TRY(sum_changes(ctx, level, ctx->scal));
     }
     TRY(gather_holes(S, level, true, bytes));
     if (e) {
+        CK(cudaSetDevice(S[0].dev));
         CK(cudaMemcpyAsync(ctx->host_scal, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         const int nH = ctx->lv[level].nH;
@@ -1561,6 +1605,7 @@ vi_status slab_next_level(std::vector<Slab> &S, int level, unsigned long long &b
     for (Slab &r : S) {
         vi_ctx *ctx = r.ctx;
         Level &c = ctx->lv[level + 1], &f = ctx->lv[level];
+        CK(cudaSetDevice(r.dev));
         launch_upsample_nnf(c.view(), c.phi[0], f.view(), false, f.targets + r.tOff[level], r.tN[level], f.sources,
                             f.nS, f.phi[0], (uint32_t)(ctx->cfg.seed & 0xFFFFFFFFull),
                             (uint32_t)(ctx->cfg.seed >> 32), make_tag(PURPOSE_UPSAMPLE, level, 0), ctx->cfg.clip,
@@ -1574,6 +1619,7 @@ vi_status slab_next_level(std::vector<Slab> &S, int level, unsigned long long &b
     for (Slab &r : S) {
         vi_ctx *ctx = r.ctx;
         Level &f = ctx->lv[level];
+        CK(cudaSetDevice(r.dev));
         launch_rescore(f.view(), f.targets + r.tOff[level], r.tN[level], f.phi[0], f.d2[0], nullptr, ctx->c5,
                        ctx->evals_dev, ctx->stream, rescore_lanes(ctx->cfg.lanes_per_target));
         CK_LAUNCH();
@@ -1587,6 +1633,7 @@ vi_status slab_next_level(std::vector<Slab> &S, int level, unsigned long long &b
 vi_status slab_ranges(std::vector<Slab> &S)
 {
     vi_ctx *ctx = S[0].ctx;
+    CK(cudaSetDevice(S[0].dev));
     for (Slab &r : S) {
         r.tOff.assign(ctx->L, 0);
         r.tN.assign(ctx->L, 0);
@@ -1621,17 +1668,20 @@ vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask,
 {
     const int n = (int)S.size();
     for (Slab &r : S) {
-        TRY(vi_upload(r.ctx, rgb, mask, W, H, T, ptr_is_device));
+        vi_ctx *ctx = r.ctx;
+        CK(cudaSetDevice(r.dev));
+        TRY(vi_upload(ctx, rgb, mask, W, H, T, ptr_is_device));
         // pyramid, initialisation and onion peel, then the coarsest level's
         // iterations: the same on every context
-        TRY(vi_prepare(r.ctx));
-        TRY(vi_iterate(r.ctx, r.ctx->L - 1, -1, 0, nullptr, nullptr));
+        TRY(vi_prepare(ctx));
+        TRY(vi_iterate(ctx, ctx->L - 1, -1, 0, nullptr, nullptr));
     }
     vi_ctx *ctx = S[0].ctx;
     const int L = ctx->L;
     std::vector<unsigned long long> before((size_t)n, 0);
     for (int i = 1; i < n; ++i) {
         vi_stats st;
+        CK(cudaSetDevice(S[i].dev));
         TRY(vi_get_stats(S[i].ctx, &st));
         before[(size_t)i] = st.evals;
     }
@@ -1641,6 +1691,7 @@ vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask,
         max_h = std::max(max_h, ctx->lv[l].nH);
     for (Slab &r : S) {
         vi_ctx *rc = r.ctx;
+        CK(cudaSetDevice(r.dev));
         TRY(dalloc(rc, &r.buf4, sizeof(float4) * (size_t)max_h));
         TRY(dalloc(rc, &r.buf1, sizeof(float) * (size_t)max_h));
     }
@@ -1657,20 +1708,24 @@ vi_status run_slabs(std::vector<Slab> &S, const float *rgb, const uint8_t *mask,
             ctx->outer[l] += k;
     }
     if (L == 1) {
+        CK(cudaSetDevice(S[0].dev));
         TRY(vi_final(ctx));
     } else {
         for (Slab &r : S) {
             Level &l = r.ctx->lv[0];
+            CK(cudaSetDevice(r.dev));
             launch_final(l.view(), l.holes + r.hOff[0], r.hN[0], l.phi[0], l.d2[0], r.ctx->c5, r.ctx->stream);
             CK_LAUNCH();
         }
         TRY(gather_holes(S, 0, false, bytes));
     }
+    CK(cudaSetDevice(S[0].dev));
     TRY(vi_fetch_result(ctx, rgb_out, ptr_is_device));
     if (stats_out) {
         TRY(vi_get_stats(ctx, stats_out));
         for (int i = 1; i < n; ++i) {
             vi_stats st;
+            CK(cudaSetDevice(S[i].dev));
             TRY(vi_get_stats(S[i].ctx, &st));
             stats_out->evals += st.evals - before[(size_t)i];
         }
@@ -1686,7 +1741,7 @@ const char *vi_slabs_last_error(void) { return g_slab_err.c_str(); }
 
 vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *mask, int W, int H, int T,
                        int ptr_is_device, int n_slabs, float *rgb_out, vi_stats *stats_out,
-                       unsigned long long *exchanged_bytes, void *cuda_stream)
+                       unsigned long long *exchanged_bytes, void *cuda_stream, const int *devices)
 {
     g_slab_err.clear();
     vi_config c;
@@ -1695,9 +1750,20 @@ vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *ma
     else
         vi_config_default(&c);
     if (!rgb || !mask || !rgb_out || n_slabs < 1 || n_slabs > 16 || T < n_slabs || c.storage != 0 ||
-        c.time_subsample != 0) {
+        c.time_subsample != 0 || (devices && cuda_stream)) {
         g_slab_err = "vi_run_slabs: bad arguments (1 <= n_slabs <= min(16, T); FP32 storage; no temporal "
-                     "subsampling)";
+                     "subsampling; a stream only without devices)";
+        return VI_ERR_ARG;
+    }
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        g_slab_err = "vi_run_slabs: no CUDA device";
+        return VI_ERR_NO_DEVICE;
+    }
+    if (devices && ptr_is_device && devices[0] != cur) {
+        // context 0 writes the result into rgb_out, which is on this device
+        g_slab_err = "vi_run_slabs: with device buffers the first slab must be on the current device";
         return VI_ERR_ARG;
     }
     std::vector<Slab> S;
@@ -1706,17 +1772,35 @@ vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *ma
     try {
         S.resize((size_t)n_slabs);
         for (int r = 0; r < n_slabs && st == VI_OK; ++r) {
-            S[(size_t)r].t0 = (int)((long long)r * T / n_slabs);
-            S[(size_t)r].t1 = (int)((long long)(r + 1) * T / n_slabs);
-            // all contexts share one stream: the caller's, else context 0's own
-            st = vi_ctx_create(&c, r ? (void *)S[0].ctx->stream : cuda_stream, &S[(size_t)r].ctx);
+            Slab &sl = S[(size_t)r];
+            sl.t0 = (int)((long long)r * T / n_slabs);
+            sl.t1 = (int)((long long)(r + 1) * T / n_slabs);
+            sl.dev = devices ? devices[r] : cur;
+            if (cudaSetDevice(sl.dev) != cudaSuccess) {
+                cudaGetLastError();
+                st = VI_ERR_ARG;
+                g_slab_err = "vi_run_slabs: bad device " + std::to_string(sl.dev);
+                break;
+            }
+            if (devices) {
+                // a stream (and an event) of its own on its device
+                st = vi_ctx_create(&c, nullptr, &sl.ctx);
+                if (st == VI_OK && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    sl.ev = nullptr;
+                    st = VI_ERR_CUDA;
+                }
+            } else {
+                // all contexts share one stream: the caller's, else context 0's own
+                st = vi_ctx_create(&c, r ? (void *)S[0].ctx->stream : cuda_stream, &sl.ctx);
+            }
         }
         if (st == VI_OK)
             st = run_slabs(S, rgb, mask, W, H, T, ptr_is_device, rgb_out, stats_out, bytes);
     } catch (...) {
         st = VI_ERR_OOM;
     }
-    if (st != VI_OK) {
+    if (st != VI_OK && g_slab_err.empty()) {
         for (const Slab &r : S)
             if (r.ctx && !r.ctx->err.empty()) {
                 g_slab_err = r.ctx->err;
@@ -1725,13 +1809,25 @@ vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *ma
     }
     if (exchanged_bytes)
         *exchanged_bytes = bytes;
+    // every stream drained before any context's memory goes (another
+    // context's stream may still read it)
+    for (Slab &r : S)
+        if (r.ctx && cudaSetDevice(r.dev) == cudaSuccess)
+            cudaStreamSynchronize(r.ctx->stream);
     for (size_t r = S.size(); r-- > 0;) {
-        if (S[r].ctx) {
-            dfree(S[r].ctx, S[r].buf4);
-            dfree(S[r].ctx, S[r].buf1);
+        Slab &sl = S[r];
+        if (cudaSetDevice(sl.dev) != cudaSuccess)
+            continue;
+        if (sl.ctx) {
+            dfree(sl.ctx, sl.buf4);
+            dfree(sl.ctx, sl.buf1);
         }
-        vi_ctx_destroy(S[r].ctx);   // context 0 (the stream's owner) last
+        vi_ctx_destroy(sl.ctx);   // context 0 (the shared stream's owner) last
+        if (sl.ev)
+            cudaEventDestroy(sl.ev);
     }
+    cudaGetLastError();
+    cudaSetDevice(cur);
     return st;
 }
 

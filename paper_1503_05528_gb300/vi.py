@@ -145,7 +145,7 @@ def _declare(L):
     L.vi_save_state.argtypes = [vp, i, vp, C.c_size_t]
     L.vi_load_state.argtypes = [vp, i, vp, C.c_size_t]
     L.vi_resume.argtypes = [vp, i, i]
-    L.vi_run_slabs.argtypes = [P(ViConfig), vp, vp, i, i, i, i, i, vp, P(ViStats), P(C.c_ulonglong), vp]
+    L.vi_run_slabs.argtypes = [P(ViConfig), vp, vp, i, i, i, i, i, vp, P(ViStats), P(C.c_ulonglong), vp, P(i)]
     L.vi_slabs_last_error.argtypes = []
     L.vi_slabs_last_error.restype = C.c_char_p
     ull = C.c_ulonglong
@@ -641,10 +641,11 @@ def auto_levels(mask):
     return load().vi_auto_levels(mask.ctypes.data, W, H, T)
 
 
-def run_slabs(rgb, mask, n_slabs, out=None, stream=None, **cfg):
+def run_slabs(rgb, mask, n_slabs, out=None, stream=None, devices=None, **cfg):
     """The whole inpainting with the finer levels split by frames over
-    n_slabs contexts (vi_run_slabs). Returns (result, stats dict, bytes
-    exchanged between the contexts)."""
+    n_slabs contexts (vi_run_slabs): on one shared stream, or with devices
+    (one device index per slab) on a stream of its own each. Returns (result,
+    stats dict, bytes exchanged between the contexts)."""
     lib = load()
     if isinstance(rgb, np.ndarray):
         rgb = np.ascontiguousarray(rgb, np.float32)
@@ -659,8 +660,13 @@ def run_slabs(rgb, mask, n_slabs, out=None, stream=None, **cfg):
     cfgs = default_config(**cfg)
     st = ViStats()
     nbytes = C.c_ulonglong(0)
+    devs = None
+    if devices is not None:
+        if len(devices) != int(n_slabs):
+            raise ValueError("one device per slab")
+        devs = (C.c_int * len(devices))(*[int(d) for d in devices])
     r = lib.vi_run_slabs(C.byref(cfgs), pr, pm, W, H, T, dev, int(n_slabs), po, C.byref(st), C.byref(nbytes),
-                         C.c_void_p(stream) if stream else None)
+                         C.c_void_p(stream) if stream else None, devs)
     if r != VI_OK:
         raise ViError(r, "vi_run_slabs: " + (lib.vi_slabs_last_error() or b"").decode(errors="replace"))
     return out, _stats_dict(st), nbytes.value

@@ -102,5 +102,6 @@ def test_slabs_argument_errors_need_no_gpu(lib):
     out = np.empty_like(rgb)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
     for n in (0, 5, 17):   # n_slabs outside 1 .. min(16, T)
-        assert lib.vi_run_slabs(ctypes.byref(cfg), p(rgb), p(mask), 8, 8, 4, 0, n, p(out), None, None, None) == 1
+        assert lib.vi_run_slabs(ctypes.byref(cfg), p(rgb), p(mask), 8, 8, 4, 0, n, p(out), None, None, None,
+                                None) == 1
     assert b"n_slabs" in lib.vi_slabs_last_error()

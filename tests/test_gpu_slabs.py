@@ -3,8 +3,9 @@ coarsest split by frames over several contexts, with the boundary frames
 copied between them, is identical to vi_run: the output bit for bit, the
 iteration counts per level and the evaluation count. Covers one slab, even
 and uneven splits, slabs of a single frame (a two-frame halo then spans
-several slabs), the multi-radius search with propagation sub-sweeps, device
-buffers, and the argument checks."""
+several slabs), the multi-radius search with propagation sub-sweeps, a
+stream per slab ordered by events (the multi-device form, here with every
+slab on this GPU), device buffers, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -30,9 +31,9 @@ def _alone(c, **cfg):
         return ctx.fetch_result(), ctx.stats()
 
 
-def _check(c, n, **cfg):
+def _check(c, n, devices=None, **cfg):
     want, ws = _alone(c, **cfg)
-    got, gs, nbytes = vi.run_slabs(c.rgb, c.mask, n, **cfg)
+    got, gs, nbytes = vi.run_slabs(c.rgb, c.mask, n, devices=devices, **cfg)
     assert (got.view(np.uint32) == want.view(np.uint32)).all()
     assert gs["outer"] == ws["outer"]
     assert gs["evals"] == ws["evals"]
@@ -58,6 +59,17 @@ def test_uneven_split_and_search_options():
     _check(c, 5, levels=2, seed=94, lanes_per_target=32)
 
 
+@pytest.mark.parametrize("n", [2, 3, 14])
+def test_a_stream_per_slab(n):
+    # the multi-device form (a context, stream and event per slab, peer
+    # copies ordered by events) with every slab on this GPU: the same result,
+    # and the same bytes exchanged as on one shared stream
+    c = synth.small_layered(W=72, H=56, T=14, levels=2, seed=1706)
+    nb = _check(c, n, devices=[0] * n, levels=2, seed=96, clip=1)
+    _, _, nb1 = vi.run_slabs(c.rgb, c.mask, n, levels=2, seed=96, clip=1)
+    assert nb == nb1
+
+
 def test_device_buffers():
     c = synth.small_layered(W=72, H=56, T=14, levels=2, seed=1704)
     want, _ = _alone(c, levels=2, seed=95)
@@ -71,6 +83,7 @@ def test_device_buffers():
 
 def test_bad_arguments():
     c = synth.small_layered(W=48, H=40, T=6, levels=1, seed=1705)
-    for n, cfg in [(0, {}), (7, {}), (17, {}), (2, {"storage": 1}), (2, {"time_subsample": 1})]:
+    for n, cfg in [(0, {}), (7, {}), (17, {}), (2, {"storage": 1}), (2, {"time_subsample": 1}),
+                   (2, {"devices": [0, 999]})]:
         with pytest.raises(vi.ViError):
             vi.run_slabs(c.rgb, c.mask, n, levels=1, **cfg)
