@@ -142,3 +142,21 @@ def test_iteration_cap_counts_from_call_zero():
     prm = O.Params(seed=5, stop=0.0, max_outer=4)      # stop 0: only the cap ends the loop
     assert O.iterate_level(lv, prm, 0, start_call=2) == 2
     assert O.iterate_level(lv, prm, 0, start_call=4) == 0
+
+
+def test_white_noise_hole_is_filled_smoother_than_the_noise():
+    # The toy example of Appendix B (Fig. 11): in i.i.d. noise no source patch
+    # is much closer than another, so the weighted mean of Eq. 4 averages many
+    # unrelated noise samples and the hole comes out smoother than the noise
+    # around it; the best-patch step (Eq. 6) copies single noise voxels back.
+    rng = np.random.default_rng(21)
+    T, H, W = 8, 28, 28
+    rgb = np.clip(0.5 + 0.1 * rng.standard_normal((T, H, W, 3)), 0.0, 1.0).astype(np.float32)
+    mask = np.zeros((T, H, W), np.uint8)
+    mask[2:6, 10:18, 10:18] = 1
+    prm = O.Params(seed=4, fixed_outer=[6])
+    out, pyr, before = O.inpaint(rgb, mask, 1, use_texture=False, prm=prm, return_levels=True)
+    h = mask == 1
+    noise = rgb[~h].std()
+    assert before[h][:, :3].std() < 0.6 * noise
+    assert out[h].std() > 0.8 * noise     # Eq. 6 copies noise voxels
