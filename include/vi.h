@@ -4,8 +4,9 @@
  * The library runs the per-pyramid-level hot path of the global patch-based
  * video inpainting method of Newson, Almansa, Fradet, Gousseau and Perez,
  * "Video Inpainting of Complex Scenes" (SIAM J. Imaging Sciences 7(4), 2014;
- * arXiv:1503.05528), Algorithm 4 without the affine realignment of
- * Algorithm 2: pyramids and texture features (Sec. 3.3, Eq. 7, Eq. 8), shift-
+ * arXiv:1503.05528), Algorithm 4 (the affine realignment of Algorithm 2,
+ * Sec. 3.4, is a separate set of calls around it): pyramids and texture
+ * features (Sec. 3.3, Eq. 7, Eq. 8), shift-
  * map initialisation, onion-peel initialisation (Sec. 3.5, Algorithm 3),
  * spatio-temporal PatchMatch (Sec. 3.1, Algorithm 1, Eq. 2, Eq. 3, Eq. 7b),
  * weighted reconstruction (Sec. 3.2, Eq. 4, Eq. 5, Eq. 9), level transition
@@ -53,11 +54,12 @@ typedef enum {
     VI_ERR_ARG = 1,        /* invalid argument (null pointer, size, level, config) */
     VI_ERR_OOM = 2,        /* device or host allocation failed */
     VI_ERR_CUDA = 3,       /* a CUDA call failed; vi_last_error() has the text */
-    VI_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+    VI_ERR_TIMEOUT = 4,    /* a bounded wait gave up (reserved: no call waits on the device) */
     VI_ERR_NO_SOURCE = 5,  /* D~ is empty at some level: nothing to copy from */
     VI_ERR_STATE = 6,      /* call out of order (e.g. iterate before upload) */
     VI_ERR_NO_DEVICE = 7,  /* no CUDA device is available */
-    VI_ERR_TOO_LARGE = 8   /* input larger than the fixed maximum of vi_energy_noalloc */
+    VI_ERR_TOO_LARGE = 8   /* input larger than a fixed maximum: vi_energy_noalloc's
+                              voxel count, a server's HBM budget */
 } vi_status;
 
 /* Parameters of the method (Sec. 3.7 gives the paper's values). */
