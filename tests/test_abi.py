@@ -105,3 +105,20 @@ def test_slabs_argument_errors_need_no_gpu(lib):
         assert lib.vi_run_slabs(ctypes.byref(cfg), p(rgb), p(mask), 8, 8, 4, 0, n, p(out), None, None, None,
                                 None) == 1
     assert b"n_slabs" in lib.vi_slabs_last_error()
+
+
+def test_tune_table_text_needs_no_gpu(lib):
+    # the lanes table's text form is host logic: lines "device family c5 fp16
+    # bucket lanes" are read, listed back in key order and validated (the
+    # warp-shared lane code 32 only for the step families)
+    before = vi.tune_export()
+    try:
+        vi.tune_import("5 0 1 0 40 32\n5 1 1 0 41 32\n5 2 1 0 42 4\n5 3 0 1 43 8\n")
+        rows = [tuple(int(v) for v in ln.split()) for ln in vi.tune_export().splitlines()]
+        for r in [(5, 0, 1, 0, 40, 32), (5, 1, 1, 0, 41, 32), (5, 2, 1, 0, 42, 4), (5, 3, 0, 1, 43, 8)]:
+            assert r in rows
+        for bad in ["5 2 1 0 44 32", "5 0 1 0 45 3", "5 4 1 0 46 1", "64 0 1 0 47 1", "5 0 2 0 48 1", "x"]:
+            with pytest.raises(vi.ViError):
+                vi.tune_import(bad + "\\n")
+    finally:
+        vi.tune_import(before)   # (entries added above stay; they name device 5)
