@@ -51,3 +51,20 @@ def test_replicas_are_independent_clips_of_the_same_size():
     assert a.rgb.shape == b.rgb.shape and a.levels == b.levels
     assert not np.array_equal(a.rgb, b.rgb)
     assert abs(a.mask.mean() - b.mask.mean()) < 0.01
+
+
+def test_clock_summary_from_nvidia_smi_samples():
+    # the clocks object of the JSON line: median SM clock, the maximum, and
+    # every throttle reason active in any sample ("Not Active" is not)
+    text = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.summarise_clocks(text)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = text + "\n0, 1500, 2070, 1400.0, 0x48, Active, Not Active, Active, Not Active"
+    assert bench.summarise_clocks(hot)["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.summarise_clocks("") is None
