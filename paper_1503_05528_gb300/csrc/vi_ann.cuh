@@ -458,12 +458,12 @@ __device__ __forceinline__ void warp_d2_multi(const LevelView &L, unsigned M0, u
 // ann_one for the targets of a warp with warp-shared lanes: the whole warp
 // calls it, and lane l owns target i of the clip a describes when active (a
 // is only read when active; with MIXED the lanes may belong to different
-// clips of a batch). The propagation candidates of all targets are gathered
-// together and decided in order (single clip; see below) or judged one
-// neighbour at a time (batch); then each random-search stage
-// offers at most one candidate per target, judged against the running best
-// as in ann_one. The warp leaves the stage loop together, when no lane has a
-// stage left.
+// clips of a batch). A single clip gathers the propagation candidates of all
+// its targets together and decides them in order (see below); a batch
+// judges them one neighbour at a time. Then each random-search stage offers
+// at most one candidate per target, judged against the running best as in
+// ann_one. The warp leaves a stage loop together, when no lane has a stage
+// left.
 template <bool C5, bool F16, bool MIXED>
 __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int i, int k, int span, StepCount &n)
 {
