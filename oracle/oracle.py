@@ -512,6 +512,16 @@ def iterate_level(lv, prm, level_index, n_outer=None, start_call=0):
     return k
 
 
+def provisional_fill(coarse_x, fine_x, fine_hole, tsub=False):
+    """The first half of the level transition (Sec. 3.6): every occluded voxel
+    (x, y, t) of the finer level takes, in place, the value of its coarse
+    parent (x // 2, y // 2, t), or (x // 2, y // 2, t // 2) with temporal
+    subsampling, so that the distances of Eq. 5 have a video to compare."""
+    tt, yy, xx = np.nonzero(fine_hole)
+    fine_x[tt, yy, xx] = coarse_x[tt // 2 if tsub else tt, yy // 2, xx // 2]
+    return fine_x
+
+
 def next_level(coarse, fine, prm, fine_index):
     """Level transition of Algorithm 4: phi^{l-1} = UpSample(phi^l, 2); the
     finer occluded voxels first take their coarse parent's value (the
@@ -520,9 +530,7 @@ def next_level(coarse, fine, prm, fine_index):
     fine.phi = upsample_nnf(coarse.phi, fine.htilde, fine.dtilde, prm.key,
                             tag(PURPOSE_UPSAMPLE, fine_index), prm.clip, prm.time_subsample)
     fine.d2 = np.full(fine.hole.shape, np.inf, np.float32)
-    T, Hf, Wf, _ = fine.x.shape
-    tt, yy, xx = np.nonzero(fine.hole)
-    fine.x[tt, yy, xx] = coarse.x[tt // 2 if prm.time_subsample else tt, yy // 2, xx // 2]
+    provisional_fill(coarse.x, fine.x, fine.hole, prm.time_subsample)
     ev = _rescore(fine, prm)
     fine.x, _ = vote(fine.x, fine.hole, fine.htilde, fine.phi, fine.d2,
                      weighted=prm.weighted, n_diff=3)
