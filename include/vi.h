@@ -270,7 +270,13 @@ vi_status vi_energy(vi_ctx *ctx, int level, double *E_H_host, double *E_Ht_host)
  * in the library's static device memory, held by every GPU that loads the
  * library until the process exits. The first call on each device looks that
  * array's device address up (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture. Every call shares the
+ * make that first call before any stream capture. The address is kept per
+ * device with the id of the CUDA context it was found in, and looked up again
+ * when the device's context has changed (after a cudaDeviceReset, which
+ * reloads the array: make the first call after a reset before any capture
+ * too). A target counts when its source patch lies inside the video, whether
+ * or not the source is in D~, exactly as in vi_energy: Eq. 1 is the energy of
+ * any shift map; a source patch leaving the video gives +inf. Every call shares the
  * array, so calls that overlap on the GPU race; calls ordered on one stream
  * do not (each reads back only what it has just written). Asynchronous: the
  * result is in out_dev once the stream reaches it. Errors: VI_ERR_ARG (null

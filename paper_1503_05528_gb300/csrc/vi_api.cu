@@ -1447,6 +1447,54 @@ vi_status barrier(std::vector<Slab> &S)
     return VI_OK;
 }
 
+// Slabs on distinct devices exchange through cudaMemcpyPeerAsync between
+// buffers of each device's default memory pool (the contexts allocate stream-
+// ordered). Peer access enabled with cudaDeviceEnablePeerAccess does not cover
+// pool memory: each pool must grant the other devices access itself. For every
+// ordered pair of distinct devices that can reach each other, peer access is
+// enabled and the owner's default pool grants the peer read/write access;
+// pairs that cannot reach each other keep the driver's staged copy.
+vi_status grant_peer_access(const std::vector<Slab> &S)
+{
+    std::vector<int> devs;
+    for (const Slab &r : S)
+        if (std::find(devs.begin(), devs.end(), r.dev) == devs.end())
+            devs.push_back(r.dev);
+    for (int owner : devs) {
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, owner) != cudaSuccess) {
+            g_slab_err = "vi_run_slabs: no default memory pool on device " + std::to_string(owner);
+            return VI_ERR_CUDA;
+        }
+        for (int peer : devs) {
+            if (peer == owner)
+                continue;
+            int can = 0;
+            if (cudaDeviceCanAccessPeer(&can, peer, owner) != cudaSuccess || !can) {
+                cudaGetLastError();
+                continue;
+            }
+            if (cudaSetDevice(peer) != cudaSuccess)
+                return VI_ERR_CUDA;
+            const cudaError_t e = cudaDeviceEnablePeerAccess(owner, 0);
+            if (e != cudaSuccess && e != cudaErrorPeerAccessAlreadyEnabled) {
+                g_slab_err = std::string("vi_run_slabs: peer access: ") + cudaGetErrorString(e);
+                return VI_ERR_CUDA;
+            }
+            cudaGetLastError();
+            cudaMemAccessDesc desc = {};
+            desc.location.type = cudaMemLocationTypeDevice;
+            desc.location.id = peer;
+            desc.flags = cudaMemAccessFlagsProtReadWrite;
+            if (cudaMemPoolSetAccess(pool, &desc, 1) != cudaSuccess) {
+                g_slab_err = "vi_run_slabs: pool access for device " + std::to_string(peer);
+                return VI_ERR_CUDA;
+            }
+        }
+    }
+    return VI_OK;
+}
+
 // n bytes at src (slab from's device) to dst (slab to's device), on to's stream.
 vi_status copy_between(Slab &to, Slab &from, void *dst, const void *src, size_t n, unsigned long long &bytes)
 {
@@ -1795,6 +1843,8 @@ vi_status vi_run_slabs(const vi_config *cfg, const float *rgb, const uint8_t *ma
                 st = vi_ctx_create(&c, r ? (void *)S[0].ctx->stream : cuda_stream, &sl.ctx);
             }
         }
+        if (st == VI_OK && devices)
+            st = grant_peer_access(S);
         if (st == VI_OK)
             st = run_slabs(S, rgb, mask, W, H, T, ptr_is_device, rgb_out, stats_out, bytes);
     } catch (...) {

@@ -16,6 +16,8 @@
 // shares the array, and a call reads back only the slots it has just written,
 // so nothing needs clearing between calls; two calls that overlap on the GPU
 // (on different streams, or from different threads) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "vi.h"
@@ -129,11 +131,56 @@ __global__ void k_energy_noalloc_sum(const double *__restrict__ scratch, int n_b
 
 namespace {
 
-// Device address of g_energy_scratch, looked up once per device. In host code
-// the symbol's name is only a host-side stand-in, never a device address.
+// Device address of g_energy_scratch. In host code the symbol's name is only a
+// host-side stand-in, never a device address, so the address is looked up with
+// cudaGetSymbolAddress while the device is current. The lookup is cached per
+// device together with the unique id of the CUDA context it was made in: if
+// the caller (or another library) resets the device, the next call finds a
+// new context, in which the library's module and its static array are loaded
+// anew, and looks the address up again instead of writing through the old one.
+// The context id comes from the driver's cuCtxGetCurrent / cuCtxGetId, reached
+// through the runtime's entry-point query so the library needs no link to
+// libcuda; with a driver that lacks them the address is looked up on every
+// call.
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    void *addr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 when there is none or
+// the driver cannot say).
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool queried = false;
+    if (!queried) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+        queried = true;
+    }
+    if (!get_current || !get_id)
+        return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 cudaError_t scratch_address(double **out)
 {
@@ -144,14 +191,18 @@ cudaError_t scratch_address(double **out)
     if (dev < 0 || dev >= kMaxDevices)
         return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    ScratchEntry &ent = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!ent.addr || id == 0 || ent.ctx_id != id) {
         void *p = nullptr;
+        // binds the device's primary context to this thread if none is
         e = cudaGetSymbolAddress(&p, vi::g_energy_scratch);
         if (e != cudaSuccess)
             return e;
-        g_scratch_addr[dev] = p;
+        ent.addr = p;
+        ent.ctx_id = current_ctx_id();
     }
-    *out = (double *)g_scratch_addr[dev];
+    *out = (double *)ent.addr;
     return cudaSuccess;
 }
 

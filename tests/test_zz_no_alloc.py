@@ -86,6 +86,80 @@ def test_noalloc_energy_matches_vi_energy_twice(tex, levels, seed):
                     assert got[1] == pytest.approx(eht, rel=1e-5)
 
 
+def _random_valid_map(code, rng):
+    """Every target of code points at a source patch of D~ drawn at random."""
+    T_, H_, W_ = code.shape
+    src = np.flatnonzero((code >> 2) & 1)
+    tgt = np.flatnonzero((code >> 1) & 1)
+    pick = src[rng.integers(0, len(src), len(tgt))]
+    ph = np.zeros((T_ * H_ * W_, 3), np.int32)
+    ph[tgt, 0] = pick % W_ - tgt % W_
+    ph[tgt, 1] = (pick // W_) % H_ - (tgt // W_) % H_
+    ph[tgt, 2] = pick // (W_ * H_) - tgt // (W_ * H_)
+    return ph, tgt
+
+
+def _both_energies(ctx, lib, stream):
+    eh, eht = ctx.energy(0)
+    info = ctx.level_info(0)
+    chans = torch.empty((info["T"], info["H"], info["W"], info["C"]), dtype=torch.float32, device="cuda")
+    ctx.get_channels(0, chans)
+    phi, _ = ctx.get_nnf(0)
+    phi_d = torch.from_numpy(phi).cuda()
+    code_d = torch.from_numpy(ctx.get_masks(0)).cuda()
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    got = []
+    for _ in range(2):   # two calls in a row share the static scratch
+        out.fill_(-1.0)
+        torch.cuda.synchronize()
+        assert _noalloc(lib, chans, phi_d, code_d, out, stream) == 0
+        torch.cuda.synchronize()
+        got.append(out.cpu().numpy().copy())
+    return (eh, eht), got
+
+
+def test_noalloc_energy_many_blocks_and_sources_outside_d_tilde():
+    # 320 x 240 x 40 = 3,072,000 voxels: 12,000 blocks of partial sums, so the
+    # final reduction takes many strided passes over the static array
+    clip = synth.fast_layered_clip(320, 240, 40, 0.08, seed=1533)
+    lib = vi.load()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(12)
+    with vi.Context(levels=1, use_texture=1, seed=5) as ctx:
+        ctx.upload(clip.rgb, clip.mask)
+        ctx.build_pyramid()
+        code = ctx.get_masks(0)
+        T_, H_, W_ = code.shape
+        ph, tgt = _random_valid_map(code, rng)
+        # some targets point at a whole patch that is not in D~ (it meets the
+        # hole): both energies count it, as Eq. 1 counts any shift
+        hole = np.flatnonzero(code & 1)
+        inner = hole[((hole % W_) >= 2) & ((hole % W_) < W_ - 2) & (((hole // W_) % H_) >= 2) &
+                     (((hole // W_) % H_) < H_ - 2) & ((hole // (W_ * H_)) >= 2) &
+                     ((hole // (W_ * H_)) < T_ - 2)]
+        assert len(inner) > 1000
+        some = tgt[rng.integers(0, len(tgt), 500)]
+        src = inner[rng.integers(0, len(inner), 500)]
+        ph[some, 0] = src % W_ - some % W_
+        ph[some, 1] = (src // W_) % H_ - (some // W_) % H_
+        ph[some, 2] = src // (W_ * H_) - some // (W_ * H_)
+        ctx.set_nnf(0, ph.reshape(T_, H_, W_, 3), None)
+        (eh, eht), got = _both_energies(ctx, lib, stream)
+        assert np.isfinite(eh) and np.isfinite(eht) and eh > 0
+        for g in got:
+            assert g[0] == pytest.approx(eh, rel=1e-5)
+            assert g[1] == pytest.approx(eht, rel=1e-5)
+        # one target whose source patch leaves the video (centre x = W - 2):
+        # +inf in both, in E_H~ and, for an occluded target, in E_H
+        p = hole[len(hole) // 2]
+        ph[p, 0] = (W_ - 2) - p % W_
+        ctx.set_nnf(0, ph.reshape(T_, H_, W_, 3), None)
+        (eh, eht), got = _both_energies(ctx, lib, stream)
+        assert eh == np.inf and eht == np.inf
+        for g in got:
+            assert g[0] == np.inf and g[1] == np.inf
+
+
 def test_noalloc_rejects_sizes_beyond_its_maximum():
     lib = vi.load()
     dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
