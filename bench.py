@@ -483,7 +483,8 @@ def run_batch(args):
     n_vox = sum(int(c.mask.size) for c in clips)
     stream = torch.cuda.current_stream()
     storage = 1 if args.storage == "fp16" else 0
-    b = vi.Batch(stream=stream.cuda_stream, levels=0, lanes_per_target=args.lanes, storage=storage)
+    b = vi.Batch(stream=stream.cuda_stream, levels=0, lanes_per_target=args.lanes, storage=storage,
+                 sub_sweeps=args.sub_sweeps)
 
     def step():
         ids = [b.add(r, m, levels=0, seed=1503 + i, clip=i) for i, (r, m) in enumerate(dev)]
@@ -535,7 +536,7 @@ def run_batch(args):
     single_evals = 0
     for i, (r, m) in enumerate(dev):
         with vi.Context(levels=0, seed=1503 + i, clip=i, stream=stream.cuda_stream,
-                        lanes_per_target=args.lanes, storage=storage) as ctx:
+                        lanes_per_target=args.lanes, storage=storage, sub_sweeps=args.sub_sweeps) as ctx:
             ctx.upload(r, m)
             ctx.run()
             ctx.fetch_result(outs[i])
