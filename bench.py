@@ -854,7 +854,8 @@ def main():
                     help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
     ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],
                     help="random search: one radius per iteration (Eq. 3) or every radius")
-    ap.add_argument("--sub-sweeps", type=int, default=1, help="propagation sweeps per iteration")
+    ap.add_argument("--sub-sweeps", type=int, default=2,
+                    help="propagation sweeps per iteration (2, the library's default)")
     ap.add_argument("--realign", action="store_true",
                     help="AlignVideo (Sec. 3.4) before and UnwarpVideo after every inpainting")
     ap.add_argument("--tune-save", default=None, help="write the lanes autotuning table after warm-up")

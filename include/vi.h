@@ -101,9 +101,14 @@ typedef struct {
                             k, each around the best shift so far (Sec. 3.1
                             discusses both) */
     int sub_sweeps;      /* propagation sweeps per PatchMatch iteration, the
-                            last one followed by the random search (1, the
-                            paper's; more spread a good shift further per
-                            parallel iteration); 1..16; batches need 1 */
+                            last one followed by the random search; 1..16.
+                            Default 2: a parallel (Jacobi) sweep spreads a
+                            good shift one voxel where the paper's sequential
+                            scan spreads it along the scan, and two sweeps per
+                            iteration bring the energy of Eq. 1 within 2% of
+                            the sequential search's (one, the paper's count,
+                            leaves it about 4% above). A batch's clips share
+                            the batch's value. */
     int time_subsample;  /* 0: pyramid levels keep every frame (Sec. 3.6); 1: the
                             option the paper uses once for long occlusions:
                             every level also halves the frames (2x2x2 means,
@@ -193,6 +198,27 @@ vi_status vi_init_nnf(vi_ctx *ctx, int level);
  * after an ANN search with the partial distance of Eq. 11.
  * Synchronises the stream once per layer. Errors: VI_ERR_STATE, VI_ERR_CUDA. */
 vi_status vi_onion_peel(vi_ctx *ctx);
+
+/* One layer of the onion-peel initialisation (Sec. 3.5, Algorithm 3,
+ * Eq. 10-12) at the coarsest level, for checking the layers one by one on
+ * injected state. With H' the voxels still to fill:
+ *   dH' = H' minus its 3x3x3 erosion (voxels outside the video count as
+ *         outside H');
+ *   targets = voxels outside H' whose 5x5x5 patch meets dH';
+ *   the ANN search of vi_ann on those targets with the partial distance of
+ *   Eq. 11 (target voxels in H' left out, the sum divided by the count kept;
+ *   +inf when none is), random draws tagged with `layer`;
+ *   the vote of Eq. 12 of every voxel of dH' from the targets of its patch;
+ *   a voxel of dH' that no target reaches stays in H'.
+ * The channels, shift map and distances are the level's (vi_set_channels /
+ * vi_set_nnf inject them). hprime_in: host uint8 [T][H][W] of the coarsest
+ * level, nonzero = in H' (copied); NULL continues from the H' the previous
+ * call left, or from the occluded set when no layer has run since the
+ * pyramid was built. hprime_out (host, nullable) receives H' after the layer
+ * (1 = still to fill); *n_left (nullable) its size. Synchronises. Errors:
+ * VI_ERR_STATE (no pyramid), VI_ERR_ARG (layer outside [0, 65535]),
+ * VI_ERR_CUDA. */
+vi_status vi_onion_layer(vi_ctx *ctx, int layer, const uint8_t *hprime_in, uint8_t *hprime_out, int *n_left);
 
 /* vi_build_pyramid + vi_init_nnf(levels-1) + vi_onion_peel. */
 vi_status vi_prepare(vi_ctx *ctx);
@@ -307,6 +333,15 @@ vi_status vi_get_masks(vi_ctx *ctx, int level, uint8_t *code_host);
  * pairs given as int32 [n][6] = (px, py, pt, sx, sy, st) in host memory;
  * +inf where the source patch leaves the video. out_host: float32 [n]. */
 vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n, float *out_host);
+
+/* The partial distance of Eq. 11 (Sec. 3.5) for the same pairs: target voxels
+ * r with excl_host[r] != 0 (host uint8 [T][H][W] of the level, e.g. H' of the
+ * onion peel) and target voxels outside the video are left out, and the sum
+ * is divided by the number kept; +inf when none is kept or the source patch
+ * leaves the video. Computed by the function the onion peel's search uses.
+ * excl_host NULL gives vi_patch_dist. */
+vi_status vi_patch_dist_partial(vi_ctx *ctx, int level, const int32_t *pairs_host, int n,
+                                const uint8_t *excl_host, float *out_host);
 
 /* The inpainted video (level-0 colour), float32 [T][H][W][3]. Known voxels
  * are the input values. Synchronises when out is host memory. */
@@ -551,6 +586,17 @@ vi_status vi_batch_remove(vi_batch *b, int id);
 
 /* A clip's counters (as vi_get_stats). */
 vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out);
+
+/* The context behind a clip of the batch, for inspecting and injecting its
+ * state between rounds with the single-clip calls (vi_level_info,
+ * vi_get/set_channels, vi_get/set_nnf, vi_get_masks at the level vi_batch_poll
+ * reports), e.g. to compare one batch round with the oracle's search and vote
+ * on the same state. *call_out (nullable) receives the clip's iteration index
+ * at its level: its next round is Algorithm 4's iteration `call` there (the
+ * Philox tag of its random search). The batch keeps ownership: the handle is
+ * valid until the clip is removed, and must not be destroyed, uploaded to or
+ * run through vi_run. Errors: VI_ERR_ARG (unknown clip). */
+vi_status vi_batch_clip_ctx(vi_batch *b, int id, vi_ctx **ctx_out, int *call_out);
 
 /* Batch counters: patch-distance evaluations (batch launches plus the own
  * launches of every clip added so far, removed ones included), source voxels

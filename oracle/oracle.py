@@ -441,27 +441,36 @@ def _rescore(lv, prm, excl=None, target=None):
                n_pm=0, schedule=prm.schedule, rho=prm.rho, key=prm.key, excl=excl)
 
 
+def onion_layer(lv, prm, level_index, n_layer, Hp):
+    """One layer of Algorithm 3 on H' = Hp (uint8): dH' = H' minus its 3x3x3
+    erosion; the ANN search (Algorithm 1, partial distance of Eq. 11, random
+    draws tagged with the layer) for the patches that meet dH' and are centred
+    outside H'; the vote of dH' with Eq. 12 from those patches only. Updates
+    lv.x, lv.phi and lv.d2 in place and returns (new H', evaluations): the
+    erosion of H' plus the layer voxels that no such patch covers."""
+    eroded = erode3(Hp)
+    layer = Hp & (1 - eroded)
+    targets = dilate5(layer) & (1 - Hp)
+    evals = ann(lv.x, targets, lv.dtilde, lv.phi, lv.d2, n_pm=prm.n_pm,
+                schedule=prm.schedule, rho=prm.rho, key=prm.key,
+                tag_base=tag(PURPOSE_ONION, level_index, n_layer), clip=prm.clip, excl=Hp,
+                rs_mode=prm.rs_mode, sub_sweeps=prm.sub_sweeps)
+    x_new, _, deferred = vote(lv.x, layer, targets, lv.phi, lv.d2, weighted=prm.weighted,
+                              n_diff=0, want_deferred=True)
+    lv.x = x_new
+    return (eroded | (layer & deferred)).astype(np.uint8), evals
+
+
 def onion_peel(lv, prm, level_index):
-    """Algorithm 3 at the coarsest level. Layer by layer: dH' = H' minus its
-    3x3x3 erosion; ANN (Algorithm 1, partial distance Eq. 11) for the patches
-    that meet dH' and are centred outside H'; vote of dH' with Eq. 12 from those
-    patches only; H' <- Erosion(H'). A layer voxel that no such patch covers is
-    kept in H' for the next layer."""
+    """Algorithm 3 at the coarsest level: onion_layer until H' is empty,
+    starting from H' = H. A layer voxel that no patch centred outside H'
+    covers is kept in H' for the next layer."""
     Hp = lv.hole.copy()
     n_layer = 0
     evals = 0
     while Hp.any():
-        eroded = erode3(Hp)
-        layer = Hp & (1 - eroded)
-        targets = dilate5(layer) & (1 - Hp)
-        evals += ann(lv.x, targets, lv.dtilde, lv.phi, lv.d2, n_pm=prm.n_pm,
-                     schedule=prm.schedule, rho=prm.rho, key=prm.key,
-                     tag_base=tag(PURPOSE_ONION, level_index, n_layer), clip=prm.clip, excl=Hp,
-                     rs_mode=prm.rs_mode, sub_sweeps=prm.sub_sweeps)
-        x_new, _, deferred = vote(lv.x, layer, targets, lv.phi, lv.d2, weighted=prm.weighted,
-                                  n_diff=0, want_deferred=True)
-        lv.x = x_new
-        new_Hp = (eroded | (layer & deferred)).astype(np.uint8)
+        new_Hp, ev = onion_layer(lv, prm, level_index, n_layer, Hp)
+        evals += ev
         if new_Hp.sum() == Hp.sum():
             raise RuntimeError("onion peel made no progress")
         Hp = new_Hp

@@ -179,8 +179,8 @@ __device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px,
 // writes phi_out / d_out. The three neighbours' shifts and their sources' set
 // codes are loaded together before any distance.
 template <bool C5, int G, bool PARTIAL, bool F16>
-__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span, int sub, unsigned gmask,
-                                        StepCount &n)
+__device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span, bool do_random, int sub,
+                                        unsigned gmask, StepCount &n)
 {
     const LevelView &L = a.L;
     const float D = F16 ? screen_d2bound(L) : 0.0f;
@@ -249,7 +249,7 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span
 
     // random search: Eq. 3 (one radius per k), or every radius rmax rho^i >= 1
     // around the best shift so far (counter word 3 = i)
-    if (a.do_random) {
+    if (do_random) {
         for (int i = 0; i < 31; ++i) {
             const int sh = a.rs_mode ? a.rho_log2 * i : a.rho_log2 * k;
             if (a.rs_mode && (sh > 30 || (a.rmax >> sh) < 1))
@@ -465,7 +465,8 @@ __device__ __forceinline__ void warp_d2_multi(const LevelView &L, unsigned M0, u
 // ann_one. The warp leaves a stage loop together, when no lane has a stage
 // left.
 template <bool C5, bool F16, bool MIXED>
-__device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int i, int k, int span, StepCount &n)
+__device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int i, int k, int span, bool do_random,
+                                             StepCount &n)
 {
     const LevelView &L = a.L;
     const unsigned FULL = 0xffffffffu;
@@ -517,7 +518,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
             if (stage >= 3 && active) {
                 ri = stage - 3;
                 sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
-                mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
+                mine = do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
             }
             if (!__any_sync(FULL, mine))
                 break;
@@ -636,7 +637,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
             if (active) {
                 ri = stage - 3;
                 sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
-                mine = a.do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
+                mine = do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
             }
             if (!__any_sync(FULL, mine))
                 break;
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, PARTIAL>() * (2
     const unsigned gmask = group_mask<G>();
     StepCount n;
     if (i < a.nT)
-        ann_one<C5, G, PARTIAL, F16>(a, i, a.k, a.chg_span, sub, gmask, n);
+        ann_one<C5, G, PARTIAL, F16>(a, i, a.k, a.chg_span, a.do_random != 0, sub, gmask, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, sub);
 }
 
@@ -733,18 +734,21 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK)) k_ann_step
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     StepCount n;
-    ann_one_warp<C5, F16, false>(a, i < a.nT, i, a.k, a.chg_span, n);
+    ann_one_warp<C5, F16, false>(a, i < a.nT, i, a.k, a.chg_span, a.do_random != 0, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, 0);
 }
 
 // Batch form: the targets of n clips in one persistent launch. Clip c owns
 // the global target indices [prefix[c], prefix[c+1]) and is described by
-// descs[c]; every clip runs iteration k. A grid-stride loop over groups keeps
-// the grid at the resident size whatever the batch holds. ctr: evaluations,
-// FP32 voxels, FP16 voxels, screened, passed.
+// clips[c]; every clip runs sweep w (BatchSweep: iteration k, sweep index,
+// change-flag span, random search or propagation only). Sweep index s reads
+// shift buffer s & 1 (clips[c].odd for even s) and writes the other. A
+// grid-stride loop over groups keeps the grid at the resident size whatever
+// the batch holds. ctr: evaluations, FP32 voxels, FP16 voxels, screened,
+// passed.
 template <bool C5, int G, bool F16>
 __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256 / STEP_BLOCK))
-    k_ann_step_batch(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, int k,
+    k_ann_step_batch(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, BatchSweep w,
                      unsigned long long *ctr)
 {
     const int total = __ldg(prefix + n);
@@ -754,31 +758,30 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256
     StepCount cnt;
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
         const int c = find_segment(prefix, n, g);
-        const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
-        // one sweep per iteration: the same neighbours were judged two sweeps ago
-        ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), k, k >= 3 ? 2 : 0, sub, gmask, cnt);
+        const AnnArgs &a = (w.sweep & 1) ? clips[c].even : clips[c].odd;
+        ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), w.k, w.span, w.do_random != 0, sub, gmask, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, sub);
 }
 
-// Batch form of the warp-shared step: warp w of the grid-stride loop takes
-// the global targets [32 w, 32 w + 32), which may belong to several clips.
+// Batch form of the warp-shared step: warp v of the grid-stride loop takes
+// the global targets [32 v, 32 v + 32), which may belong to several clips.
 template <bool C5, bool F16>
 __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
-    k_ann_step_batch_warp(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, int k,
+    k_ann_step_batch_warp(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, BatchSweep w,
                           unsigned long long *ctr)
 {
     const int total = __ldg(prefix + n);
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x / 32);
     StepCount cnt;
-    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / 32; w * 32 < total; w += warps) {
-        const int g = w * 32 + lane;
+    for (int v = (blockIdx.x * blockDim.x + threadIdx.x) / 32; v * 32 < total; v += warps) {
+        const int g = v * 32 + lane;
         const bool active = g < total;
         const int c = active ? find_segment(prefix, n, g) : 0;
-        const AnnArgs &a = (k & 1) ? clips[c].odd : clips[c].even;
-        // one sweep per iteration: the same neighbours were judged two sweeps ago
-        ann_one_warp<C5, F16, true>(a, active, active ? g - __ldg(prefix + c) : 0, k, k >= 3 ? 2 : 0, cnt);
+        const AnnArgs &a = (w.sweep & 1) ? clips[c].even : clips[c].odd;
+        ann_one_warp<C5, F16, true>(a, active, active ? g - __ldg(prefix + c) : 0, w.k, w.span, w.do_random != 0,
+                                    cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, 0);
 }
@@ -821,7 +824,7 @@ void launch_ann_step_impl(const AnnArgs &a, bool c5, cudaStream_t st)
 }
 
 template <bool C5, int G, bool F16>
-void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, int total, int k,
+void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, int total, BatchSweep k,
                              unsigned long long *ctr, cudaStream_t st)
 {
     k_ann_step_batch<C5, G, F16><<<persistent_grid((long long)total * G,
@@ -830,7 +833,7 @@ void launch_ann_step_batch_g(const BatchClip *clips, const int *tprefix, int n, 
 }
 
 template <bool F16>
-void launch_ann_step_batch_impl(const BatchClip *clips, const int *tprefix, int n, int total, int k, bool c5,
+void launch_ann_step_batch_impl(const BatchClip *clips, const int *tprefix, int n, int total, BatchSweep k, bool c5,
                                 unsigned long long *ctr, int lanes, cudaStream_t st)
 {
     if (lanes == 32) {

@@ -430,7 +430,7 @@ void vi_config_default(vi_config *cfg)
     cfg->lanes_per_target = 0;
     cfg->stream_priority = 0;
     cfg->rs_mode = 0;
-    cfg->sub_sweeps = 1;
+    cfg->sub_sweeps = 2;
     cfg->time_subsample = 0;
     cfg->mem_limit = 0;
 }
@@ -719,6 +719,7 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
     TRY(ensure_partials(ctx, max_list));
     TRY(ensure_partials2(ctx, energy_blocks(max_t)));
     ctx->built = true;
+    ctx->hp_ready = false;
     return VI_OK;
 }
 
@@ -738,17 +739,10 @@ vi_status vi_init_nnf(vi_ctx *ctx, int level)
     return VI_OK;
 }
 
-vi_status vi_onion_peel(vi_ctx *ctx)
+// The onion-peel buffers of the coarsest level (once per context).
+static vi_status onion_buffers(vi_ctx *ctx)
 {
-    const Phase ph("onion peel");
-    if (!ctx)
-        return VI_ERR_ARG;
-    if (!ctx->built)
-        return fail(ctx, VI_ERR_STATE, "vi_onion_peel: no pyramid");
-    const int level = ctx->L - 1;
-    Level &l = ctx->lv[level];
-    const LevelView v = l.view();
-    cudaStream_t st = ctx->stream;
+    Level &l = ctx->lv[ctx->L - 1];
     const size_t V = (size_t)l.V;
     if (!ctx->hp) {
         TRY(dalloc(ctx, &ctx->hp, V));
@@ -757,50 +751,111 @@ vi_status vi_onion_peel(vi_ctx *ctx)
         TRY(dalloc(ctx, &ctx->layer_list, V * sizeof(int)));
         TRY(dalloc(ctx, &ctx->ltgt_list, V * sizeof(int)));
     }
-    TRY(ensure_partials(ctx, l.V));
-    launch_extract_bit(l.code, CODE_HOLE, ctx->hp, l.V, st);
-    CK_LAUNCH();
+    return ctx_ensure_partials(ctx, l.V);
+}
+
+// |H'| (ctx->hp at the coarsest level) into *out: one synchronisation.
+static vi_status onion_count(vi_ctx *ctx, int *out)
+{
+    Level &l = ctx->lv[ctx->L - 1];
+    cudaStream_t st = ctx->stream;
     launch_count(ctx->hp, l.V, ctx->count_dev + 60, st);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(ctx->host_counts + 60, ctx->count_dev + 60, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    int remaining = ctx->host_counts[60];
+    *out = ctx->host_counts[60];
+    return VI_OK;
+}
+
+// One layer of Algorithm 3 on H' = ctx->hp: dH' (H' minus its 3x3x3 erosion),
+// the targets (voxels outside H' whose patch meets dH'), the search of
+// Algorithm 1 with the partial distance of Eq. 11 (random draws tagged with
+// the layer index), and the vote of Eq. 12, which clears the voxels it fills
+// from H'; a layer voxel no target reaches stays in H'.
+static vi_status onion_step(vi_ctx *ctx, int n_layer)
+{
+    const int level = ctx->L - 1;
+    Level &l = ctx->lv[level];
+    const LevelView v = l.view();
+    cudaStream_t st = ctx->stream;
+    launch_onion_layer(v, ctx->hp, ctx->layer, st);
+    launch_onion_targets(v, ctx->hp, ctx->layer, ctx->ltgt, st);
+    launch_compact(ctx->layer, 1, l.V, ctx->block_counts, ctx->layer_list, ctx->count_dev + 61, st);
+    launch_compact(ctx->ltgt, 1, l.V, ctx->block_counts, ctx->ltgt_list, ctx->count_dev + 62, st);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(ctx->host_counts + 61, ctx->count_dev + 61, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int n_lay = ctx->host_counts[61], n_tgt = ctx->host_counts[62];
+    TRY(run_ann(ctx, level, ctx->ltgt_list, n_tgt, ctx->ltgt, 1, ctx->hp, make_tag(PURPOSE_ONION, level, n_layer)));
+    VoteArgs a;
+    a.L = v;
+    a.list = ctx->layer_list;
+    a.n = n_lay;
+    a.phi = l.phi[0];
+    a.d2 = l.d2[0];
+    a.allowed = ctx->ltgt;
+    a.abit = 1;
+    a.weighted = ctx->cfg.weighted;
+    a.hp = ctx->hp;
+    a.partials = ctx->partials;
+    launch_vote(a, ctx->c5, st);
+    CK_LAUNCH();
+    return VI_OK;
+}
+
+vi_status vi_onion_peel(vi_ctx *ctx)
+{
+    const Phase ph("onion peel");
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!ctx->built)
+        return fail(ctx, VI_ERR_STATE, "vi_onion_peel: no pyramid");
+    Level &l = ctx->lv[ctx->L - 1];
+    TRY(onion_buffers(ctx));
+    launch_extract_bit(l.code, CODE_HOLE, ctx->hp, l.V, ctx->stream);
+    CK_LAUNCH();
+    int remaining = 0;
+    TRY(onion_count(ctx, &remaining));
     int n_layer = 0;
     while (remaining > 0) {
-        launch_onion_layer(v, ctx->hp, ctx->layer, st);
-        launch_onion_targets(v, ctx->hp, ctx->layer, ctx->ltgt, st);
-        launch_compact(ctx->layer, 1, l.V, ctx->block_counts, ctx->layer_list, ctx->count_dev + 61, st);
-        launch_compact(ctx->ltgt, 1, l.V, ctx->block_counts, ctx->ltgt_list, ctx->count_dev + 62, st);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(ctx->host_counts + 61, ctx->count_dev + 61, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        const int n_lay = ctx->host_counts[61], n_tgt = ctx->host_counts[62];
-        TRY(run_ann(ctx, level, ctx->ltgt_list, n_tgt, ctx->ltgt, 1, ctx->hp,
-                    make_tag(PURPOSE_ONION, level, n_layer)));
-        VoteArgs a;
-        a.L = v;
-        a.list = ctx->layer_list;
-        a.n = n_lay;
-        a.phi = l.phi[0];
-        a.d2 = l.d2[0];
-        a.allowed = ctx->ltgt;
-        a.abit = 1;
-        a.weighted = ctx->cfg.weighted;
-        a.hp = ctx->hp;
-        a.partials = ctx->partials;
-        launch_vote(a, ctx->c5, st);
-        CK_LAUNCH();
-        launch_count(ctx->hp, l.V, ctx->count_dev + 60, st);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(ctx->host_counts + 60, ctx->count_dev + 60, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        const int now = ctx->host_counts[60];
+        TRY(onion_step(ctx, n_layer));
+        int now = 0;
+        TRY(onion_count(ctx, &now));
         ++n_layer;
         if (now >= remaining)
             return fail(ctx, VI_ERR_STATE, "vi_onion_peel: a layer filled no voxel");
         remaining = now;
     }
     ctx->onion_layers = n_layer;
+    ctx->hp_ready = false;
+    return VI_OK;
+}
+
+vi_status vi_onion_layer(vi_ctx *ctx, int layer, const uint8_t *hprime_in, uint8_t *hprime_out, int *n_left)
+{
+    const Phase ph("onion layer %d", layer);
+    if (!ctx)
+        return VI_ERR_ARG;
+    if (!ctx->built)
+        return fail(ctx, VI_ERR_STATE, "vi_onion_layer: no pyramid");
+    if (layer < 0 || layer > 0xFFFF)
+        return fail(ctx, VI_ERR_ARG, "vi_onion_layer: layer outside [0, 65535]");
+    Level &l = ctx->lv[ctx->L - 1];
+    TRY(onion_buffers(ctx));
+    if (hprime_in) {
+        CK(cudaMemcpyAsync(ctx->hp, hprime_in, (size_t)l.V, cudaMemcpyHostToDevice, ctx->stream));
+    } else if (!ctx->hp_ready) {
+        launch_extract_bit(l.code, CODE_HOLE, ctx->hp, l.V, ctx->stream);
+        CK_LAUNCH();
+    }
+    ctx->hp_ready = true;
+    TRY(onion_step(ctx, layer));
+    if (hprime_out)
+        CK(cudaMemcpyAsync(hprime_out, ctx->hp, (size_t)l.V, cudaMemcpyDeviceToHost, ctx->stream));
+    int left = 0;
+    TRY(onion_count(ctx, &left));
+    if (n_left)
+        *n_left = left;
     return VI_OK;
 }
 
@@ -1317,6 +1372,50 @@ vi_status vi_patch_dist(vi_ctx *ctx, int level, const int32_t *pairs_host, int n
     dfree(ctx, dout);
     if (e != cudaSuccess)
         return fail(ctx, VI_ERR_CUDA, std::string("vi_patch_dist: ") + cudaGetErrorString(e));
+    return VI_OK;
+}
+
+vi_status vi_patch_dist_partial(vi_ctx *ctx, int level, const int32_t *pairs_host, int n,
+                                const uint8_t *excl_host, float *out_host)
+{
+    if (!excl_host)
+        return vi_patch_dist(ctx, level, pairs_host, n, out_host);
+    if (!ctx || (n > 0 && (!pairs_host || !out_host)) || n < 0)
+        return VI_ERR_ARG;
+    if (!ctx->uploaded || level < 0 || level >= ctx->L)
+        return fail(ctx, VI_ERR_ARG, "vi_patch_dist_partial: bad level");
+    if (n == 0)
+        return VI_OK;
+    const size_t V = (size_t)ctx->lv[level].V;
+    int *dp = nullptr;
+    float *dout = nullptr;
+    uint8_t *dex = nullptr;
+    TRY(dalloc(ctx, &dp, sizeof(int) * 6 * (size_t)n));
+    vi_status r = dalloc(ctx, &dout, sizeof(float) * (size_t)n);
+    if (r == VI_OK)
+        r = dalloc(ctx, &dex, V);
+    if (r != VI_OK) {
+        dfree(ctx, dp);
+        dfree(ctx, dout);
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(dp, pairs_host, sizeof(int) * 6 * (size_t)n, cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dex, excl_host, V, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        launch_patch_dist_partial(ctx->lv[level].view(), dp, n, dex, dout, ctx->c5, ctx->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, dout, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, dp);
+    dfree(ctx, dout);
+    dfree(ctx, dex);
+    if (e != cudaSuccess)
+        return fail(ctx, VI_ERR_CUDA, std::string("vi_patch_dist_partial: ") + cudaGetErrorString(e));
     return VI_OK;
 }
 

@@ -238,10 +238,9 @@ static vi_status vi_batch_add_body(vi_batch *b, const vi_config *job_cfg, const 
     if (!b || !id_out)
         return VI_ERR_ARG;
     vi_config cfg = job_cfg ? *job_cfg : b->cfg;
-    if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm || cfg.storage != b->cfg.storage)
-        return bfail(b, VI_ERR_ARG, "vi_batch_add: use_texture, n_pm and storage must match the batch");
-    if (cfg.sub_sweeps != 1)
-        return bfail(b, VI_ERR_ARG, "vi_batch_add: batches run one propagation sweep per iteration");
+    if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm || cfg.storage != b->cfg.storage ||
+        cfg.sub_sweeps != b->cfg.sub_sweeps)
+        return bfail(b, VI_ERR_ARG, "vi_batch_add: use_texture, n_pm, sub_sweeps and storage must match the batch");
     vi_ctx *ctx = nullptr;
     vi_status s = vi_ctx_create(&cfg, b->stream, &ctx);
     if (s != VI_OK)
@@ -368,7 +367,10 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
         const int lanes = b->cfg.lanes_per_target;
         const int rescore_lanes = lanes == 32 ? 1 : lanes;
         launch_rescore_batch(b->d_clips, tpre, n, (int)tot_t, c5, b->counters, rescore_lanes, st);
-        for (int k = 1; k <= b->cfg.n_pm; ++k) {
+        const int J = std::max(b->cfg.sub_sweeps, 1);
+        int sweep = 0;
+        for (int k = 1; k <= b->cfg.n_pm; ++k)
+            for (int j = 0; j < J; ++j, ++sweep) {
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (b->profiling) {
                 if (b->events_used == b->events.size()) {
@@ -382,12 +384,19 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
                 ++b->events_used;
                 BCK(cudaEventRecord(e0, st));
             }
-            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, k, c5, b->cfg.storage == 1, b->counters + 1,
+            // the span of vi_run's sweeps: the previous sub-sweep, or at the
+            // first sub-sweep of iteration k >= 3 the last of iteration k - 2
+            BatchSweep w;
+            w.k = k;
+            w.sweep = sweep;
+            w.span = j > 0 ? 1 : (k >= 3 && J + 1 <= 8 ? J + 1 : 0);
+            w.do_random = j == J - 1;
+            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, w, c5, b->cfg.storage == 1, b->counters + 1,
                                   lanes, st);
             if (b->profiling)
                 BCK(cudaEventRecord(e1, st));
         }
-        if (b->cfg.n_pm & 1)
+        if (sweep & 1)
             for (int i = 0; i < n; ++i) {
                 Level &l = act[i]->ctx->lv[act[i]->level];
                 launch_copy_targets(l.targets, l.nT, l.phi[1], l.d2[1], l.phi[0], l.d2[0], st);
@@ -495,6 +504,19 @@ vi_status vi_batch_clip_stats(vi_batch *b, int id, vi_stats *out)
     if (!c)
         return bfail(b, VI_ERR_ARG, "vi_batch_clip_stats: unknown clip");
     return vi_get_stats(c->ctx, out);
+}
+
+vi_status vi_batch_clip_ctx(vi_batch *b, int id, vi_ctx **ctx_out, int *call_out)
+{
+    if (!b || !ctx_out)
+        return VI_ERR_ARG;
+    Entry *c = find(b, id);
+    if (!c)
+        return bfail(b, VI_ERR_ARG, "vi_batch_clip_ctx: unknown clip");
+    *ctx_out = c->ctx;
+    if (call_out)
+        *call_out = c->outer;
+    return VI_OK;
 }
 
 vi_status vi_batch_profile(vi_batch *b, int enable)

@@ -118,7 +118,8 @@ struct vi_ctx {
     // [3] FP16 voxels gathered, [4] candidates screened, [5] screened and passed
     unsigned long long *evals_dev = nullptr;
 
-    uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;
+    uint8_t *hp = nullptr, *layer = nullptr, *ltgt = nullptr;   // onion peel: H', dH', its targets
+    bool hp_ready = false;         // hp holds the H' left by the last vi_onion_layer
     int *layer_list = nullptr, *ltgt_list = nullptr;
 
     bool uploaded = false, built = false;

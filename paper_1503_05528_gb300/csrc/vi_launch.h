@@ -98,6 +98,8 @@ void launch_upsample_nnf(LevelView coarse, const Shift *phi_c, LevelView fine, b
 void launch_provisional_fill(LevelView coarse, LevelView fine, const int *holes_f, int nH,
                              bool c5, bool tsub, cudaStream_t st);
 void launch_patch_dist(LevelView L, const int *pairs, int n, float *out, bool c5, cudaStream_t st);
+void launch_patch_dist_partial(LevelView L, const int *pairs, int n, const uint8_t *excl, float *out, bool c5,
+                               cudaStream_t st);
 
 // ---- reconstruction (vi_vote.cu) -----------------------------------------------
 struct VoteArgs {
@@ -140,12 +142,23 @@ struct BatchClip {
     VoteArgs vote;
     float *d0;
 };
+// One Jacobi sweep of a batch round: PatchMatch iteration k (1..n_pm; the
+// scan direction and the Philox counter), sweep index (0-based over the
+// round's n_pm * sub_sweeps sweeps: sweep s reads shift buffer s & 1),
+// change-flag span (as AnnArgs::chg_span), and whether the sweep ends with
+// the random search (the last sub-sweep of an iteration) or only propagates.
+struct BatchSweep {
+    int k;
+    int sweep;
+    int span;
+    int do_random;
+};
 // clips[c] owns targets [tprefix[c], tprefix[c+1]) / holes [hprefix[c],
 // hprefix[c+1]); prefixes in device memory (n + 1 entries); totals on the host.
 // ctr: evaluations, FP32 voxels read, FP16 voxels read, screened, passed.
-void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, BatchSweep w,
                            bool c5, bool f16, unsigned long long *ctr, int lanes, cudaStream_t st);
-void launch_ann_step_batch_f16(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+void launch_ann_step_batch_f16(const BatchClip *clips, const int *tprefix, int n, int total_targets, BatchSweep w,
                                bool c5, unsigned long long *ctr, int lanes, cudaStream_t st);
 void launch_rescore_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, bool c5,
                           unsigned long long *evals, int lanes, cudaStream_t st);

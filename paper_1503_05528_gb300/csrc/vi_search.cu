@@ -218,7 +218,7 @@ void launch_ann_step(const AnnArgs &a, bool c5, cudaStream_t st)
     run(b);
 }
 
-void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, int total_targets, BatchSweep k,
                            bool c5, bool f16, unsigned long long *ctr, int lanes, cudaStream_t st)
 {
     if (total_targets <= 0 || n <= 0)
@@ -233,7 +233,7 @@ void launch_ann_step_batch(const BatchClip *clips, const int *tprefix, int n, in
     if (lanes <= 0) {
         const uint64_t key = tune_key(TUNE_STEP_BATCH, c5, f16, total_targets);
         // as in launch_ann_step: tuned on the first sweep with the change-flag rule (k >= 3)
-        lanes = k < 3 ? known_lanes(key)
+        lanes = k.k < 3 ? known_lanes(key)
                       : tuned_lanes(
                             key, st,
                             [&](int G, unsigned long long *scr) {
@@ -531,6 +531,43 @@ __global__ void k_patch_dist(LevelView L, const int *__restrict__ pairs, int n, 
         d = patch_d2<C5>(L, p, px, py, pt, s, nullptr);
     }
     out[i] = d;
+}
+
+// The partial distance of Eq. 11 for (target, source) pairs, through the
+// function the onion peel's search uses (group_d2 with PARTIAL, here by one
+// lane): target voxels with excl != 0 are left out, the sum is divided by the
+// count kept (+inf when none is).
+template <bool C5>
+__global__ void k_patch_dist_partial(LevelView L, const int *__restrict__ pairs, int n,
+                                     const uint8_t *__restrict__ excl, float *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d = __int_as_float(0x7f800000);
+    if (i < n) {
+        const int *q = pairs + 6 * i;
+        const int px = q[0], py = q[1], pt = q[2], sx = q[3], sy = q[4], st = q[5];
+        const bool src_ok = sx >= 2 && sx < L.W - 2 && sy >= 2 && sy < L.H - 2 && st >= 2 && st < L.T - 2;
+        if (src_ok && inside(L, px, py, pt)) {
+            const int p = pt * L.HW + py * L.W + px;
+            const int s = st * L.HW + sy * L.W + sx;
+            unsigned gathered = 0;
+            d = group_d2<C5, 1, true>(L, p, px, py, pt, s, excl, __int_as_float(0x7f800000), 0,
+                                      1u << (threadIdx.x & 31), gathered);
+        }
+        out[i] = d;
+    }
+}
+
+void launch_patch_dist_partial(LevelView L, const int *pairs, int n, const uint8_t *excl, float *out, bool c5,
+                               cudaStream_t st)
+{
+    if (n <= 0)
+        return;
+    VI_COUNT_LAUNCH();
+    if (c5)
+        k_patch_dist_partial<true><<<blocks_for(n, 256), 256, 0, st>>>(L, pairs, n, excl, out);
+    else
+        k_patch_dist_partial<false><<<blocks_for(n, 256), 256, 0, st>>>(L, pairs, n, excl, out);
 }
 
 void launch_patch_dist(LevelView L, const int *pairs, int n, float *out, bool c5, cudaStream_t st)

@@ -7,7 +7,7 @@ namespace vi {
 
 void launch_ann_step_f16(const AnnArgs &a, bool c5, cudaStream_t st) { launch_ann_step_impl<true>(a, c5, st); }
 
-void launch_ann_step_batch_f16(const BatchClip *clips, const int *tprefix, int n, int total_targets, int k,
+void launch_ann_step_batch_f16(const BatchClip *clips, const int *tprefix, int n, int total_targets, BatchSweep k,
                                bool c5, unsigned long long *ctr, int lanes, cudaStream_t st)
 {
     launch_ann_step_batch_impl<true>(clips, tprefix, n, total_targets, k, c5, ctr, lanes, st);

@@ -24,7 +24,7 @@ STATUS = {0: "VI_OK", 1: "VI_ERR_ARG", 2: "VI_ERR_OOM", 3: "VI_ERR_CUDA", 4: "VI
 EXPORTS = [
     "vi_config_default", "vi_ctx_create", "vi_ctx_destroy", "vi_last_error", "vi_auto_levels",
     "vi_footprint_bytes", "vi_upload", "vi_build_pyramid", "vi_init_nnf", "vi_onion_peel",
-    "vi_prepare", "vi_rescore", "vi_ann", "vi_reconstruct", "vi_iterate", "vi_next_level",
+    "vi_onion_layer", "vi_patch_dist_partial", "vi_prepare", "vi_rescore", "vi_ann", "vi_reconstruct", "vi_iterate", "vi_next_level",
     "vi_final", "vi_run", "vi_energy", "vi_level_info", "vi_get_channels", "vi_set_channels",
     "vi_get_nnf", "vi_set_nnf", "vi_get_masks", "vi_patch_dist", "vi_fetch_result",
     "vi_profile", "vi_get_stats", "vi_energy_noalloc", "vi_tune_export", "vi_tune_import",
@@ -36,6 +36,7 @@ EXPORTS = [
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
+    "vi_batch_clip_ctx",
 ]
 
 
@@ -116,6 +117,8 @@ def _declare(L):
     L.vi_set_nnf.argtypes = [vp, i, vp, vp]
     L.vi_get_masks.argtypes = [vp, i, vp]
     L.vi_patch_dist.argtypes = [vp, i, vp, i, vp]
+    L.vi_patch_dist_partial.argtypes = [vp, i, vp, i, vp, vp]
+    L.vi_onion_layer.argtypes = [vp, i, vp, vp, P(i)]
     L.vi_fetch_result.argtypes = [vp, vp, i]
     L.vi_profile.argtypes = [vp, i]
     L.vi_get_stats.argtypes = [vp, P(ViStats)]
@@ -161,6 +164,7 @@ def _declare(L):
     L.vi_batch_fetch.argtypes = [vp, i, vp, i]
     L.vi_batch_remove.argtypes = [vp, i]
     L.vi_batch_clip_stats.argtypes = [vp, i, P(ViStats)]
+    L.vi_batch_clip_ctx.argtypes = [vp, i, P(vp), P(i)]
     L.vi_batch_get_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
     L.vi_batch_screen_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
     L.vi_batch_profile.argtypes = [vp, i]
@@ -202,8 +206,17 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.vi_ctx_destroy(self.h)
+            if not getattr(self, "borrowed", False):
+                self.lib.vi_ctx_destroy(self.h)
             self.h = None
+
+    @classmethod
+    def borrow(cls, lib, h):
+        """A view of a context the library owns (a batch clip's): the same
+        methods, and close() leaves the context alone."""
+        obj = cls.__new__(cls)
+        obj.lib, obj.h, obj.cfg, obj.borrowed = lib, h, None, True
+        return obj
 
     def __del__(self):
         try:
@@ -242,6 +255,21 @@ class Context:
 
     def onion_peel(self):
         self._ck(self.lib.vi_onion_peel(self.h))
+
+    def onion_layer(self, layer, hprime=None):
+        """One layer of Algorithm 3 (vi_onion_layer). hprime: uint8 [T][H][W]
+        of the coarsest level (None: continue from the context's own H').
+        Returns (H' after the layer, its size)."""
+        info = self.level_info(self.stats()["levels"] - 1)
+        out = np.zeros((info["T"], info["H"], info["W"]), np.uint8)
+        hin = None
+        if hprime is not None:
+            hin = np.ascontiguousarray(hprime, np.uint8)
+            assert hin.shape == out.shape
+        left = C.c_int(0)
+        self._ck(self.lib.vi_onion_layer(self.h, int(layer), hin.ctypes.data if hin is not None else None,
+                                         out.ctypes.data, C.byref(left)))
+        return out, left.value
 
     def prepare(self):
         self._ck(self.lib.vi_prepare(self.h))
@@ -318,6 +346,16 @@ class Context:
         code = np.zeros((info["T"], info["H"], info["W"]), np.uint8)
         self._ck(self.lib.vi_get_masks(self.h, level, code.ctypes.data))
         return code
+
+    def patch_dist_partial(self, level, pairs, excl):
+        """Eq. 11 distances for (px, py, pt, sx, sy, st) pairs, target voxels
+        with excl != 0 left out (vi_patch_dist_partial)."""
+        pairs = np.ascontiguousarray(pairs, np.int32).reshape(-1, 6)
+        ex = np.ascontiguousarray(excl, np.uint8)
+        out = np.zeros(len(pairs), np.float32)
+        self._ck(self.lib.vi_patch_dist_partial(self.h, level, pairs.ctypes.data, len(pairs), ex.ctypes.data,
+                                                out.ctypes.data))
+        return out
 
     def patch_dist(self, level, pairs):
         pairs = np.ascontiguousarray(pairs, np.int32).reshape(-1, 6)
@@ -455,6 +493,14 @@ class Batch:
     def remove(self, cid):
         self._ck(self.lib.vi_batch_remove(self.h, cid))
         self._keep.pop(cid, None)
+
+    def clip_context(self, cid):
+        """(context view, iteration index at its level) of a clip
+        (vi_batch_clip_ctx), for injecting and reading its state."""
+        h = C.c_void_p()
+        call = C.c_int(0)
+        self._ck(self.lib.vi_batch_clip_ctx(self.h, cid, C.byref(h), C.byref(call)))
+        return Context.borrow(self.lib, h), call.value
 
     def clip_stats(self, cid):
         s = ViStats()

@@ -50,7 +50,7 @@ def test_config_defaults_are_the_papers(lib):
     assert cfg.lambda_ == 50.0 and cfg.n_pm == 10 and cfg.rho == 0.5
     assert cfg.max_outer == 20 and abs(cfg.stop - 0.1 / 255) < 1e-9
     assert cfg.weighted == 1 and cfg.use_texture == 1 and cfg.storage == 0
-    assert cfg.mem_limit == 0 and cfg.time_subsample == 0 and cfg.sub_sweeps == 1
+    assert cfg.mem_limit == 0 and cfg.time_subsample == 0 and cfg.sub_sweeps == 2
 
 
 def test_auto_levels_rule(lib):

@@ -120,3 +120,21 @@ def test_warp_shared_batch_mixed_search_modes():
                 ctx.run()
                 want = ctx.fetch_result()
             assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
+
+
+@pytest.mark.parametrize("lanes", [0, 32])
+def test_batch_with_sub_sweeps_is_identical_to_vi_run(lanes):
+    # two propagation sweeps per iteration: a clip's batch result equals the
+    # single-clip run with the same setting, bit for bit
+    clips = [_clip(s) for s in SPECS[:4]]
+    with vi.Batch(sub_sweeps=2, lanes_per_target=lanes) as b:
+        ids = [b.add(c.rgb, c.mask, levels=c.levels, seed=500 + i, clip=i) for i, c in enumerate(clips)]
+        b.run()
+        for i, (cid, c) in enumerate(zip(ids, clips)):
+            with vi.Context(levels=c.levels, seed=500 + i, clip=i, sub_sweeps=2, lanes_per_target=lanes) as ctx:
+                ctx.upload(c.rgb, c.mask)
+                ctx.run()
+                want = ctx.fetch_result()
+                outer = ctx.stats()["outer"]
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
+            assert b.clip_stats(cid)["outer"] == outer

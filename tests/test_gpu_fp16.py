@@ -37,7 +37,7 @@ def _make(case, seed, n_pm=10, lanes=0):
     spec = CASES[case]
     clip = spec["clip"]()
     pyr = O.build_pyramid(clip.rgb, clip.mask, spec["levels"], spec["tex"])
-    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=1,
+    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=1, sub_sweeps=2,
                      lanes_per_target=lanes)
     ctx.upload(clip.rgb, clip.mask)
     ctx.build_pyramid()
@@ -65,7 +65,7 @@ def _ann_check(ctx, lv, level, x, phi, d2, seed, n_pm, call):
     s1 = ctx.stats()
     gphi, gd2 = ctx.get_nnf(level)
     o_evals = O.ann(x, lv.htilde, lv.dtilde, phi, d2, n_pm=n_pm, schedule="JAC", key=(seed, 0),
-                    tag_base=O.tag(O.PURPOSE_SEARCH, level, call))
+                    tag_base=O.tag(O.PURPOSE_SEARCH, level, call), sub_sweeps=2)
     m = lv.htilde == 1
     assert (gphi[m] == phi[m]).all()
     assert (gd2[m].view(np.uint32) == d2[m].view(np.uint32)).all()
