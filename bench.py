@@ -1,25 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the inpainting hot path on GB300.
 
-A step is one whole inpainting of a synthetic layered-motion clip through the
-C ABI (vi_upload + vi_run + vi_fetch_result): pyramid and features, shift-map
-initialisation, onion-peel initialisation, per level the PatchMatch search
-and reconstruction until the stopping rule, level transitions and the final
-best-patch step. Default workload: 320x240 px x 60 frames RGB, 3 sprites,
-8% occlusion tube, 4 levels, colour + 2 texture channels, FP32 storage.
+Default workload (batch48): 48 synthetic layered-motion clips of uneven sizes
+(W ~ logU[160, 640], H ~ logU[120, 480], frames ~ logU[20, 80], 3-12%
+occlusion tubes; 163M voxels, levels by the rule of Sec. 3.6), inpainted as
+one batch through the C ABI (vi_batch_add / vi_batch_run / vi_batch_fetch /
+vi_batch_remove): pyramids and features, initialisations, onion peels, per
+level the PatchMatch search and reconstruction rounds until each clip's
+stopping rule, level transitions and the final best-patch step. A step is
+the whole batch. --workload layered_320x240x60 / layered_1280x720x100 runs one
+clip per step through vi_run; serve_poisson4 the serving stream.
 
-Output: one JSON line (rank 0). `value` is patch-distance evaluations per
+Output: one JSON line (rank 0). `value` is inpainted (occluded) voxels per
 second over the whole job (all ranks), inputs resident in device memory when
-the timed region starts. `e2e` is the same metric through the same calls with
-host buffers (host->device upload and device->host fetch inside the timed
-region). `roofline` is the PatchMatch step kernel's gathered source bytes
-(20 B per source voxel read; a full evaluation is 125 voxels = 2,500 B, and
-exact pruning skips or shortens most of them) over its CUDA-event time,
-against the measured HBM copy bandwidth. `cpu_baseline` times the CPU oracle
-(sequential PatchMatch, one thread) on a bounded sample of the same workload.
---workload layered_1280x720x100 selects the HD clip (5 levels).
+the timed region starts; `evals_per_s` is the patch-distance evaluation rate
+of the same run (every candidate of Algorithm 1 that lands in D~, whether or
+not exact pruning let it skip its gather). `e2e` is the same metric with the
+inputs uploaded from pinned host buffers and every result fetched to host
+memory inside the timed region. `roofline` is the PatchMatch step kernel's
+gathered source bytes over its CUDA-event time against the measured HBM copy
+bandwidth, with the per-evaluation count beside it. `cpu_baseline` times the
+CPU oracle on the host cores, one clip per core, on a bounded sample of the
+same workload.
 
-Multi-GPU (torchrun): replicas only -- each rank inpaints its own clip; no
+Multi-GPU (torchrun): replicas only -- each rank inpaints its own clips; no
 collective on the data path; barrier + max-over-ranks timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -38,22 +42,61 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "patch-distance evals/s (and inpainted voxels/s) vs HBM roofline"
-UNIT = "evals/s"
-WORKLOAD = "layered_320x240x60"
+METRIC = "patch-distance evals/s and inpainted voxels/s vs HBM roofline; serving p50/p99"
+UNIT = "inpainted voxels/s"
+WORKLOAD = "batch48"
 BYTES_PER_VOXEL_FP32_C5 = 5 * 4           # one source voxel: 5 FP32 channels
 BYTES_PER_EVAL_FP32_C5 = 125 * BYTES_PER_VOXEL_FP32_C5   # a whole source patch
 BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the FP16 copy
 
-# DRAM bytes (read + write) per launch of the PatchMatch step kernels,
-# averaged over the step launches of one inpainting of the default workload
-# in its default configuration (FP32 storage, Eq. 3 random search, one sweep
-# per iteration, autotuned lanes, no realignment), and the source voxels
-# those launches gathered per launch, from one ncu capture
-# (profiles/k_ann_step_layered_320x240x60.md). Applies to that configuration
-# only; None while the kernels have changed since the capture.
-NCU_STEP_TRAFFIC = {"workload": "layered_320x240x60", "storage": "fp32", "rs_mode": "eq3", "sub_sweeps": 1,
-                    "bytes": (3634.43e6 + 38.00e6) / 330, "gathered_voxels": 68953343.0 / 20}
+# DRAM bytes (read + write) of the PatchMatch step kernel per gathered source
+# voxel, from one ncu capture of a few launches of that kernel (the profiles
+# directory names the command), keyed by (workload, storage, propagation
+# sweeps per iteration). A run of the same configuration scales it by the
+# source voxels its launches gathered. Empty while the kernels have changed
+# since the capture.
+NCU_STEP_TRAFFIC = {}
+
+# What the ncu counters of the step kernel show binds it (the roofline object
+# reports the gather against the HBM copy bandwidth; this says what actually
+# limits it).
+STEP_LIMITER = ("latency of dependent gathers served by L1/L2 (ncu: long-scoreboard stalls dominate, "
+                "L1 throughput the next limit, DRAM throughput low); not HBM bandwidth")
+
+
+def step_traffic(args, workload, gathered, gathered_h, launches):
+    key = (workload, args.storage, args.sub_sweeps)
+    per_voxel = NCU_STEP_TRAFFIC.get(key)
+    if per_voxel is None or not launches or args.lanes or getattr(args, "realign", False) or \
+            getattr(args, "rs_mode", "eq3") != "eq3":
+        return None
+    return per_voxel * (gathered + gathered_h) / launches
+
+
+def step_roofline(gathered, gathered_h, step_evals, step_ms, wall_ms, peak, peak_kind, kernel, traffic,
+                  launches):
+    """The roofline object of the step kernel: bytes it gathers (20 B per FP32
+    source voxel, 8 B per FP16 one) over its CUDA-event time against the
+    measured HBM copy bandwidth; beside it the same launches counted at a
+    whole patch per evaluation (125 voxels x 20 B)."""
+    if step_ms <= 0:
+        return None
+    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16
+    achieved = gbytes / (step_ms / 1e3) / 1e9
+    full = step_evals * BYTES_PER_EVAL_FP32_C5 / (step_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "unit_of_work": "one gathered source voxel: 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
+            "gathered_bytes_per_launch": gbytes / launches if launches else None,
+            "launches_timed": launches,
+            "gathered_voxels_per_eval": (gathered + gathered_h) / step_evals if step_evals else None,
+            "limiter": STEP_LIMITER,
+            "per_evaluation_unit": {
+                "bytes_per_eval": BYTES_PER_EVAL_FP32_C5, "achieved": full, "frac": full / peak,
+                "evals_per_s_in_kernel": step_evals / (step_ms / 1e3),
+                "note": "every counted evaluation at a whole 125-voxel FP32 patch; exact pruning skips most "
+                        "of each patch and L1/L2 serve most of the rest, so this is not a bandwidth"},
+            "kernel_ms_share": step_ms / wall_ms if wall_ms > 0 else None}
 
 
 def combine_ranks(values, dist=None, device="cpu"):
@@ -165,7 +208,7 @@ WORKLOADS = {
 }
 
 
-def make_clip(rank, workload=WORKLOAD):
+def make_clip(rank, workload="layered_320x240x60"):
     from paper_1503_05528_gb300 import synth
     W, H, T, ns, sp, frac, L, off, dyn = WORKLOADS[workload]
     # weak scaling: every rank inpaints its own clip of the same size
@@ -179,13 +222,18 @@ def make_clip(rank, workload=WORKLOAD):
 class OracleSample:
     """Level-0 state of the workload for timing the oracle's PatchMatch:
     the oracle's own pyramid level, occluded voxels set to mid-grey, a random
-    shift map from the oracle's initialisation."""
+    shift map from the oracle's initialisation. The search is the one the GPU
+    path runs (the Jacobi schedule with its propagation sweeps per
+    iteration), so its evaluation counts are comparable."""
 
-    def __init__(self, clip):
+    def __init__(self, clip, sub_sweeps=2, schedule="JAC"):
         import numpy as np
         from oracle import oracle as O
         self.O = O
-        lv = O.build_pyramid(clip.rgb, clip.mask, clip.levels, True)[0]
+        self.sub_sweeps = sub_sweeps
+        self.schedule = schedule
+        levels = clip.levels or 1
+        lv = O.build_pyramid(clip.rgb, clip.mask, levels, True)[0]
         lv.x[lv.hole == 1] = 0.5
         lv.phi = O.init_nnf(lv.htilde, lv.dtilde, (1503, 0), O.tag(O.PURPOSE_INIT, 0))
         lv.d2 = np.full(lv.hole.shape, np.inf, np.float32)
@@ -194,9 +242,9 @@ class OracleSample:
         self.next_t = 2
 
     def slab(self, frames):
-        """One ANN search (rescore + 10 sequential PatchMatch iterations,
-        Algorithm 1 as printed) over the targets of `frames` consecutive frames.
-        Returns (evals, seconds)."""
+        """One ANN search (rescore + 10 PatchMatch iterations of Algorithm 1)
+        over the targets of `frames` consecutive frames. Returns (evals,
+        seconds)."""
         import numpy as np
         lv = self.lv
         t0 = self.next_t
@@ -206,49 +254,140 @@ class OracleSample:
         phi = lv.phi.copy()
         d2 = lv.d2.copy()
         s = time.perf_counter()
-        ev = self.O.ann(lv.x, tgt, lv.dtilde, phi, d2, n_pm=10, schedule="SEQ", key=(1503, 0),
-                        tag_base=self.O.tag(self.O.PURPOSE_SEARCH, 0, 0))
+        ev = self.O.ann(lv.x, tgt, lv.dtilde, phi, d2, n_pm=10, schedule=self.schedule, key=(1503, 0),
+                        tag_base=self.O.tag(self.O.PURPOSE_SEARCH, 0, 0), sub_sweeps=self.sub_sweeps)
         return ev, time.perf_counter() - s
 
 
-def cpu_baseline(clip, seconds):
-    smp = OracleSample(clip)
-    evals, el, frames = 0, 0.0, 0
-    while el < seconds:
-        ev, dt = smp.slab(2)
-        evals += ev
-        el += dt
-        frames += 2
-    return {"value": evals / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"sequential ANN search (rescore + 10 PatchMatch iterations) over the "
-                      f"level-0 targets of {frames} frames of {clip.name}: {evals} evaluations "
-                      f"in {el:.1f} s, one thread"}
+def _oracle_worker(conn, clip_spec, sub_sweeps):
+    """A spawned process holding one clip's oracle sample: answers each
+    number of seconds received with (evaluations, seconds, frames) of
+    two-frame slab searches run for at least that long; None ends it."""
+    clip = _make_clip_from_spec(clip_spec)
+    smp = OracleSample(clip, sub_sweeps=sub_sweeps)
+    conn.send(("ready", clip.name))
+    while True:
+        seconds = conn.recv()
+        if seconds is None:
+            break
+        evals, el, frames = 0, 0.0, 0
+        while el < seconds:
+            ev, dt = smp.slab(2)
+            evals += ev
+            el += dt
+            frames += 2
+        conn.send((evals, el, frames))
+    conn.close()
+
+
+class OracleWorkers:
+    """One spawned process per host core, each with its own clip of the
+    workload (clips spread one per core), for timing the CPU oracle on all
+    cores at once. Spawned, not forked: the parent may hold a CUDA context."""
+
+    def __init__(self, specs, sub_sweeps):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.procs, self.conns = [], []
+        for spec in specs:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, spec, sub_sweeps), daemon=True)
+            p.start()
+            self.procs.append(p)
+            self.conns.append(a)
+        self.names = [c.recv()[1] for c in self.conns]
+
+    def run(self, seconds):
+        """(evaluations of all workers, wall seconds, frames) of one bounded
+        sample: every worker searches for about `seconds`."""
+        t = time.perf_counter()
+        for c in self.conns:
+            c.send(seconds)
+        res = [c.recv() for c in self.conns]
+        return sum(r[0] for r in res), time.perf_counter() - t, sum(r[2] for r in res)
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(specs, seconds, sub_sweeps, evals_per_voxel, workload):
+    """The oracle on the host cores, one clip per core (one core for a single
+    clip), as it stands: its Jacobi search over two-frame slabs of each
+    clip's level-0 targets for about `seconds`. Its evaluation rate, divided
+    by the evaluations the GPU run made per inpainted voxel (the oracle makes
+    the same evaluations for the same state), gives the extrapolated
+    inpainted voxels/s."""
+    w = OracleWorkers(specs, sub_sweeps)
+    try:
+        evals, wall, frames = w.run(seconds)
+    finally:
+        w.close()
+    rate = evals / wall
+    return {"value": rate / evals_per_voxel, "unit": UNIT, "cores": len(specs), "kind": "oracle",
+            "evals_per_s": rate,
+            "sample": f"{workload}: {len(specs)} clip(s), one per core; the oracle's search (rescore + 10 "
+                      f"PatchMatch iterations, {sub_sweeps} propagation sweeps each) over two-frame slabs of "
+                      f"each clip's level-0 targets, {frames} frames in all, {evals} evaluations in "
+                      f"{wall:.1f} s; inpainted voxels/s extrapolated by the GPU run's "
+                      f"{evals_per_voxel:.0f} evaluations per inpainted voxel"}
 
 
 def run_reference(args):
+    """The CPU oracle as the reference arm: on the host cores, one clip per
+    core, each step a bounded sample (every worker searches two-frame slabs of
+    its clip's level-0 targets for about --ref-seconds), reported in the GPU
+    arm's unit by the workload's evaluations per inpainted voxel."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    workload = args.workload if args.workload in WORKLOADS else WORKLOAD
-    clip = make_clip(0, workload)
-    smp = OracleSample(clip)
-    frames = 2
-    for _ in range(args.warmup):
-        smp.slab(frames)
-    evals, el = 0, 0.0
-    for _ in range(args.steps):
-        ev, dt = smp.slab(frames)
-        evals += ev
-        el += dt
-    value = evals / el
+    workload = args.workload
+    if workload not in EVALS_PER_HOLE_VOXEL or EVALS_PER_HOLE_VOXEL[workload] is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no evaluation count per inpainted voxel "
+                                                                f"stored for {workload}"}), flush=True)
+        return 0
+    epv = EVALS_PER_HOLE_VOXEL[workload]
+    specs = oracle_specs(workload)
+    w = OracleWorkers(specs, args.sub_sweeps)
+    try:
+        for _ in range(args.warmup):
+            w.run(args.ref_seconds)
+        evals, wall, frames = 0, 0.0, 0
+        for _ in range(args.steps):
+            ev, dt, fr = w.run(args.ref_seconds)
+            evals += ev
+            wall += dt
+            frames += fr
+    finally:
+        w.close()
+    rate = evals / wall
+    value = rate / epv
+    sample = (f"each step: {len(specs)} clip(s) of {workload}, one per core; the oracle's search (rescore + "
+              f"10 PatchMatch iterations, {args.sub_sweeps} propagation sweeps each) over two-frame slabs of "
+              f"each clip's level-0 targets for about {args.ref_seconds:.1f} s; inpainted voxels/s "
+              f"extrapolated by {epv:.0f} evaluations per inpainted voxel")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * el / args.steps, "higher_is_better": True,
+            "ms_per_step": 1000.0 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "sample": f"{frames} frames per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: sequential ANN search over the level-0 "
-                                       f"targets of {frames} frames of {workload}, one thread"},
+            "config": {"workload": workload, "sub_sweeps": args.sub_sweeps, "sample": sample},
+            "evals_per_s": rate,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(specs), "kind": "oracle",
+                             "evals_per_s": rate, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -385,21 +524,9 @@ def run_gpu(args):
         return 0
 
     peak, peak_kind = _peaks()
-    # algorithmic bytes of the step kernel: the source voxels it has to gather
-    # (20 B each: 5 FP32 channels; 8 B from the FP16 copy when screening). A
-    # candidate equal to a shift already compared needs no gather, and a gather
-    # stops once the partial sum shows the candidate cannot win; both leave
-    # every decision unchanged.
-    gathered_bytes = step_gathered * BYTES_PER_VOXEL_FP32_C5 + step_gathered_h * BYTES_PER_VOXEL_FP16
-    achieved = gathered_bytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
-    traffic = None
-    if (NCU_STEP_TRAFFIC and step_launches and NCU_STEP_TRAFFIC["workload"] == args.workload
-            and NCU_STEP_TRAFFIC["storage"] == args.storage and NCU_STEP_TRAFFIC["rs_mode"] == args.rs_mode
-            and NCU_STEP_TRAFFIC["sub_sweeps"] == args.sub_sweeps and not args.lanes and not args.realign):
-        per_voxel = NCU_STEP_TRAFFIC["bytes"] / NCU_STEP_TRAFFIC["gathered_voxels"]
-        traffic = per_voxel * step_gathered / step_launches
+    evals_per_voxel = evals / (n_hole * args.steps)
     line = {
-        "metric": METRIC, "value": evals_tot / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": hole_tot * args.steps / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -409,8 +536,11 @@ def run_gpu(args):
                    "hole_voxels": n_hole, "parallelism": f"replicas x{world}",
                    "lanes_per_target": args.lanes or "auto",
                    "l2": "inputs larger than L2: level-0 state about 0.3 GB per clip, rebuilt every step"},
-        "inpainted_voxels_per_s": hole_tot * args.steps / (ms_max / 1e3),
+        "evals_per_s": evals_tot / (ms_max / 1e3),
         "evals_per_step": evals / args.steps,
+        "evals_per_inpainted_voxel": evals_per_voxel,
+        "gathered_evals_per_s": ((step_gathered * BYTES_PER_VOXEL_FP32_C5 + step_gathered_h * BYTES_PER_VOXEL_FP16)
+                                 / BYTES_PER_EVAL_FP32_C5 * world / (ms_max / 1e3)),
         "outer_iterations_per_level": outer[:clip.levels],
         "energy_level0": {"E_H": energy[0], "E_Htilde": energy[1]},
         "realign_ms_per_step": realign_ms,
@@ -418,19 +548,12 @@ def run_gpu(args):
                        "pass_rate": passed / screened if screened else None,
                        "fp16_voxels": step_gathered_h, "fp32_voxels": step_gathered}
                       if storage else None),
-        "roofline": {"bound": "hbm", "kernel": "k_ann_step + k_ann_step_warp (PatchMatch propagation + random search, every level)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": traffic,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
-                     "gathered_bytes_per_launch": gathered_bytes / step_launches if step_launches else None,
-                     "launches_timed": step_launches,
-                     "evals_per_launch": step_evals / step_launches if step_launches else None,
-                     "evals_per_s_in_kernel": step_evals / (step_ms / 1e3) if step_ms > 0 else None,
-                     "full_eval_bytes": BYTES_PER_EVAL_FP32_C5,
-                     "gathered_bytes_per_eval": gathered_bytes / step_evals if step_evals else None,
-                     "kernel_ms_share": step_ms / ms if ms > 0 else None},
-        "e2e": {"value": e2e_evals_tot / e2e_max, "unit": UNIT,
+        "roofline": step_roofline(step_gathered, step_gathered_h, step_evals, step_ms, ms, peak, peak_kind,
+                                  "k_ann_step_warp + k_ann_step (PatchMatch propagation + random search, "
+                                  "every level)",
+                                  step_traffic(args, args.workload, step_gathered, step_gathered_h, step_launches),
+                                  step_launches),
+        "e2e": {"value": hole_tot * args.steps / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": int(clip.rgb.nbytes + clip.mask.nbytes),
                 "d2h_bytes_per_step": int(clip.rgb.nbytes)},
         "gpu_launches": launches,
@@ -438,7 +561,8 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(clip, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(oracle_specs(args.workload), args.cpu_seconds, args.sub_sweeps,
+                                            evals_per_voxel, args.workload)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -448,22 +572,50 @@ def run_gpu(args):
 BATCH_WORKLOAD = "batch48"
 
 
-def make_batch_clips(rank, n=48):
-    """48 layered clips of uneven sizes (W ~ logU[160, 640], H ~ logU[120, 480],
-    frames ~ logU[20, 80], hole 3-12%); levels by the rule of Sec. 3.6."""
+def make_batch_clip(rank, i, n=48):
+    """Clip i of the 48 layered clips of uneven sizes (W ~ logU[160, 640],
+    H ~ logU[120, 480], frames ~ logU[20, 80], hole 3-12%); levels by the
+    rule of Sec. 3.6."""
     from paper_1503_05528_gb300 import synth
-    clips = []
-    for i, (W, H, T, frac) in enumerate(synth.batch_sizes(n)):
-        clips.append(synth.layered_clip(W, H, T, 3, (16, 48), frac, 0,
-                                        synth.BASE_SEED + 200 + 1000 * rank + i, name=f"batch_{i}"))
-    return clips
+    W, H, T, frac = synth.batch_sizes(n)[i]
+    return synth.layered_clip(W, H, T, 3, (16, 48), frac, 0, synth.BASE_SEED + 200 + 1000 * rank + i,
+                              name=f"batch_{i}")
+
+
+def make_batch_clips(rank, n=48):
+    return [make_batch_clip(rank, i, n) for i in range(n)]
+
+
+def _make_clip_from_spec(spec):
+    """("batch", rank, i) or ("clip", rank, workload)."""
+    if spec[0] == "batch":
+        return make_batch_clip(spec[1], spec[2])
+    return make_clip(spec[1], spec[2])
+
+
+def oracle_specs(workload, rank=0):
+    """The clips the CPU oracle is timed on: one per host core for the batch
+    (the first min(cores, 48) clips), the clip itself for a single clip."""
+    if workload == BATCH_WORKLOAD:
+        return [("batch", rank, i) for i in range(min(host_cores(), 48))]
+    return [("clip", rank, workload)]
+
+
+# Evaluations per inpainted voxel of a whole inpainting of each workload in
+# the default configuration (two propagation sweeps per iteration, Eq. 3
+# random search): a property of the workload, not a timing -- the GPU path's
+# count, which equals the oracle's for the same state (tests compare the
+# counts). The GPU arm measures it on every run; the --impl reference arm,
+# which has no GPU, converts the oracle's evaluation rate with it.
+EVALS_PER_HOLE_VOXEL = {"batch48": None, "layered_320x240x60": None, "layered_1280x720x100": None}
 
 
 def run_batch(args):
     """A step inpaints 48 uneven clips as one batch (vi_batch_*): add and
-    prepare every clip, rounds until all are done, fetch every result. The
-    same clips run one after another through vi_run give the single-clip
-    comparison (bit-identical results, hence the same energies)."""
+    prepare every clip, rounds until all are done, fetch every result; the
+    inputs are resident in device memory. The e2e leg repeats the step from
+    pinned host buffers to host buffers. The same clips one after another
+    through vi_run give the single-clip comparison (bit-identical results)."""
     import torch
 
     from paper_1503_05528_gb300 import vi
@@ -476,29 +628,31 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     vi.load(build_if_missing=True)
     _tune_load(args, vi)
-    clips = make_batch_clips(rank)
+    clips = [make_batch_clip(rank, i) for i in range(min(args.clips, 48))]
     dev = [(torch.from_numpy(c.rgb).cuda(), torch.from_numpy(c.mask).cuda()) for c in clips]
     outs = [torch.empty_like(r) for r, _ in dev]
     n_hole = sum(int(c.mask.sum()) for c in clips)
     n_vox = sum(int(c.mask.size) for c in clips)
     stream = torch.cuda.current_stream()
     storage = 1 if args.storage == "fp16" else 0
-    b = vi.Batch(stream=stream.cuda_stream, levels=0, lanes_per_target=args.lanes, storage=storage,
-                 sub_sweeps=args.sub_sweeps)
+    kw = dict(levels=0, lanes_per_target=args.lanes, storage=storage, sub_sweeps=args.sub_sweeps)
+    b = vi.Batch(stream=stream.cuda_stream, **kw)
+    counter = vi.Context(**kw)      # reads the library's launch counter
 
-    def step():
-        ids = [b.add(r, m, levels=0, seed=1503 + i, clip=i) for i, (r, m) in enumerate(dev)]
+    def step(inputs, outputs):
+        ids = [b.add(r, m, levels=0, seed=1503 + i, clip=i) for i, (r, m) in enumerate(inputs)]
         b.run()
-        for cid, o in zip(ids, outs):
+        for cid, o in zip(ids, outputs):
             b.fetch(cid, o)
         for cid in ids:
             b.remove(cid)
 
     for _ in range(args.warmup):
-        step()
+        step(dev, outs)
     _tune_save(args, vi)
     b.profile(True)
     s0 = b.stats()
+    l0 = counter.stats()["launches"]
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
@@ -513,30 +667,49 @@ def run_batch(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(dev, outs)
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop()
     s1 = b.stats()
+    launches = counter.stats()["launches"] - l0
     b.profile(False)
     ms = e0.elapsed_time(e1)
     evals = s1["evals"] - s0["evals"]
     step_ms = s1["step_ms"] - s0["step_ms"]
+    step_evals = s1["step_evals"] - s0["step_evals"]
     gathered = s1["gathered"] - s0["gathered"]
     gathered_h = s1["gathered_h"] - s0["gathered_h"]
     screened = s1["screened"] - s0["screened"]
     passed = s1["screen_passed"] - s0["screen_passed"]
     rounds = (s1["rounds"] - s0["rounds"]) / args.steps
+    step_launches = (s1["rounds"] - s0["rounds"]) * 10 * args.sub_sweeps   # n_pm sweeps x sub-sweeps per round
+
+    # end to end through host buffers: every step uploads its clips from
+    # pinned host memory and fetches every result to pinned host memory
+    e2e_steps = max(1, min(args.steps, 5))
+    host_in = [(torch.from_numpy(c.rgb).pin_memory().numpy(), torch.from_numpy(c.mask).pin_memory().numpy())
+               for c in clips]
+    host_out = [torch.empty(c.rgb.shape, dtype=torch.float32).pin_memory().numpy() for c in clips]
+    step(host_in, host_out)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(host_in, host_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t
+    assert all((h == o.cpu().numpy()).all() for h, o in zip(host_out, outs)), "host and device runs differ"
 
     # the same clips one after another through the single-clip path
     torch.cuda.synchronize()
     t = time.perf_counter()
     single_evals = 0
     for i, (r, m) in enumerate(dev):
-        with vi.Context(levels=0, seed=1503 + i, clip=i, stream=stream.cuda_stream,
-                        lanes_per_target=args.lanes, storage=storage, sub_sweeps=args.sub_sweeps) as ctx:
+        with vi.Context(seed=1503 + i, clip=i, stream=stream.cuda_stream, **kw) as ctx:
             ctx.upload(r, m)
             ctx.run()
             ctx.fetch_result(outs[i])
@@ -544,41 +717,52 @@ def run_batch(args):
     torch.cuda.synchronize()
     single_s = time.perf_counter() - t
     b.close()
+    counter.close()
 
-    mx, sm = combine_ranks([ms, float(evals), float(n_hole), single_s, float(single_evals)], dist, "cuda")
+    mx, sm = combine_ranks([ms, float(evals), float(n_hole), single_s, float(single_evals), e2e_s], dist, "cuda")
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
+    ms_max, evals_tot, hole_tot = mx[0], sm[1], sm[2]
     peak, peak_kind = _peaks()
-    gbytes = gathered * BYTES_PER_VOXEL_FP32_C5 + gathered_h * BYTES_PER_VOXEL_FP16
-    achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    evals_per_voxel = evals / (n_hole * args.steps)
     line = {
-        "metric": METRIC, "value": sm[1] / (mx[0] / 1e3), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx[0] / args.steps,
+        "metric": METRIC, "value": hole_tot * args.steps / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "clips": len(clips), "voxels": n_vox, "hole_voxels": n_hole,
+        "config": {"workload": BATCH_WORKLOAD if len(clips) == 48 else f"{BATCH_WORKLOAD}[:{len(clips)}]",
+                   "clips": len(clips), "voxels": n_vox, "hole_voxels": n_hole,
                    "levels": "rule of Sec. 3.6 per clip", "channels": 5, "storage": args.storage,
+                   "sub_sweeps": args.sub_sweeps, "random_search": "eq3",
                    "parallelism": f"replicas x{world}", "lanes_per_target": args.lanes or "auto",
                    "rounds_per_step": rounds,
                    "l2": "inputs larger than L2: about 10 GB of clip state rebuilt every step"},
-        "inpainted_voxels_per_s": sm[2] * args.steps / (mx[0] / 1e3),
+        "evals_per_s": evals_tot / (ms_max / 1e3),
         "evals_per_step": evals / args.steps,
+        "evals_per_inpainted_voxel": evals_per_voxel,
+        "gathered_evals_per_s": (gathered * 20 + gathered_h * 8) / BYTES_PER_EVAL_FP32_C5 * world / (ms_max / 1e3),
         "screening": ({"screened": screened, "passed": passed,
                        "pass_rate": passed / screened if screened else None} if storage else None),
-        "single_clip_path": {"value": sm[4] / mx[3], "unit": UNIT,
-                             "inpainted_voxels_per_s": sm[2] / mx[3], "seconds": mx[3],
+        "single_clip_path": {"value": sm[2] / mx[3], "unit": UNIT, "evals_per_s": sm[4] / mx[3],
+                             "seconds": mx[3],
                              "note": "the same 48 clips one after another through vi_run; "
                                      "bit-identical results"},
-        "roofline": {"bound": "hbm", "kernel": "k_ann_step_batch + k_ann_step_batch_warp (PatchMatch step, all clips)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
-                     "traffic": None,
-                     "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
-                     "kernel_ms_share": step_ms / ms if ms > 0 else None},
+        "roofline": step_roofline(gathered, gathered_h, step_evals, step_ms, ms, peak, peak_kind,
+                                  "k_ann_step_batch_warp + k_ann_step_batch (PatchMatch step, all clips)",
+                                  step_traffic(args, BATCH_WORKLOAD, gathered, gathered_h, step_launches),
+                                  step_launches),
+        "e2e": {"value": hole_tot * e2e_steps / mx[5], "unit": UNIT,
+                "steps": e2e_steps,
+                "h2d_bytes_per_step": int(sum(c.rgb.nbytes + c.mask.nbytes for c in clips)),
+                "d2h_bytes_per_step": int(sum(c.rgb.nbytes for c in clips))},
+        "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(oracle_specs(BATCH_WORKLOAD), args.cpu_seconds, args.sub_sweeps,
+                                            evals_per_voxel, BATCH_WORKLOAD)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -725,8 +909,9 @@ def run_serve(args):
     achieved = gbytes / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     pct = lambda x, q: float(np.percentile(x, q, method="inverted_cdf"))  # noqa: E731
     line = {
-        "metric": METRIC, "value": sm[1] / mx[0], "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": sm[2] / mx[0], "unit": UNIT, "n_gpus": world,
         "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * mx[0],
+        "evals_per_s": sm[1] / mx[0],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": SERVE_WORKLOAD, "requests": n, "rate_per_s": args.rate,
@@ -742,7 +927,7 @@ def run_serve(args):
         "inpainted_voxels_per_s": sm[2] / mx[0],
         "requests_per_s": n * world / mx[0],
         "failed": failed, "max_concurrent": srv.max_concurrent, "rounds": rounds,
-        "plain_fp32_path": {"value": sm[4] / mx[3], "unit": UNIT,
+        "plain_fp32_path": {"value": sm[2] / mx[3], "unit": UNIT, "evals_per_s": sm[4] / mx[3],
                             "latency_s": {"p50": pct(lat1, 50), "p99": pct(lat1, 99),
                                           "max": float(lat1.max())},
                             "inpainted_voxels_per_s": sm[2] / mx[3],
@@ -755,7 +940,7 @@ def run_serve(args):
                       "unit_of_work": "gathered source voxel, 20 B (5 FP32 channels) or 8 B (FP16 copy of c0..c3)",
                       "kernel_ms_share": step_ms / (1e3 * wall) if wall > 0 else None}
                      if args.serve_backend == "batch" else None),
-        "e2e": {"value": sm[1] / mx[0], "unit": UNIT,
+        "e2e": {"value": sm[2] / mx[0], "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(v * 13 for v in vox)),
                 "d2h_bytes_per_step": int(sum(v * 12 for v in vox))},
         "clocks": clocks,
@@ -818,13 +1003,15 @@ def run_slabs(args):
     assert same, "slab result differs from vi_run"
     if rank != 0:
         return 0
-    line = {"metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    n_hole = int(clip.mask.sum())
+    line = {"metric": METRIC, "value": n_hole / (ms / 1e3), "unit": UNIT, "evals_per_s": evals / (ms / 1e3),
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "levels": clip.levels, "slabs": args.slabs,
                        "slab_devices": "all on this GPU, one stream"},
             "exchanged_bytes_per_step": nbytes, "identical_to_vi_run": same,
-            "vi_run": {"ms_per_step": ms1, "value": evals1 / (ms1 / 1e3), "unit": UNIT},
+            "vi_run": {"ms_per_step": ms1, "value": n_hole / (ms1 / 1e3), "unit": UNIT},
             "roofline": None, "note": "the coarsest level runs in every slab's context"}
     print(json.dumps(line), flush=True)
     return 0
@@ -837,9 +1024,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU baseline: seconds of oracle search per core")
+    ap.add_argument("--ref-seconds", type=float, default=2.0,
+                    help="--impl reference: seconds of oracle search per core and step")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=sorted(WORKLOADS) + [BATCH_WORKLOAD, SERVE_WORKLOAD])
+    ap.add_argument("--clips", type=int, default=48,
+                    help="batch: the first N of the 48 clips (a smaller case for profiling)")
     ap.add_argument("--slabs", type=int, default=1,
                     help="split one clip by frames over this many contexts on this GPU (vi_run_slabs)")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the stream")
@@ -865,11 +1057,13 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == BATCH_WORKLOAD:
+    if args.workload == BATCH_WORKLOAD and args.slabs <= 1:
         return run_batch(args)
     if args.workload == SERVE_WORKLOAD:
         return run_serve(args)
     if args.slabs > 1:
+        if args.workload not in WORKLOADS:
+            args.workload = "layered_320x240x60"
         return run_slabs(args)
     return run_gpu(args)
 

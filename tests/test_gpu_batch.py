@@ -101,8 +101,8 @@ def test_batch_multi_radius_search_equals_alone():
                 ctx.run()
                 want = ctx.fetch_result()
             assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
-        with pytest.raises(vi.ViError):
-            b.add(clips[0].rgb, clips[0].mask, sub_sweeps=2)
+        with pytest.raises(vi.ViError):   # a batch's clips share its propagation sweeps per iteration
+            b.add(clips[0].rgb, clips[0].mask, sub_sweeps=3)
 
 
 def test_warp_shared_batch_mixed_search_modes():

@@ -310,7 +310,10 @@ def test_end_to_end_energy_layered_two_levels():
         gphi, _ = ctx.get_nnf(0)
     es = {}
     for sched in ("JAC", "SEQ"):
-        prm = O.Params(seed=67, schedule=sched, fixed_outer=counts)
+        # the Jacobi oracle with the library's propagation sweeps per
+        # iteration; the sequential one as printed (one scan per iteration)
+        prm = O.Params(seed=67, schedule=sched, fixed_outer=counts,
+                       sub_sweeps=vi.default_config().sub_sweeps if sched == "JAC" else 1)
         _, pyr, before = O.inpaint(clip.rgb, clip.mask, 2, use_texture=True, prm=prm,
                                    return_levels=True)
         lv = pyr[0]
