@@ -112,6 +112,9 @@ def _declare(L):
     L.vio_ann2.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p, i, i, i, d,
                            u32, u32, u32, u32, i, i]
     L.vio_ann2.restype = C.c_longlong
+    L.vio_ann2_f64.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f64p, i, i, i, d,
+                               u32, u32, u32, u32, i, i]
+    L.vio_ann2_f64.restype = C.c_longlong
     L.vio_rescore.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p]
     L.vio_rescore.restype = C.c_longlong
     L.vio_ann_iteration.argtypes = [_f32p, i, i, i, i, _u8p, _OptU8, _u8p, _OptU8, _i32p, _f32p, i, i, d,
@@ -120,6 +123,9 @@ def _declare(L):
     L.vio_bruteforce_nn.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _OptU8, _i32p, _f32p]
     L.vio_vote.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _u8p, _i32p, _f32p, i, i, _OptU8]
     L.vio_vote.restype = d
+    L.vio_vote_f64.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _u8p, _i32p, _f64p, i, i, _OptU8]
+    L.vio_vote_f64.restype = d
+    L.vio_final_f64.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _i32p, _f64p]
     L.vio_final.argtypes = [_f32p, _f32p, i, i, i, i, _u8p, _i32p, _f32p]
     L.vio_energy.argtypes = [_f32p, i, i, i, i, _u8p, _u8p, _i32p, _f64p]
 
@@ -252,6 +258,8 @@ def ann(x, target, dtilde, phi, d2, n_pm=10, schedule="JAC", rmax=None, rho=0.5,
         key=(0, 0), tag_base=0, clip=0, excl=None, rs_mode=0, sub_sweeps=1):
     """Algorithm 1 in place on (phi, d2). Returns the number of distance
     evaluations. ``schedule``: "SEQ" (Algorithm 1 as printed) or "JAC".
+    ``d2`` float32: FP32 distances in the canonical summation order (the
+    GPU's); float64: distances and decisions in FP64 (the FP64 reference).
     ``rs_mode`` 0: one random candidate per k at radius r_max rho^k (Eq. 3);
     1: a candidate at every radius r_max rho^i >= 1 per k (the original
     PatchMatch search). ``sub_sweeps``: propagation sweeps before each random
@@ -259,12 +267,13 @@ def ann(x, target, dtilde, phi, d2, n_pm=10, schedule="JAC", rmax=None, rho=0.5,
     x = _c(x, np.float32)
     T, H, W, Cn = x.shape
     assert phi.dtype == np.int32 and phi.flags.c_contiguous
-    assert d2.dtype == np.float32 and d2.flags.c_contiguous
+    assert d2.dtype in (np.float32, np.float64) and d2.flags.c_contiguous
     if rmax is None:
         rmax = max(W, H, T)
     sched = {"SEQ": 0, "JAC": 1}[schedule]
     assert rs_mode in (0, 1) and sub_sweeps >= 1
-    return lib().vio_ann2(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
+    fn = lib().vio_ann2_f64 if d2.dtype == np.float64 else lib().vio_ann2
+    return fn(x.reshape(-1), W, H, T, Cn, _c(target, np.uint8).reshape(-1),
                           _c(dtilde, np.uint8).reshape(-1),
                           None if excl is None else _c(excl, np.uint8).reshape(-1),
                           phi.reshape(-1), d2.reshape(-1), int(n_pm), sched, int(rmax),
@@ -321,14 +330,17 @@ def bruteforce_nn(x, target, dtilde, excl=None):
 
 
 def vote(x, vote_mask, allowed, phi, d2, weighted=True, n_diff=3, want_deferred=False):
-    """Eq. 4/5 (Eq. 9, Eq. 12). Returns (x_new, change_sum[, deferred])."""
+    """Eq. 4/5 (Eq. 9, Eq. 12). Returns (x_new, change_sum[, deferred]).
+    Weights and sums in FP64; d2 float32 or float64."""
     x = _c(x, np.float32)
     T, H, W, Cn = x.shape
     out = np.empty_like(x)
     deferred = np.zeros((T, H, W), np.uint8) if want_deferred else None
-    ch = lib().vio_vote(x.reshape(-1), out.reshape(-1), W, H, T, Cn,
+    f64 = np.asarray(d2).dtype == np.float64
+    fn = lib().vio_vote_f64 if f64 else lib().vio_vote
+    ch = fn(x.reshape(-1), out.reshape(-1), W, H, T, Cn,
                         _c(vote_mask, np.uint8).reshape(-1), _c(allowed, np.uint8).reshape(-1),
-                        _c(phi, np.int32).reshape(-1), _c(d2, np.float32).reshape(-1),
+                        _c(phi, np.int32).reshape(-1), _c(d2, np.float64 if f64 else np.float32).reshape(-1),
                         1 if weighted else 0, int(n_diff),
                         None if deferred is None else deferred.reshape(-1))
     if want_deferred:
@@ -341,9 +353,10 @@ def final(x, hole, phi, d2):
     x = _c(x, np.float32)
     T, H, W, Cn = x.shape
     out = np.empty_like(x)
-    lib().vio_final(x.reshape(-1), out.reshape(-1), W, H, T, Cn,
-                    _c(hole, np.uint8).reshape(-1), _c(phi, np.int32).reshape(-1),
-                    _c(d2, np.float32).reshape(-1))
+    f64 = np.asarray(d2).dtype == np.float64
+    fn = lib().vio_final_f64 if f64 else lib().vio_final
+    fn(x.reshape(-1), out.reshape(-1), W, H, T, Cn, _c(hole, np.uint8).reshape(-1),
+       _c(phi, np.int32).reshape(-1), _c(d2, np.float64 if f64 else np.float32).reshape(-1))
     return out
 
 
@@ -378,6 +391,12 @@ class Params:
     rs_mode: int = 0           # 0: Eq. 3 (one radius per k); 1: every radius r_max rho^i >= 1
     sub_sweeps: int = 1        # propagation sweeps before each random search
     time_subsample: bool = False  # halve the frames at every pyramid level too (Sec. 3.6 option)
+    fp64: bool = False         # distances, stored distances and decisions in FP64 (the reference
+                               # the FP32 path's errors are stated against); the video stays FP32
+
+    @property
+    def d2_dtype(self):
+        return np.float64 if self.fp64 else np.float32
 
     @property
     def key(self):
@@ -538,7 +557,7 @@ def next_level(coarse, fine, prm, fine_index):
     u and T at the finer level (Eq. 4/5, Eq. 9)."""
     fine.phi = upsample_nnf(coarse.phi, fine.htilde, fine.dtilde, prm.key,
                             tag(PURPOSE_UPSAMPLE, fine_index), prm.clip, prm.time_subsample)
-    fine.d2 = np.full(fine.hole.shape, np.inf, np.float32)
+    fine.d2 = np.full(fine.hole.shape, np.inf, prm.d2_dtype)
     provisional_fill(coarse.x, fine.x, fine.hole, prm.time_subsample)
     ev = _rescore(fine, prm)
     fine.x, _ = vote(fine.x, fine.hole, fine.htilde, fine.phi, fine.d2,
@@ -556,7 +575,7 @@ def inpaint(rgb, mask, levels, use_texture=True, prm=None, return_levels=False):
     if top.dtilde.sum() == 0:
         raise ValueError("no valid source patch at the coarsest level")
     top.phi = init_nnf(top.htilde, top.dtilde, prm.key, tag(PURPOSE_INIT, L - 1), prm.clip)
-    top.d2 = np.full(top.hole.shape, np.inf, np.float32)
+    top.d2 = np.full(top.hole.shape, np.inf, prm.d2_dtype)
     onion_peel(top, prm, L - 1)
     before_final = None
     for i, lv_index in enumerate(range(L - 1, -1, -1)):

@@ -495,17 +495,27 @@ typedef struct {
     const float *x; int W, H, T, C;
     const uint8_t *target, *dtilde, *excl;
     long long evals;
+    int fp64;   /* 0: FP32 distances (the canonical order); 1: FP64 distances */
 } ann_ctx;
 
+/* The distance the search compares, held in double: the FP32 one converted
+ * exactly (so comparisons decide as in FP32), or the FP64 one. */
+static double ann_dist(const ann_ctx *a, int px, int py, int pt, int sx, int sy, int st)
+{
+    if (a->fp64)
+        return vio_dist_f64(a->x, a->W, a->H, a->T, a->C, px, py, pt, sx, sy, st, a->excl);
+    return (double)vio_dist_f32(a->x, a->W, a->H, a->T, a->C, px, py, pt, sx, sy, st, a->excl);
+}
+
 static void try_shift(ann_ctx *a, int px, int py, int pt, int cdx, int cdy, int cdt,
-                      int32_t *bphi, float *bd)
+                      int32_t *bphi, double *bd)
 {
     int sx = px + cdx, sy = py + cdy, st = pt + cdt;
     if (!inside(sx, sy, st, a->W, a->H, a->T))
         return;
     if (!a->dtilde[vidx(sx, sy, st, a->W, a->H)])
         return;
-    float d = vio_dist_f32(a->x, a->W, a->H, a->T, a->C, px, py, pt, sx, sy, st, a->excl);
+    double d = ann_dist(a, px, py, pt, sx, sy, st);
     a->evals++;
     if (d < *bd) {
         *bd = d;
@@ -514,14 +524,14 @@ static void try_shift(ann_ctx *a, int px, int py, int pt, int cdx, int cdy, int 
 }
 
 static void propagate_one(ann_ctx *a, size_t p, int k, const int32_t *phi_src,
-                          int32_t *phi, float *d2)
+                          int32_t *phi, double *d2)
 {
     int W = a->W, H = a->H, T = a->T;
     int px, py, pt;
     coords(p, W, H, &px, &py, &pt);
     int sgn = (k % 2 == 0) ? -1 : +1;
     int32_t best[3] = {phi[3 * p], phi[3 * p + 1], phi[3 * p + 2]};
-    float bd = d2[p];
+    double bd = d2[p];
     int nb[3][3] = {{px + sgn, py, pt}, {px, py + sgn, pt}, {px, py, pt + sgn}};
     for (int i = 0; i < 3; ++i) {
         int rx = nb[i][0], ry = nb[i][1], rt = nb[i][2];
@@ -544,12 +554,12 @@ static void propagate_one(ann_ctx *a, size_t p, int k, const int32_t *phi_src,
  * the best shift so far. */
 static void random_search_one(ann_ctx *a, size_t p, int k, int rmax, double rho, int rs_mode,
                               uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip,
-                              int32_t *phi, float *d2)
+                              int32_t *phi, double *d2)
 {
     int px, py, pt;
     coords(p, a->W, a->H, &px, &py, &pt);
     int32_t best[3] = {phi[3 * p], phi[3 * p + 1], phi[3 * p + 2]};
-    float bd = d2[p];
+    double bd = d2[p];
     for (int i = 0;; ++i) {
         double radius;
         uint32_t w[4];
@@ -582,14 +592,14 @@ static void random_search_one(ann_ctx *a, size_t p, int k, int rmax, double rho,
  * sweep started from). sub_sweeps >= 1 propagation sweeps (same direction)
  * run before the random search of each iteration k; rs_mode as in
  * random_search_one. */
-long long vio_ann2(const float *x, int W, int H, int T, int C,
-                   const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
-                   int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,
-                   uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip, int rs_mode,
-                   int sub_sweeps)
+static long long ann_core(const float *x, int W, int H, int T, int C,
+                          const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
+                          int32_t *phi, double *d2, int n_pm, int schedule, int rmax, double rho,
+                          uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip, int rs_mode,
+                          int sub_sweeps, int fp64)
 {
     size_t V = (size_t)W * H * T;
-    ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0};
+    ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0, fp64};
 
     /* distance of each target to its current correspondent */
     for (size_t p = 0; p < V; ++p) {
@@ -599,7 +609,7 @@ long long vio_ann2(const float *x, int W, int H, int T, int C,
         coords(p, W, H, &px, &py, &pt);
         int sx = px + phi[3 * p], sy = py + phi[3 * p + 1], st = pt + phi[3 * p + 2];
         if (inside(sx, sy, st, W, H, T) && dtilde[vidx(sx, sy, st, W, H)]) {
-            d2[p] = vio_dist_f32(x, W, H, T, C, px, py, pt, sx, sy, st, excl);
+            d2[p] = ann_dist(&a, px, py, pt, sx, sy, st);
             a.evals++;
         } else {
             d2[p] = INFINITY;
@@ -637,6 +647,51 @@ long long vio_ann2(const float *x, int W, int H, int T, int C,
     return a.evals;
 }
 
+/* FP32 distances in and out as float (exact both ways). */
+static double *widen(const float *d2, size_t V)
+{
+    double *w = (double *)malloc(V * sizeof(double));
+    if (w)
+        for (size_t v = 0; v < V; ++v)
+            w[v] = (double)d2[v];
+    return w;
+}
+
+static void narrow(const double *w, float *d2, size_t V)
+{
+    for (size_t v = 0; v < V; ++v)
+        d2[v] = (float)w[v];
+}
+
+long long vio_ann2(const float *x, int W, int H, int T, int C,
+                   const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
+                   int32_t *phi, float *d2, int n_pm, int schedule, int rmax, double rho,
+                   uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip, int rs_mode,
+                   int sub_sweeps)
+{
+    size_t V = (size_t)W * H * T;
+    double *w = widen(d2, V);
+    if (!w)
+        return -1;
+    long long n = ann_core(x, W, H, T, C, target, dtilde, excl, phi, w, n_pm, schedule, rmax, rho, key0, key1,
+                           tag_base, clip, rs_mode, sub_sweeps, 0);
+    narrow(w, d2, V);
+    free(w);
+    return n;
+}
+
+/* The same search with FP64 distances and decisions (d2 in double): the
+ * reference the FP32 path's errors are stated against. */
+long long vio_ann2_f64(const float *x, int W, int H, int T, int C,
+                       const uint8_t *target, const uint8_t *dtilde, const uint8_t *excl,
+                       int32_t *phi, double *d2, int n_pm, int schedule, int rmax, double rho,
+                       uint32_t key0, uint32_t key1, uint32_t tag_base, uint32_t clip, int rs_mode,
+                       int sub_sweeps)
+{
+    return ann_core(x, W, H, T, C, target, dtilde, excl, phi, d2, n_pm, schedule, rmax, rho, key0, key1,
+                    tag_base, clip, rs_mode, sub_sweeps, 1);
+}
+
 /* The two parts of vio_ann2's Jacobi schedule on their own, so that ranks
  * holding different targets can exchange shifts between iterations: the
  * distance of every target to its current correspondent (+inf where that is
@@ -672,21 +727,27 @@ long long vio_ann_iteration(const float *x, int W, int H, int T, int C, const ui
                             uint32_t tag_base, uint32_t clip, int rs_mode, int sub_sweeps)
 {
     size_t V = (size_t)W * H * T;
-    ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0};
+    ann_ctx a = {x, W, H, T, C, target, dtilde, excl, 0, 0};
     const uint8_t *mine = own ? own : target;
     int32_t *phi_old = (int32_t *)malloc(V * 3 * sizeof(int32_t));
-    if (!phi_old)
+    double *w = widen(d2, V);
+    if (!phi_old || !w) {
+        free(phi_old);
+        free(w);
         return -1;
+    }
     for (int j = 0; j < sub_sweeps; ++j) {
         memcpy(phi_old, phi, V * 3 * sizeof(int32_t));
         for (size_t p = 0; p < V; ++p)
             if (mine[p])
-                propagate_one(&a, p, k, phi_old, phi, d2);
+                propagate_one(&a, p, k, phi_old, phi, w);
     }
     for (size_t p = 0; p < V; ++p)
         if (mine[p])
-            random_search_one(&a, p, k, rmax, rho, rs_mode, key0, key1, tag_base, clip, phi, d2);
+            random_search_one(&a, p, k, rmax, rho, rs_mode, key0, key1, tag_base, clip, phi, w);
+    narrow(w, d2, V);
     free(phi_old);
+    free(w);
     return a.evals;
 }
 
@@ -750,9 +811,9 @@ static int cmp_double(const void *a, const void *b)
     return (x > y) - (x < y);
 }
 
-double vio_vote(const float *x_in, float *x_out, int W, int H, int T, int C,
-                const uint8_t *vote, const uint8_t *allowed, const int32_t *phi,
-                const float *d2, int weighted, int n_diff, uint8_t *deferred)
+static double vote_core(const float *x_in, float *x_out, int W, int H, int T, int C,
+                        const uint8_t *vote, const uint8_t *allowed, const int32_t *phi,
+                        const double *d2, int weighted, int n_diff, uint8_t *deferred)
 {
     size_t V = (size_t)W * H * T;
     memcpy(x_out, x_in, V * (size_t)C * sizeof(float));
@@ -776,7 +837,7 @@ double vio_vote(const float *x_in, float *x_out, int W, int H, int T, int C,
                     size_t q = vidx(qx, qy, qt, W, H);
                     if (!allowed[q] || !isfinite(d2[q]))
                         continue;
-                    dq[n] = (double)d2[q];
+                    dq[n] = d2[q];
                     srcv[n] = vidx(px + phi[3 * q], py + phi[3 * q + 1], pt + phi[3 * q + 2], W, H);
                     ++n;
                 }
@@ -815,11 +876,32 @@ double vio_vote(const float *x_in, float *x_out, int W, int H, int T, int C,
     return change;
 }
 
+double vio_vote(const float *x_in, float *x_out, int W, int H, int T, int C,
+                const uint8_t *vote, const uint8_t *allowed, const int32_t *phi,
+                const float *d2, int weighted, int n_diff, uint8_t *deferred)
+{
+    size_t V = (size_t)W * H * T;
+    double *w = widen(d2, V);
+    if (!w)
+        return NAN;
+    double r = vote_core(x_in, x_out, W, H, T, C, vote, allowed, phi, w, weighted, n_diff, deferred);
+    free(w);
+    return r;
+}
+
+/* The vote with distances in double (the FP64 reference). */
+double vio_vote_f64(const float *x_in, float *x_out, int W, int H, int T, int C,
+                    const uint8_t *vote, const uint8_t *allowed, const int32_t *phi,
+                    const double *d2, int weighted, int n_diff, uint8_t *deferred)
+{
+    return vote_core(x_in, x_out, W, H, T, C, vote, allowed, phi, d2, weighted, n_diff, deferred);
+}
+
 /* Final reconstruction, Eq. 6: p in H takes the value of its best contributor,
  * u(p + phi(q*)) with q* = argmin over q in N_p of d2[q] (ties: the first q in
  * the patch order dt, dy, dx ascending). */
-void vio_final(const float *x_in, float *x_out, int W, int H, int T, int C,
-               const uint8_t *hole, const int32_t *phi, const float *d2)
+static void final_core(const float *x_in, float *x_out, int W, int H, int T, int C,
+                       const uint8_t *hole, const int32_t *phi, const double *d2)
 {
     size_t V = (size_t)W * H * T;
     memcpy(x_out, x_in, V * (size_t)C * sizeof(float));
@@ -828,7 +910,7 @@ void vio_final(const float *x_in, float *x_out, int W, int H, int T, int C,
             continue;
         int px, py, pt;
         coords(p, W, H, &px, &py, &pt);
-        float bd = INFINITY;
+        double bd = INFINITY;
         long long best = -1;
         for (int dt = -R; dt <= R; ++dt)
             for (int dy = -R; dy <= R; ++dy)
@@ -847,6 +929,22 @@ void vio_final(const float *x_in, float *x_out, int W, int H, int T, int C,
         for (int c = 0; c < C; ++c)
             x_out[p * (size_t)C + c] = x_in[s * (size_t)C + c];
     }
+}
+
+void vio_final(const float *x_in, float *x_out, int W, int H, int T, int C,
+               const uint8_t *hole, const int32_t *phi, const float *d2)
+{
+    double *w = widen(d2, (size_t)W * H * T);
+    if (!w)
+        return;
+    final_core(x_in, x_out, W, H, T, C, hole, phi, w);
+    free(w);
+}
+
+void vio_final_f64(const float *x_in, float *x_out, int W, int H, int T, int C,
+                   const uint8_t *hole, const int32_t *phi, const double *d2)
+{
+    final_core(x_in, x_out, W, H, T, C, hole, phi, d2);
 }
 
 /* Energy, Eq. 1, evaluated in FP64: E_H = sum over p in H of d^2(W_p,

@@ -759,13 +759,18 @@ __global__ void __launch_bounds__(STEP_BLOCK, step_min_blocks<G, false>() * (256
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
         const int c = find_segment(prefix, n, g);
         const AnnArgs &a = (w.sweep & 1) ? clips[c].even : clips[c].odd;
-        ann_one<C5, G, false, F16>(a, g - __ldg(prefix + c), w.k, w.span, w.do_random != 0, sub, gmask, cnt);
+        const int i = g - __ldg(prefix + c);
+        if (i < a.nT)   // a clip's range is padded to whole warps
+            ann_one<C5, G, false, F16>(a, i, w.k, w.span, w.do_random != 0, sub, gmask, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, sub);
 }
 
 // Batch form of the warp-shared step: warp v of the grid-stride loop takes
-// the global targets [32 v, 32 v + 32), which may belong to several clips.
+// the global targets [32 v, 32 v + 32). Every clip's range starts on a whole
+// warp (the host pads the prefix sums to multiples of 32), so a warp holds
+// targets of one clip only and runs the single-clip form, the three
+// propagation candidates of its targets gathered in one round.
 template <bool C5, bool F16>
 __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
     k_ann_step_batch_warp(const BatchClip *__restrict__ clips, const int *__restrict__ prefix, int n, BatchSweep w,
@@ -776,12 +781,10 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
     const int warps = gridDim.x * (blockDim.x / 32);
     StepCount cnt;
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) / 32; v * 32 < total; v += warps) {
-        const int g = v * 32 + lane;
-        const bool active = g < total;
-        const int c = active ? find_segment(prefix, n, g) : 0;
+        const int c = find_segment(prefix, n, v * 32);
         const AnnArgs &a = (w.sweep & 1) ? clips[c].even : clips[c].odd;
-        ann_one_warp<C5, F16, true>(a, active, active ? g - __ldg(prefix + c) : 0, w.k, w.span, w.do_random != 0,
-                                    cnt);
+        const int i = v * 32 - __ldg(prefix + c) + lane;
+        ann_one_warp<C5, F16, false>(a, i < a.nT, i < a.nT ? i : 0, w.k, w.span, w.do_random != 0, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, 0);
 }

@@ -293,7 +293,9 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
             tpre_h[i] = (int)tot_t;
             hpre_h[i] = (int)tot_h;
             cpre_h[i] = (int)tot_c;
-            tot_t += act[i]->ctx->lv[act[i]->level].nT;
+            // each clip's target range starts on a whole warp, so that a warp of
+            // the step kernel holds targets of one clip (the kernels skip the padding)
+            tot_t += (act[i]->ctx->lv[act[i]->level].nT + 31) & ~31;
             tot_h += act[i]->ctx->lv[act[i]->level].nH;
             tot_c += sum_chunks(act[i]->ctx->lv[act[i]->level].nH);
         }

@@ -259,8 +259,11 @@ __global__ void __launch_bounds__(256, step_min_blocks<G, false>()) k_rescore_ba
     for (int g = (blockIdx.x * blockDim.x + threadIdx.x) / G; g < total; g += stride) {
         const int c = find_segment(prefix, n, g);
         const AnnArgs &a = clips[c].odd;
+        const int i = g - __ldg(prefix + c);
+        if (i >= a.nT)
+            continue;   // a clip's range is padded to whole warps
         const LevelView &L = a.L;
-        const int p = a.targets[g - __ldg(prefix + c)];
+        const int p = a.targets[i];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);
         const Shift f = a.phi_in[p];
