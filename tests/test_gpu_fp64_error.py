@@ -4,7 +4,8 @@ video between steps in FP32, as the input is): shift maps, distances, the
 vote and the final step of Eq. 6, and a whole inpainting. FP16 storage
 takes the FP32 path's decisions and votes from the FP32 channels, so its
 outputs are the FP32 path's bit for bit (tests/test_gpu_fp16.py checks
-that) and so are its errors; both storages run here. The figures are printed (pytest -s) and bounded:
+that) and so are its errors; both storages run here. The figures are printed
+(pytest -s) and bounded:
 
   - the shift map after one search agrees with the FP64 search on at least
     99% of the targets (FP32 rounding decides only near-ties);
