@@ -292,27 +292,11 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span
 // is the same as with a fixed G.
 // ---------------------------------------------------------------------------
 
-// The level view of lane o (a batch warp may hold targets of several clips):
-// the fields the distance and the screen read.
-__device__ __forceinline__ LevelView view_of_lane(const LevelView &L, int o)
-{
-    const unsigned FULL = 0xffffffffu;
-    LevelView v = L;
-    v.W = __shfl_sync(FULL, L.W, o);
-    v.H = __shfl_sync(FULL, L.H, o);
-    v.T = __shfl_sync(FULL, L.T, o);
-    v.HW = __shfl_sync(FULL, L.HW, o);
-    v.x4 = reinterpret_cast<float4 *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.x4), o));
-    v.x1 = reinterpret_cast<float *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.x1), o));
-    v.h4 = reinterpret_cast<uint2 *>(__shfl_sync(FULL, reinterpret_cast<unsigned long long>(L.h4), o));
-    return v;
-}
-
 // The pending candidates of mask M (owner lanes), G lanes each: group j
 // serves the owner holding the j-th set bit of M, with the owner's target,
-// source, bound and (MIXED: targets of several clips in the warp) level.
-// Returns, on each owner lane, its candidate's bounded distance (group_d2).
-template <bool C5, int G, bool MIXED>
+// source and bound. Returns, on each owner lane, its candidate's bounded
+// distance (group_d2).
+template <bool C5, int G>
 __device__ __forceinline__ float warp_serve_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                                int pt, int s, float best, unsigned &gathered)
 {
@@ -323,32 +307,31 @@ __device__ __forceinline__ float warp_serve_d2(const LevelView &L, unsigned M, i
     const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
               opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
     const float ob = __shfl_sync(FULL, best, o);
-    const LevelView OL = MIXED ? view_of_lane(L, o) : L;
     float dd = __int_as_float(0x7f800000);
     if (j < c)
-        dd = group_d2<C5, G, false>(OL, op, opx, opy, opt, os, nullptr, ob, lane & (G - 1), group_mask<G>(),
+        dd = group_d2<C5, G, false>(L, op, opx, opy, opt, os, nullptr, ob, lane & (G - 1), group_mask<G>(),
                                     gathered);
     const int r = __popc(M & ((1u << lane) - 1u));
     return __shfl_sync(FULL, dd, (r * G) & 31);
 }
 
-template <bool C5, bool MIXED>
+template <bool C5>
 __device__ __forceinline__ float warp_d2(const LevelView &L, unsigned M, int lane, int p, int px, int py, int pt,
                                          int s, float best, unsigned &gathered)
 {
     const int c = __popc(M);
     if (c > 16)
-        return warp_serve_d2<C5, 1, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 1>(L, M, lane, p, px, py, pt, s, best, gathered);
     if (c > 8)
-        return warp_serve_d2<C5, 2, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 2>(L, M, lane, p, px, py, pt, s, best, gathered);
     if (c > 4)
-        return warp_serve_d2<C5, 4, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
-    return warp_serve_d2<C5, 8, MIXED>(L, M, lane, p, px, py, pt, s, best, gathered);
+        return warp_serve_d2<C5, 4>(L, M, lane, p, px, py, pt, s, best, gathered);
+    return warp_serve_d2<C5, 8>(L, M, lane, p, px, py, pt, s, best, gathered);
 }
 
 // The FP16 screen (group_screen) of the pending candidates of M, the same way
 // (the owner's magnitude bound D too).
-template <bool C5, int G, bool MIXED>
+template <bool C5, int G>
 __device__ __forceinline__ bool warp_serve_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                                   int pt, int s, float best, float D, unsigned &gathered_h)
 {
@@ -359,26 +342,25 @@ __device__ __forceinline__ bool warp_serve_screen(const LevelView &L, unsigned M
     const int op = __shfl_sync(FULL, p, o), opx = __shfl_sync(FULL, px, o), opy = __shfl_sync(FULL, py, o),
               opt = __shfl_sync(FULL, pt, o), os = __shfl_sync(FULL, s, o);
     const float ob = __shfl_sync(FULL, best, o), oD = __shfl_sync(FULL, D, o);
-    const LevelView OL = MIXED ? view_of_lane(L, o) : L;
     int pass = 0;
     if (j < c)
-        pass = group_screen<C5, G>(OL, op, opx, opy, opt, os, ob, oD, lane & (G - 1), group_mask<G>(), gathered_h);
+        pass = group_screen<C5, G>(L, op, opx, opy, opt, os, ob, oD, lane & (G - 1), group_mask<G>(), gathered_h);
     const int r = __popc(M & ((1u << lane) - 1u));
     return __shfl_sync(FULL, pass, (r * G) & 31) != 0;
 }
 
-template <bool C5, bool MIXED>
+template <bool C5>
 __device__ __forceinline__ bool warp_screen(const LevelView &L, unsigned M, int lane, int p, int px, int py,
                                             int pt, int s, float best, float D, unsigned &gathered_h)
 {
     const int c = __popc(M);
     if (c > 16)
-        return warp_serve_screen<C5, 1, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 1>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
     if (c > 8)
-        return warp_serve_screen<C5, 2, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 2>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
     if (c > 4)
-        return warp_serve_screen<C5, 4, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
-    return warp_serve_screen<C5, 8, MIXED>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+        return warp_serve_screen<C5, 4>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
+    return warp_serve_screen<C5, 8>(L, M, lane, p, px, py, pt, s, best, D, gathered_h);
 }
 
 // One round of the propagation candidates of a warp: the pending (target,
@@ -387,7 +369,7 @@ __device__ __forceinline__ bool warp_screen(const LevelView &L, unsigned M, int 
 // M1; c: all of them), and group g of G lanes serves pair base + g with its
 // owner's target, source s[j] and bound. Each owner receives the distances
 // of its pairs served in this round into out[j].
-template <bool C5, int G, bool MIXED>
+template <bool C5, int G>
 __device__ __forceinline__ void multi_round(const LevelView &L, unsigned M0, unsigned M1, unsigned M2, int n0,
                                             int n1, int c, int base, int lane, int p, int px, int py, int pt,
                                             int s0, int s1, int s2, float best, float (&out)[3],
@@ -411,10 +393,9 @@ __device__ __forceinline__ void multi_round(const LevelView &L, unsigned M0, uns
               opt = __shfl_sync(FULL, pt, o);
     const int os0 = __shfl_sync(FULL, s0, o), os1 = __shfl_sync(FULL, s1, o), os2 = __shfl_sync(FULL, s2, o);
     const float ob = __shfl_sync(FULL, best, o);
-    const LevelView OL = MIXED ? view_of_lane(L, o) : L;
     float dd = __int_as_float(0x7f800000);
     if (q < c)
-        dd = group_d2<C5, G, false>(OL, op, opx, opy, opt, which == 0 ? os0 : which == 1 ? os1 : os2, nullptr, ob,
+        dd = group_d2<C5, G, false>(L, op, opx, opy, opt, which == 0 ? os0 : which == 1 ? os1 : os2, nullptr, ob,
                                     lane & (G - 1), group_mask<G>(), gathered);
     const unsigned lt = (1u << lane) - 1u;
     const int cap = 32 / G;
@@ -433,7 +414,7 @@ __device__ __forceinline__ void multi_round(const LevelView &L, unsigned M0, uns
 // each target's distance before them: one round when at most 32 are
 // pending (G lanes each, the most that still serve them all, up to 8),
 // else rounds of 32 with one lane each.
-template <bool C5, bool MIXED>
+template <bool C5>
 __device__ __forceinline__ void warp_d2_multi(const LevelView &L, unsigned M0, unsigned M1, unsigned M2, int lane,
                                               int p, int px, int py, int pt, int s0, int s1, int s2, float best,
                                               float (&out)[3], unsigned &gathered)
@@ -441,30 +422,29 @@ __device__ __forceinline__ void warp_d2_multi(const LevelView &L, unsigned M0, u
     const int n0 = __popc(M0), n1 = __popc(M1), c = n0 + n1 + __popc(M2);
     if (c > 16) {
         for (int base = 0; base < c; base += 32)
-            multi_round<C5, 1, MIXED>(L, M0, M1, M2, n0, n1, c, base, lane, p, px, py, pt, s0, s1, s2, best, out,
+            multi_round<C5, 1>(L, M0, M1, M2, n0, n1, c, base, lane, p, px, py, pt, s0, s1, s2, best, out,
                                       gathered);
     } else if (c > 8) {
-        multi_round<C5, 2, MIXED>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
+        multi_round<C5, 2>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
                                   gathered);
     } else if (c > 4) {
-        multi_round<C5, 4, MIXED>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
+        multi_round<C5, 4>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
                                   gathered);
     } else {
-        multi_round<C5, 8, MIXED>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
+        multi_round<C5, 8>(L, M0, M1, M2, n0, n1, c, 0, lane, p, px, py, pt, s0, s1, s2, best, out,
                                   gathered);
     }
 }
 
 // ann_one for the targets of a warp with warp-shared lanes: the whole warp
-// calls it, and lane l owns target i of the clip a describes when active (a
-// is only read when active; with MIXED the lanes may belong to different
-// clips of a batch). A single clip gathers the propagation candidates of all
-// its targets together and decides them in order (see below); a batch
-// judges them one neighbour at a time. Then each random-search stage offers
-// at most one candidate per target, judged against the running best as in
+// calls it, and lane l owns target i of the clip a describes when active (all
+// lanes of a warp belong to one clip; a batch pads every clip's range to whole
+// warps). The propagation candidates of all its targets are gathered together
+// and decided in order (see below). Then each random-search stage offers at
+// most one candidate per target, judged against the running best as in
 // ann_one. The warp leaves a stage loop together, when no lane has a stage
 // left.
-template <bool C5, bool F16, bool MIXED>
+template <bool C5, bool F16>
 __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int i, int k, int span, bool do_random,
                                              StepCount &n)
 {
@@ -505,90 +485,18 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
     }
     Rejected rej;
     const Shift start = cur;
-    if (MIXED) {
-        // batch: every candidate judged one stage at a time (the single-clip
-        // form below measured slower where warps mix clips)
-#pragma unroll 1
-        for (int stage = 0;; ++stage) {
-            int s = -1, cdx = 0, cdy = 0, cdt = 0;
-            bool skip = false;
-            // does this lane's target have a candidate at this stage
-            bool mine = active;
-            int ri = 0, sh = 0;
-            if (stage >= 3 && active) {
-                ri = stage - 3;
-                sh = a.rs_mode ? a.rho_log2 * ri : a.rho_log2 * k;
-                mine = do_random && (a.rs_mode ? (ri < 31 && sh <= 30 && (a.rmax >> sh) >= 1) : ri == 0);
-            }
-            if (!__any_sync(FULL, mine))
-                break;
-            if (stage < 3) {
-                // (a register array indexed by a loop variable would spill: select)
-                const Shift c = stage == 0 ? cn[0] : (stage == 1 ? cn[1] : cn[2]);
-                s = stage == 0 ? sn[0] : (stage == 1 ? sn[1] : sn[2]);
-                skip = stage == 0 ? stale[0] : (stage == 1 ? stale[1] : stale[2]);
-                cdx = c.dx;
-                cdy = c.dy;
-                cdt = c.dt;
-            } else if (mine) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)p, a.tag | (uint32_t)k, a.clip,
-                                                         a.rs_mode ? (uint32_t)ri : 0u),
-                                              a.key0, a.key1);
-                cdx = cur.dx + random_offset(w.x, a.rmax, sh + 24);
-                cdy = cur.dy + random_offset(w.y, a.rmax, sh + 24);
-                cdt = cur.dt + random_offset(w.z, a.rmax, sh + 24);
-                s = source_of(L, px, py, pt, cdx, cdy, cdt);
-            }
-            bool need = false;
-            unsigned long long key = 0;
-            if (active && s >= 0) {
-                ++n.evals;
-                if (!skip) {
-                    key = shift_key(cdx, cdy, cdt);
-                    need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
-                }
-            }
-            if (F16 && stage >= 3) {
-                const unsigned M = __ballot_sync(FULL, need);
-                if (M) {
-                    const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
-                    if (need) {
-                        ++n.screened;
-                        if (pass) {
-                            ++n.passed;
-                        } else {
-                            rej.add(key);
-                            need = false;
-                        }
-                    }
-                }
-            }
-            const unsigned M = __ballot_sync(FULL, need);
-            if (M) {
-                const float dd = warp_d2<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, n.gathered);
-                if (need) {
-                    if (dd < d) {
-                        d = dd;
-                        cur.dx = (short)cdx;
-                        cur.dy = (short)cdy;
-                        cur.dt = (short)cdt;
-                    } else {
-                        rej.add(key);
-                    }
-                }
-            }
-        }
-    } else {
-        // Propagation, single clip: the three neighbours' candidates are gathered
+    {
+        // Propagation: the three neighbours' candidates are gathered
         // together, each bounded by the distance the target had before them, and
         // then decided in order against the running best. A gather the bound
         // stopped is at or above every later best, and a completed one has the
         // exact distance, so the decisions are those of judging them one by one.
         // A candidate equal to the current shift, or to an earlier candidate of
         // the same target that is gathered, is decided by that one. (320x240x60:
-        // 18.5 against 19.9 ms per inpainting. In a batch, whose warps mix clips
-        // and need the level of every pair's owner, it measured slower, 1,392
-        // against 1,286 ms for 48 clips, so there the candidates go one by one.)
+        // 18.5 against 19.9 ms per inpainting; the 8-clip batch, its clips'
+        // ranges padded to whole warps: 252.9 against 263.8 ms per batch with
+        // the candidates judged one neighbour at a time in warps that mix
+        // clips.)
         {
             bool need[3] = {false, false, false};
             unsigned long long key[3] = {0ull, 0ull, 0ull};
@@ -613,7 +521,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
                            M2 = __ballot_sync(FULL, need[2]);
             if (M0 | M1 | M2) {
                 float dist[3] = {INF, INF, INF};
-                warp_d2_multi<C5, MIXED>(L, M0, M1, M2, lane, p, px, py, pt, sn[0], sn[1], sn[2], d, dist, n.gathered);
+                warp_d2_multi<C5>(L, M0, M1, M2, lane, p, px, py, pt, sn[0], sn[1], sn[2], d, dist, n.gathered);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     if (!need[j])
@@ -660,7 +568,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
             if (F16) {
                 const unsigned M = __ballot_sync(FULL, need);
                 if (M) {
-                    const bool pass = warp_screen<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
+                    const bool pass = warp_screen<C5>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
                     if (need) {
                         ++n.screened;
                         if (pass) {
@@ -674,7 +582,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
             }
             const unsigned M = __ballot_sync(FULL, need);
             if (M) {
-                const float dd = warp_d2<C5, MIXED>(L, M, lane, p, px, py, pt, s, d, n.gathered);
+                const float dd = warp_d2<C5>(L, M, lane, p, px, py, pt, s, d, n.gathered);
                 if (need) {
                     if (dd < d) {
                         d = dd;
@@ -734,7 +642,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK)) k_ann_step
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     StepCount n;
-    ann_one_warp<C5, F16, false>(a, i < a.nT, i, a.k, a.chg_span, a.do_random != 0, n);
+    ann_one_warp<C5, F16>(a, i < a.nT, i, a.k, a.chg_span, a.do_random != 0, n);
     flush_counts<F16>(a.evals, a.gathered, a.screen, n, 0);
 }
 
@@ -784,7 +692,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, 2 * (256 / STEP_BLOCK))
         const int c = find_segment(prefix, n, v * 32);
         const AnnArgs &a = (w.sweep & 1) ? clips[c].even : clips[c].odd;
         const int i = v * 32 - __ldg(prefix + c) + lane;
-        ann_one_warp<C5, F16, false>(a, i < a.nT, i < a.nT ? i : 0, w.k, w.span, w.do_random != 0, cnt);
+        ann_one_warp<C5, F16>(a, i < a.nT, i < a.nT ? i : 0, w.k, w.span, w.do_random != 0, cnt);
     }
     flush_counts<F16>(ctr, ctr + 1, ctr + 2, cnt, 0);
 }
