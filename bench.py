@@ -55,7 +55,12 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # sweeps per iteration). A run of the same configuration scales it by the
 # source voxels its launches gathered. Empty while the kernels have changed
 # since the capture.
-NCU_STEP_TRAFFIC = {}
+NCU_STEP_TRAFFIC = {
+    # 1,440 launches of one batch step of the first 8 clips (62.72 GB read +
+    # 2.32 GB written over 17.97 G gathered voxels), scaled to the 48 clips by
+    # gathered voxels (profiles/k_ann_step_batch_warp_batch48_8clips.md)
+    ("batch48", "fp32", 2): (62.72e9 + 2.32e9) / 17.97e9,
+}
 
 # What the ncu counters of the step kernel show binds it (the roofline object
 # reports the gather against the HBM copy bandwidth; this says what actually
@@ -687,28 +692,51 @@ def run_batch(args):
     rounds = (s1["rounds"] - s0["rounds"]) / args.steps
     step_launches = (s1["rounds"] - s0["rounds"]) * 10 * args.sub_sweeps   # n_pm sweeps x sub-sweeps per round
 
+    # where one step's time goes (one more step, outside the timed region):
+    # adding and preparing the clips (upload, pyramid, initialisation, onion
+    # peel), the rounds, fetching and removing
+    torch.cuda.synchronize()
+    phase = {}
+    t = time.perf_counter()
+    ids = [b.add(r, m, levels=0, seed=1503 + i, clip=i) for i, (r, m) in enumerate(dev)]
+    torch.cuda.synchronize()
+    phase["add_ms"] = 1e3 * (time.perf_counter() - t)
+    t = time.perf_counter()
+    b.run()
+    torch.cuda.synchronize()
+    phase["rounds_ms"] = 1e3 * (time.perf_counter() - t)
+    t = time.perf_counter()
+    for cid, o in zip(ids, outs):
+        b.fetch(cid, o)
+    for cid in ids:
+        b.remove(cid)
+    torch.cuda.synchronize()
+    phase["fetch_remove_ms"] = 1e3 * (time.perf_counter() - t)
+
     # end to end through host buffers: every step uploads its clips from
     # pinned host memory and fetches every result to pinned host memory
-    e2e_steps = max(1, min(args.steps, 5))
-    host_in = [(torch.from_numpy(c.rgb).pin_memory().numpy(), torch.from_numpy(c.mask).pin_memory().numpy())
-               for c in clips]
-    host_out = [torch.empty(c.rgb.shape, dtype=torch.float32).pin_memory().numpy() for c in clips]
-    step(host_in, host_out)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e_steps = 0 if args.device_only else max(1, min(args.steps, 5))
+    e2e_s = 0.0
+    if e2e_steps:
+        host_in = [(torch.from_numpy(c.rgb).pin_memory().numpy(), torch.from_numpy(c.mask).pin_memory().numpy())
+                   for c in clips]
+        host_out = [torch.empty(c.rgb.shape, dtype=torch.float32).pin_memory().numpy() for c in clips]
         step(host_in, host_out)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t
-    assert all((h == o.cpu().numpy()).all() for h, o in zip(host_out, outs)), "host and device runs differ"
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            step(host_in, host_out)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t
+        assert all((h == o.cpu().numpy()).all() for h, o in zip(host_out, outs)), "host and device runs differ"
 
     # the same clips one after another through the single-clip path
     torch.cuda.synchronize()
     t = time.perf_counter()
     single_evals = 0
-    for i, (r, m) in enumerate(dev):
+    for i, (r, m) in enumerate([] if args.device_only else dev):
         with vi.Context(seed=1503 + i, clip=i, stream=stream.cuda_stream, **kw) as ctx:
             ctx.upload(r, m)
             ctx.run()
@@ -743,24 +771,26 @@ def run_batch(args):
         "evals_per_step": evals / args.steps,
         "evals_per_inpainted_voxel": evals_per_voxel,
         "gathered_evals_per_s": (gathered * 20 + gathered_h * 8) / BYTES_PER_EVAL_FP32_C5 * world / (ms_max / 1e3),
+        "step_phases": phase,
         "screening": ({"screened": screened, "passed": passed,
                        "pass_rate": passed / screened if screened else None} if storage else None),
-        "single_clip_path": {"value": sm[2] / mx[3], "unit": UNIT, "evals_per_s": sm[4] / mx[3],
-                             "seconds": mx[3],
-                             "note": "the same 48 clips one after another through vi_run; "
-                                     "bit-identical results"},
+        "single_clip_path": ({"value": sm[2] / mx[3], "unit": UNIT, "evals_per_s": sm[4] / mx[3],
+                              "seconds": mx[3],
+                              "note": "the same clips one after another through vi_run; bit-identical results"}
+                             if not args.device_only else None),
         "roofline": step_roofline(gathered, gathered_h, step_evals, step_ms, ms, peak, peak_kind,
                                   "k_ann_step_batch_warp + k_ann_step_batch (PatchMatch step, all clips)",
                                   step_traffic(args, BATCH_WORKLOAD, gathered, gathered_h, step_launches),
                                   step_launches),
-        "e2e": {"value": hole_tot * e2e_steps / mx[5], "unit": UNIT,
-                "steps": e2e_steps,
-                "h2d_bytes_per_step": int(sum(c.rgb.nbytes + c.mask.nbytes for c in clips)),
-                "d2h_bytes_per_step": int(sum(c.rgb.nbytes for c in clips))},
+        "e2e": ({"value": hole_tot * e2e_steps / mx[5], "unit": UNIT,
+                 "steps": e2e_steps,
+                 "h2d_bytes_per_step": int(sum(c.rgb.nbytes + c.mask.nbytes for c in clips)),
+                 "d2h_bytes_per_step": int(sum(c.rgb.nbytes for c in clips))} if e2e_steps else None),
         "gpu_launches": launches,
+        "lanes_tuned": vi.tune_export().splitlines(),
         "clocks": clocks,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.device_only:
         line["cpu_baseline"] = cpu_baseline(oracle_specs(BATCH_WORKLOAD), args.cpu_seconds, args.sub_sweeps,
                                             evals_per_voxel, BATCH_WORKLOAD)
     print(json.dumps(line), flush=True)
@@ -1024,6 +1054,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--device-only", action="store_true",
+                    help="batch: time the device-resident steps only (no e2e, single-clip or CPU legs), "
+                         "for profiler runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU baseline: seconds of oracle search per core")
     ap.add_argument("--ref-seconds", type=float, default=2.0,

@@ -378,6 +378,23 @@ vi_status vi::ctx_ensure_partials(vi_ctx *ctx, int n) { return ensure_partials(c
 
 namespace {
 
+// The level rule of Sec. 3.6 for the largest per-frame extent of the hole: the
+// smallest L with ext / 2^(L-1) <= 9, keeping the next level's side >= 16.
+int levels_for_extent(int ext, int W, int H)
+{
+    int L = 1;
+    while (true) {
+        const int scale = 1 << (L - 1);
+        if ((ext + scale - 1) / scale <= 9)
+            break;
+        const int side = (std::min(W, H) + 2 * scale - 1) / (2 * scale);   // next level's side
+        if (side < 16 || L >= 15)
+            break;
+        ++L;
+    }
+    return L;
+}
+
 int host_auto_levels(const uint8_t *mask, int W, int H, int T)
 {
     int ext = 0;
@@ -395,17 +412,7 @@ int host_auto_levels(const uint8_t *mask, int W, int H, int T)
         if (x1 >= 0)
             ext = std::max(ext, std::max(x1 - x0 + 1, y1 - y0 + 1));
     }
-    int L = 1;
-    while (true) {
-        const int scale = 1 << (L - 1);
-        if ((ext + scale - 1) / scale <= 9)
-            break;
-        const int side = (std::min(W, H) + 2 * scale - 1) / (2 * scale);   // next level's side
-        if (side < 16 || L >= 15)
-            break;
-        ++L;
-    }
-    return L;
+    return levels_for_extent(ext, W, H);
 }
 
 }  // namespace
@@ -547,23 +554,36 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
     const size_t V0 = (size_t)ctx->V0;
     const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 
-    int L = ctx->cfg.levels;
-    if (L <= 0) {
-        if (ptr_is_device) {
-            std::vector<uint8_t> hm(V0);
-            CK(cudaMemcpyAsync(hm.data(), mask, V0, cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            L = host_auto_levels(hm.data(), W, H, T);
-        } else {
-            L = host_auto_levels(mask, W, H, T);
-        }
-    }
-    ctx->L = L;
-
     TRY(dalloc(ctx, &ctx->rgb, V0 * 3 * sizeof(float)));
     TRY(dalloc(ctx, &ctx->mask, V0));
     CK(cudaMemcpyAsync(ctx->rgb, rgb, V0 * 3 * sizeof(float), kind, ctx->stream));
     CK(cudaMemcpyAsync(ctx->mask, mask, V0, kind, ctx->stream));
+
+    int L = ctx->cfg.levels;
+    if (L <= 0) {
+        // the level rule from the hole's per-frame extents, found on the
+        // device (16 bytes per frame come back) instead of a scan of the mask
+        // on the host
+        int4 *ext_dev = nullptr;
+        TRY(dalloc(ctx, &ext_dev, sizeof(int4) * (size_t)T));
+        std::vector<int4> ext_host((size_t)T);
+        launch_mask_extents(ctx->mask, W, H, T, ext_dev, ctx->stream);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ext_host.data(), ext_dev, sizeof(int4) * (size_t)T, cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(ctx->stream);
+        dfree(ctx, ext_dev);
+        if (e != cudaSuccess)
+            return fail(ctx, VI_ERR_CUDA, std::string("vi_upload: ") + cudaGetErrorString(e));
+        int ext = 0;
+        for (const int4 &f : ext_host)
+            if (f.y >= 0)
+                ext = std::max(ext, std::max(f.y - f.x + 1, f.w - f.z + 1));
+        L = levels_for_extent(ext, W, H);
+    }
+    ctx->L = L;
     TRY(dalloc(ctx, &ctx->tmpA, V0));
     TRY(dalloc(ctx, &ctx->tmpB, V0));
     {

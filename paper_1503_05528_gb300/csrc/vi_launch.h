@@ -34,6 +34,8 @@ void launch_downsample(LevelView fine, LevelView coarse, int level, const float2
                        int H0, float sqrt_lambda, bool c5, bool tsub, cudaStream_t st);
 // code = H | H~ | D~ of a level from its occlusion bits (3 separable dilations).
 void launch_codes(LevelView L, uint8_t *tmp_a, uint8_t *tmp_b, cudaStream_t st);
+// out[t] = (x0, x1, y0, y1) of the occluded pixels of frame t ((W, -1, H, -1): none).
+void launch_mask_extents(const uint8_t *mask, int W, int H, int T, int4 *out, cudaStream_t st);
 // Raster-ordered compaction of {v : (flags[v] & bits) != 0} into list.
 // block_counts needs compact_blocks(V) + 1 ints; *count_dev receives the size.
 int compact_blocks(int V);

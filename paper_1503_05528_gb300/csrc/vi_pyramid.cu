@@ -269,6 +269,50 @@ __global__ void k_codes(LevelView L, const uint8_t *__restrict__ near)
     }
 }
 
+// Bounding box of the occluded pixels of every frame, for the level rule of
+// Sec. 3.6: out[t] = (x0, x1, y0, y1), or (W, -1, H, -1) for a frame without
+// one. One block per frame; the threads scan its pixels, then warp and block
+// reductions.
+__global__ void __launch_bounds__(512) k_mask_extents(const uint8_t *__restrict__ mask, int W, int H,
+                                                     int4 *__restrict__ out)
+{
+    const unsigned FULL = 0xffffffffu;
+    const uint8_t *m = mask + (size_t)blockIdx.x * W * H;
+    const int n = W * H;
+    int x0 = W, x1 = -1, y0 = H, y1 = -1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (m[i]) {
+            const int y = i / W, x = i - y * W;
+            x0 = min(x0, x);
+            x1 = max(x1, x);
+            y0 = min(y0, y);
+            y1 = max(y1, y);
+        }
+    x0 = __reduce_min_sync(FULL, x0);
+    x1 = __reduce_max_sync(FULL, x1);
+    y0 = __reduce_min_sync(FULL, y0);
+    y1 = __reduce_max_sync(FULL, y1);
+    __shared__ int4 part[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        part[warp] = make_int4(x0, x1, y0, y1);
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        const int4 v = lane < nw ? part[lane] : make_int4(W, -1, H, -1);
+        const int a = __reduce_min_sync(FULL, v.x), b = __reduce_max_sync(FULL, v.y),
+                  c = __reduce_min_sync(FULL, v.z), d = __reduce_max_sync(FULL, v.w);
+        if (lane == 0)
+            out[blockIdx.x] = make_int4(a, b, c, d);
+    }
+}
+
+void launch_mask_extents(const uint8_t *mask, int W, int H, int T, int4 *out, cudaStream_t st)
+{
+    VI_COUNT_LAUNCH();
+    k_mask_extents<<<T, 512, 0, st>>>(mask, W, H, out);
+}
+
 void launch_codes(LevelView L, uint8_t *tmp_a, uint8_t *tmp_b, cudaStream_t st)
 {
     const int grid = grid_for(L.V, 256);

@@ -34,6 +34,38 @@ __device__ __forceinline__ VoteLane vote_lane(int lane)
     return v;
 }
 
+// Sums six values over the warp and returns the sums on lane 0 (other lanes:
+// unspecified). A transposed butterfly: at xor 16 each lane keeps three of the
+// six values and sends the other three, at xor 8 two of its three (padded to
+// four), at xor 4 one of those two; xor 2 and xor 1 finish the sums, which
+// then sit on lanes 0, 4, 8, 16, 20 and 24. 13 shuffles and 8 adds instead of
+// six trees of 5 each.
+__device__ __forceinline__ void warp_sum6(float (&v)[6])
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float a[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float keep = b4 ? v[i + 3] : v[i];
+        const float send = b4 ? v[i] : v[i + 3];
+        a[i] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+    // values (b4 ? 3 : 0) + 0, 1, 2; the fourth slot is 0
+    const float c0 = (b3 ? a[2] : a[0]) + __shfl_xor_sync(FULL, b3 ? a[0] : a[2], 8);
+    const float c1 = (b3 ? 0.0f : a[1]) + __shfl_xor_sync(FULL, b3 ? a[1] : 0.0f, 8);
+    float r = (b2 ? c1 : c0) + __shfl_xor_sync(FULL, b2 ? c0 : c1, 4);
+    r += __shfl_xor_sync(FULL, r, 2);
+    r += __shfl_xor_sync(FULL, r, 1);
+    v[0] = r;
+    v[1] = __shfl_sync(FULL, r, 4);
+    v[2] = __shfl_sync(FULL, r, 8);
+    v[3] = __shfl_sync(FULL, r, 16);
+    v[4] = __shfl_sync(FULL, r, 20);
+    v[5] = __shfl_sync(FULL, r, 24);
+}
+
 // One warp per voxel p; lane l handles the q = p + offset of its offsets
 // (the q in N_p).
 //  1. each lane loads d2(q) of its contributors (q inside the video, allowed,
@@ -42,9 +74,10 @@ __device__ __forceinline__ VoteLane vote_lane(int lane)
 //     rank), found by a bitwise radix select over the IEEE bit patterns of the
 //     non-negative d2 with warp-wide counts;
 //  3. s_q = exp(-d2(q) / (2 sigma_p^2)) (limit 1/0 for sigma_p = 0; 1 when
-//     unweighted); each lane accumulates s_q u(p + phi(q)) over all channels;
-//  4. warp sums; lane 0 writes u(p) and stores |u_new - u_old| summed over
-//     R, G, B in the voxel's slot of partials.
+//     unweighted); each lane accumulates s_q u(p + phi(q)) over all channels,
+//     from the source voxels found in step 1;
+//  4. warp sums (warp_sum6); lane 0 writes u(p) and stores |u_new - u_old|
+//     summed over R, G, B in the voxel's slot of partials.
 // A voxel at least 2 from every border has its whole patch inside the video
 // and skips those tests.
 template <bool C5>
@@ -58,13 +91,13 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
         decode(p, L.W, L.HW, px, py, pt);
         const bool interior = px >= 2 && px < L.W - 2 && py >= 2 && py < L.H - 2 && pt >= 2 && pt < L.T - 2;
         float dq[4];
-        int qv[4];
+        int sv[4];   // source voxel p + phi(q) of each contributor
         unsigned okm = 0;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const unsigned o = vl.off[m];
             dq[m] = 0.0f;
-            qv[m] = 0;
+            sv[m] = 0;
             if (o) {
                 const int ox = (int)(o & 0xFFu) - 2, oy = (int)((o >> 8) & 0xFFu) - 2,
                           ot = (int)((o >> 16) & 0xFFu) - 2;
@@ -79,7 +112,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                         if (d < __int_as_float(0x7f800000) &&
                             inside(L, px + f.dx, py + f.dy, pt + f.dt)) {
                             dq[m] = d;
-                            qv[m] = q;
+                            sv[m] = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
                             okm |= 1u << m;
                         }
                     }
@@ -156,8 +189,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                     w = dq[m] > 0.0f ? expf(-(dq[m] * inv2s)) : 1.0f;   // inv2s may be +inf
                 else
                     w = (dq[m] == 0.0f) ? 1.0f : 0.0f;
-                const Shift f = a.phi[qv[m]];
-                const int s = p + (int)f.dt * L.HW + (int)f.dy * L.W + (int)f.dx;
+                const int s = sv[m];
                 const float4 v = L.x4[s];
                 n0 = fmaf(w, v.x, n0);
                 n1 = fmaf(w, v.y, n1);
@@ -167,13 +199,14 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
                     n4 = fmaf(w, L.x1[s], n4);
                 den += w;
             }
-            n0 = warp_sum(n0);
-            n1 = warp_sum(n1);
-            n2 = warp_sum(n2);
-            n3 = warp_sum(n3);
-            if (C5)
-                n4 = warp_sum(n4);
-            den = warp_sum(den);
+            float sums[6] = {n0, n1, n2, n3, n4, den};
+            warp_sum6(sums);
+            n0 = sums[0];
+            n1 = sums[1];
+            n2 = sums[2];
+            n3 = sums[3];
+            n4 = sums[4];
+            den = sums[5];
             if (lane == 0) {
                 const float4 old = L.x4[p];
                 const float4 nw = make_float4(n0 / den, n1 / den, n2 / den, n3 / den);
@@ -200,35 +233,20 @@ __global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
         vote_one<C5>(a, item, threadIdx.x & 31, vote_lane(threadIdx.x & 31));
 }
 
-// Batch form: warp g of the launch grid-strides over the occluded voxels of
-// all clips; clip c owns [prefix[c], prefix[c+1]).
+// Batch form: warp g takes occluded voxel g of the clips' concatenated lists
+// (clip c owns [prefix[c], prefix[c+1])), one voxel per warp as in k_vote. A
+// data-sized grid: a persistent grid-stride form sized for 8 resident blocks
+// per SM got 5 (46 registers), and its remaining blocks ran their whole share
+// of the voxels as a late second wave.
 template <bool C5>
 __global__ void __launch_bounds__(VOTE_BLOCK) k_vote_batch(const BatchClip *__restrict__ clips,
                                                            const int *__restrict__ prefix, int n)
 {
-    const VoteLane vl = vote_lane(threadIdx.x & 31);
-    const int total = __ldg(prefix + n);
-    const int nwarps = gridDim.x * VOTE_WARPS;
-    for (int g = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5); g < total; g += nwarps) {
-        const int c = find_segment(prefix, n, g);
-        vote_one<C5>(clips[c].vote, g - __ldg(prefix + c), threadIdx.x & 31, vl);
-    }
-}
-
-// One wave of VOTE_BLOCK blocks (8 per SM at the vote's register count), or
-// fewer when there is less work.
-static int vote_grid(long long items)
-{
-    static int sms = 0;
-    if (sms <= 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-    }
-    const long long need = (items + VOTE_WARPS - 1) / VOTE_WARPS;
-    const long long cap = (long long)sms * 8;
-    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
+    const int g = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5);
+    if (g >= __ldg(prefix + n))
+        return;
+    const int c = find_segment(prefix, n, g);
+    vote_one<C5>(clips[c].vote, g - __ldg(prefix + c), threadIdx.x & 31, vote_lane(threadIdx.x & 31));
 }
 
 void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int total_holes, bool c5,
@@ -236,8 +254,8 @@ void launch_vote_batch(const BatchClip *clips, const int *hprefix, int n, int to
 {
     if (total_holes <= 0 || n <= 0)
         return;
-    const int grid = vote_grid(total_holes);
     VI_COUNT_LAUNCH();
+    const int grid = blocks_for(total_holes, VOTE_WARPS);
     if (c5)
         k_vote_batch<true><<<grid, VOTE_BLOCK, 0, st>>>(clips, hprefix, n);
     else

@@ -406,3 +406,35 @@ def test_bad_arguments_are_rejected():
     with vi.Context(levels=1) as ctx:
         with pytest.raises(vi.ViError):
             ctx.ann(0, 0)          # no pyramid yet
+
+
+def test_level_rule_on_the_device_equals_the_host_rule():
+    # vi_upload with levels = 0 finds the hole's per-frame extents on the GPU;
+    # the level count must be the host rule's (vi_auto_levels) for every mask
+    rng = np.random.default_rng(17)
+    masks = []
+    for (W, H, T) in [(64, 48, 6), (200, 120, 9), (33, 170, 5), (640, 480, 3)]:
+        m = np.zeros((T, H, W), np.uint8)
+        masks.append(m.copy())                                   # no hole at all
+        for _ in range(3):
+            m = np.zeros((T, H, W), np.uint8)
+            for t in range(T):
+                if rng.random() < 0.3:
+                    continue                                     # frames without a hole
+                w, h = int(rng.integers(1, W)), int(rng.integers(1, H))
+                x, y = int(rng.integers(0, W - w + 1)), int(rng.integers(0, H - h + 1))
+                m[t, y:y + h, x:x + w] = 1                       # may touch the borders
+            masks.append(m)
+    masks.append(bench_clip_mask())                             # a layered tube of the batch
+    for m in masks:
+        T, H, W = m.shape
+        rgb = rng.random((T, H, W, 3), dtype=np.float32)
+        want = vi.auto_levels(m)
+        with vi.Context(levels=0, use_texture=0, seed=3) as ctx:
+            ctx.upload(rgb, m)
+            assert ctx.stats()["levels"] == want, (m.shape, int(m.sum()))
+
+
+def bench_clip_mask():
+    import bench
+    return bench.make_batch_clip(0, 0).mask
