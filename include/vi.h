@@ -568,6 +568,24 @@ const char *vi_batch_last_error(const vi_batch *b);
 vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, const uint8_t *mask,
                        int W, int H, int T, int ptr_is_device, int *id_out);
 
+/* Adds n clips at once: as n calls of vi_batch_add, except that the clips'
+ * uploads and preparations (pyramid, initialisation, onion peel: chains of
+ * small launches and synchronisations) run concurrently, each on a stream of
+ * its own from one of n_threads host threads (0: 8), and join the batch's
+ * stream when all are done. The copies start after everything queued on the
+ * batch's stream before the call; the call returns when every clip is
+ * prepared, so the inputs may then be reused. Per clip i: job_cfgs[i]
+ * (job_cfgs or job_cfgs[i] NULL: the batch's cfg), rgbs[i] / masks[i] of
+ * Ws[i] x Hs[i] x Ts[i] (all host or all device memory, ptr_is_device),
+ * ids_out[i] its id (-1 if it failed), status_out[i] (nullable array) its
+ * status. Results are those of adding the clips one by one. Returns VI_OK, or
+ * the first failing clip's status (its message in vi_batch_last_error); the
+ * other clips are added regardless. The paper has no counterpart (batching
+ * serves many clips on one GPU). */
+vi_status vi_batch_add_many(vi_batch *b, int n, const vi_config *const *job_cfgs, const float *const *rgbs,
+                            const uint8_t *const *masks, const int *Ws, const int *Hs, const int *Ts,
+                            int ptr_is_device, int n_threads, int *ids_out, vi_status *status_out);
+
 /* One round for every iterating clip (synchronises once). *n_active (nullable)
  * receives the number of clips still iterating afterwards. */
 vi_status vi_batch_step(vi_batch *b, int *n_active);

@@ -376,6 +376,18 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
 
 vi_status vi::ctx_ensure_partials(vi_ctx *ctx, int n) { return ensure_partials(ctx, n); }
 
+vi_status vi::ctx_adopt_stream(vi_ctx *ctx, cudaStream_t st)
+{
+    if (!ctx)
+        return VI_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->own_stream && ctx->stream)
+        CK(cudaStreamDestroy(ctx->stream));
+    ctx->stream = st;
+    ctx->own_stream = false;
+    return VI_OK;
+}
+
 namespace {
 
 // The level rule of Sec. 3.6 for the largest per-frame extent of the hole: the

@@ -16,9 +16,11 @@
 // kernels evaluate each target and voxel exactly as the single-clip ones do,
 // and e is reduced per clip with the same fixed-order sum.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "vi_ctx.h"
@@ -268,6 +270,130 @@ vi_status vi_batch_add(vi_batch *b, const vi_config *job_cfg, const float *rgb, 
     // host allocations proportional to the clip may throw; no exception crosses the C ABI
     try {
         return vi_batch_add_body(b, job_cfg, rgb, mask, W, H, T, ptr_is_device, id_out);
+    } catch (...) {
+        return VI_ERR_OOM;
+    }
+}
+
+// Upload and preparation of one clip of vi_batch_add_many on its context's own
+// stream, which first waits for everything the caller queued on the batch's
+// stream before the call (ready), so that the inputs are complete.
+static vi_status prepare_clip(vi_ctx *ctx, cudaEvent_t ready, int dev, const float *rgb, const uint8_t *mask, int W,
+                              int H, int T, int ptr_is_device)
+{
+    if (cudaSetDevice(dev) != cudaSuccess || cudaStreamWaitEvent(ctx->stream, ready, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ERR_CUDA;
+    }
+    vi_status s = vi_upload(ctx, rgb, mask, W, H, T, ptr_is_device);
+    if (s == VI_OK)
+        s = vi_prepare(ctx);
+    if (s == VI_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        s = VI_ERR_CUDA;
+    }
+    return s;
+}
+
+static vi_status vi_batch_add_many_body(vi_batch *b, int n, const vi_config *const *job_cfgs,
+                                        const float *const *rgbs, const uint8_t *const *masks, const int *Ws,
+                                        const int *Hs, const int *Ts, int ptr_is_device, int n_threads,
+                                        int *ids_out, vi_status *status_out)
+{
+    if (!b || n < 0 || (n > 0 && (!rgbs || !masks || !Ws || !Hs || !Ts || !ids_out)))
+        return VI_ERR_ARG;
+    if (n == 0)
+        return VI_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, VI_ERR_NO_DEVICE, "vi_batch_add_many: no CUDA device");
+    }
+    std::vector<vi_ctx *> ctxs((size_t)n, nullptr);
+    std::vector<vi_status> st((size_t)n, VI_OK);
+    for (int i = 0; i < n; ++i) {
+        ids_out[i] = -1;
+        vi_config cfg = (job_cfgs && job_cfgs[i]) ? *job_cfgs[i] : b->cfg;
+        if (cfg.use_texture != b->cfg.use_texture || cfg.n_pm != b->cfg.n_pm || cfg.storage != b->cfg.storage ||
+            cfg.sub_sweeps != b->cfg.sub_sweeps) {
+            st[(size_t)i] = VI_ERR_ARG;
+            continue;
+        }
+        // a stream of its own for the preparation (priority from the clip's config)
+        st[(size_t)i] = vi_ctx_create(&cfg, nullptr, &ctxs[(size_t)i]);
+    }
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        for (vi_ctx *c : ctxs)
+            vi_ctx_destroy(c);
+        if (ready)
+            cudaEventDestroy(ready);
+        return bfail(b, VI_ERR_CUDA, "vi_batch_add_many: event");
+    }
+    // the clips' uploads and preparations run concurrently, one worker thread
+    // each at a time: they are chains of small launches and synchronisations
+    // that would otherwise leave the GPU idle between them
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int i; (i = next.fetch_add(1)) < n;)
+            if (st[(size_t)i] == VI_OK)
+                st[(size_t)i] = prepare_clip(ctxs[(size_t)i], ready, dev, rgbs[i], masks[i], Ws[i], Hs[i], Ts[i],
+                                             ptr_is_device);
+    };
+    const int nt = std::max(1, std::min(n, n_threads > 0 ? n_threads : 8));
+    std::vector<std::thread> pool;
+    try {
+        for (int t = 1; t < nt; ++t)
+            pool.emplace_back(work);
+    } catch (...) {
+        // fewer threads than asked for: the calling thread does the rest
+    }
+    work();
+    for (std::thread &t : pool)
+        t.join();
+    cudaEventDestroy(ready);
+    // the prepared clips join the batch's stream and its rounds, in order
+    vi_status first = VI_OK;
+    for (int i = 0; i < n; ++i) {
+        vi_ctx *ctx = ctxs[(size_t)i];
+        vi_status s = st[(size_t)i];
+        if (s == VI_OK)
+            s = ctx_adopt_stream(ctx, b->stream);
+        if (s != VI_OK) {
+            if (first == VI_OK) {
+                first = s;
+                bfail(b, s, "vi_batch_add_many: clip " + std::to_string(i) + ": " +
+                                (ctx ? std::string(vi_last_error(ctx)) : std::string("bad configuration")));
+            }
+            vi_ctx_destroy(ctx);
+            if (status_out)
+                status_out[i] = s;
+            continue;
+        }
+        Entry c;
+        c.ctx = ctx;
+        c.id = b->next_id++;
+        c.level = ctx->L - 1;
+        b->clips.push_back(c);
+        ids_out[i] = c.id;
+        s = advance(b, b->clips.back());
+        if (status_out)
+            status_out[i] = s;
+        if (s != VI_OK && first == VI_OK)
+            first = s;
+    }
+    return first;
+}
+
+vi_status vi_batch_add_many(vi_batch *b, int n, const vi_config *const *job_cfgs, const float *const *rgbs,
+                            const uint8_t *const *masks, const int *Ws, const int *Hs, const int *Ts,
+                            int ptr_is_device, int n_threads, int *ids_out, vi_status *status_out)
+{
+    try {
+        return vi_batch_add_many_body(b, n, job_cfgs, rgbs, masks, Ws, Hs, Ts, ptr_is_device, n_threads, ids_out,
+                                      status_out);
     } catch (...) {
         return VI_ERR_OOM;
     }

@@ -140,4 +140,8 @@ namespace vi {
 vi_status ctx_fail(vi_ctx *ctx, vi_status st, const std::string &msg);
 // Grows ctx->partials to hold at least n floats.
 vi_status ctx_ensure_partials(vi_ctx *ctx, int n);
+// Moves a context onto stream st (which the caller keeps owning): its own
+// stream, if it had one, is drained and destroyed. Everything the context
+// queued before is complete when this returns.
+vi_status ctx_adopt_stream(vi_ctx *ctx, cudaStream_t st);
 }  // namespace vi

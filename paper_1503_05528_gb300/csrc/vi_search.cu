@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<G, false>()) k_rescore_ba
         const int i = g - __ldg(prefix + c);
         if (i >= a.nT)
             continue;   // a clip's range is padded to whole warps
-        const LevelView &L = a.L;
+        const LevelView L = a.L;   // a register copy (the batch kernels read a from global memory)
         const int p = a.targets[i];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);

@@ -85,7 +85,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
 {
     float change = 0.0f;
     {
-        const LevelView &L = a.L;
+        const LevelView L = a.L;   // a register copy (the batch kernels read a from global memory)
         const int p = a.list[item];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);

@@ -36,7 +36,7 @@ EXPORTS = [
     "vi_batch_create", "vi_batch_destroy", "vi_batch_last_error", "vi_batch_add", "vi_batch_step",
     "vi_batch_run", "vi_batch_poll", "vi_batch_fetch", "vi_batch_remove", "vi_batch_clip_stats",
     "vi_batch_get_stats", "vi_batch_screen_stats", "vi_batch_profile", "vi_batch_step_time",
-    "vi_batch_clip_ctx",
+    "vi_batch_clip_ctx", "vi_batch_add_many",
 ]
 
 
@@ -165,6 +165,7 @@ def _declare(L):
     L.vi_batch_remove.argtypes = [vp, i]
     L.vi_batch_clip_stats.argtypes = [vp, i, P(ViStats)]
     L.vi_batch_clip_ctx.argtypes = [vp, i, P(vp), P(i)]
+    L.vi_batch_add_many.argtypes = [vp, i, vp, vp, vp, P(i), P(i), P(i), i, i, P(i), P(i)]
     L.vi_batch_get_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
     L.vi_batch_screen_stats.argtypes = [vp, P(ull), P(ull), P(ull)]
     L.vi_batch_profile.argtypes = [vp, i]
@@ -468,6 +469,45 @@ class Batch:
         self._ck(self.lib.vi_batch_add(self.h, C.byref(cfg), pr, pm, W, H, T, dr, C.byref(cid)))
         self._keep[cid.value] = (rgb, mask, (T, H, W))
         return cid.value
+
+    def add_many(self, items, n_threads=0):
+        """Adds clips at once (vi_batch_add_many: uploads and preparations
+        run concurrently). items: (rgb, mask, job dict) per clip, all numpy
+        or all CUDA tensors. Returns the ids; raises ViError when a clip
+        fails (the others are added)."""
+        n = len(items)
+        if n == 0:
+            return []
+        cfgs = [default_config(**{**self.defaults, **job}) for _, _, job in items]
+        cfg_ptrs = (C.c_void_p * n)(*[C.addressof(c) for c in cfgs])
+        rgbs, masks, keep, dev = [], [], [], None
+        Ws, Hs, Ts = (C.c_int * n)(), (C.c_int * n)(), (C.c_int * n)()
+        for k, (rgb, mask, _) in enumerate(items):
+            if isinstance(rgb, np.ndarray):
+                rgb = np.ascontiguousarray(rgb, dtype=np.float32)
+            if isinstance(mask, np.ndarray):
+                mask = np.ascontiguousarray(mask, dtype=np.uint8)
+            pr, dr = _ptr(rgb)
+            pm, dm = _ptr(mask)
+            assert dr == dm and (dev is None or dev == dr), "all host or all device buffers"
+            dev = dr
+            T, H, W = mask.shape[:3]
+            Ws[k], Hs[k], Ts[k] = W, H, T
+            rgbs.append(pr)
+            masks.append(pm)
+            keep.append((rgb, mask, (T, H, W)))
+        ids = (C.c_int * n)()
+        sts = (C.c_int * n)()
+        st = self.lib.vi_batch_add_many(self.h, n, cfg_ptrs, (C.c_void_p * n)(*rgbs), (C.c_void_p * n)(*masks),
+                                        Ws, Hs, Ts, int(dev), int(n_threads), ids, sts)
+        for k in range(n):
+            if ids[k] >= 0:
+                self._keep[ids[k]] = keep[k]
+        if st != VI_OK:
+            err = ViError(st, self.lib.vi_batch_last_error(self.h).decode(errors="replace"))
+            err.ids, err.statuses = list(ids), list(sts)   # the clips that were added
+            raise err
+        return list(ids)
 
     def step(self):
         n = C.c_int(0)

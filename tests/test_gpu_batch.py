@@ -138,3 +138,50 @@ def test_batch_with_sub_sweeps_is_identical_to_vi_run(lanes):
                 outer = ctx.stats()["outer"]
             assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
             assert b.clip_stats(cid)["outer"] == outer
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_add_many_prepares_concurrently_with_the_same_results(device):
+    # vi_batch_add_many uploads and prepares the clips on streams of their own
+    # from several threads; every clip's result and iteration counts are the
+    # ones it gets alone through vi_run, bit for bit
+    clips = [_clip(s) for s in SPECS[:5]]
+    items = []
+    for i, c in enumerate(clips):
+        rgb, mask = (torch.from_numpy(c.rgb).cuda(), torch.from_numpy(c.mask).cuda()) if device else (c.rgb, c.mask)
+        items.append((rgb, mask, dict(levels=c.levels, seed=600 + i, clip=i)))
+    stream = torch.cuda.current_stream()
+    with vi.Batch(stream=stream.cuda_stream, lanes_per_target=32) as b:
+        ids = b.add_many(items, n_threads=3)
+        assert sorted(ids) == list(range(5))
+        b.run()
+        for i, (cid, c) in enumerate(zip(ids, clips)):
+            with vi.Context(levels=c.levels, seed=600 + i, clip=i) as ctx:
+                ctx.upload(c.rgb, c.mask)
+                ctx.run()
+                want = ctx.fetch_result()
+                outer = ctx.stats()["outer"]
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), i
+            assert b.clip_stats(cid)["outer"] == outer
+
+
+def test_add_many_reports_a_failing_clip_and_adds_the_others():
+    clips = [_clip(s) for s in SPECS[:3]]
+    bad = synth.Clip("all occluded", clips[0].rgb.copy(), np.ones_like(clips[0].mask), clips[0].levels, True)
+    items = [(c.rgb, c.mask, dict(levels=c.levels, seed=700 + i, clip=i)) for i, c in enumerate(clips)]
+    items.insert(1, (bad.rgb, bad.mask, dict(levels=bad.levels, seed=799, clip=9)))
+    with vi.Batch() as b:
+        with pytest.raises(vi.ViError) as e:
+            b.add_many(items)
+        ids = e.value.ids
+        assert ids[1] == -1 and all(x >= 0 for k, x in enumerate(ids) if k != 1)
+        assert e.value.statuses[1] != 0
+        b.run()
+        for k, (cid, (rgb, mask, job)) in enumerate(zip(ids, items)):
+            if k == 1:
+                continue
+            with vi.Context(**job) as ctx:
+                ctx.upload(rgb, mask)
+                ctx.run()
+                want = ctx.fetch_result()
+            assert (b.fetch(cid).view(np.uint32) == want.view(np.uint32)).all(), k
