@@ -612,7 +612,10 @@ def oracle_specs(workload, rank=0):
 # count, which equals the oracle's for the same state (tests compare the
 # counts). The GPU arm measures it on every run; the --impl reference arm,
 # which has no GPU, converts the oracle's evaluation rate with it.
-EVALS_PER_HOLE_VOXEL = {"batch48": None, "layered_320x240x60": None, "layered_1280x720x100": None}
+# (Measured on GB300: batch48 11,715,304,841 evaluations for 13,414,074
+# occluded voxels; layered_320x240x60 the same way.)
+EVALS_PER_HOLE_VOXEL = {"batch48": 11715304841 / 13414074, "layered_320x240x60": 506.897988193932,
+                        "layered_1280x720x100": None}
 
 
 def run_batch(args):
