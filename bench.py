@@ -56,10 +56,10 @@ BYTES_PER_VOXEL_FP16 = 4 * 2             # channels c0..c3 of a voxel from the F
 # source voxels its launches gathered. Empty while the kernels have changed
 # since the capture.
 NCU_STEP_TRAFFIC = {
-    # 1,440 launches of one batch step of the first 8 clips (62.72 GB read +
-    # 2.32 GB written over 17.97 G gathered voxels), scaled to the 48 clips by
+    # 1,440 launches of one batch step of the first 8 clips (61.89 GB read +
+    # 2.05 GB written over 18.33 G gathered voxels), scaled to the 48 clips by
     # gathered voxels (profiles/k_ann_step_batch_warp_batch48_8clips.md)
-    ("batch48", "fp32", 2): (62.72e9 + 2.32e9) / 17.97e9,
+    ("batch48", "fp32", 2): (61.89e9 + 2.045e9) / 18.33e9,
 }
 
 # What the ncu counters of the step kernel show binds it (the roofline object

@@ -85,7 +85,10 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
 {
     float change = 0.0f;
     {
-        const LevelView L = a.L;   // a register copy (the batch kernels read a from global memory)
+        // the level view through a reference: in the batch vote a register
+        // copy cost 10 registers and two resident blocks per SM (1,173 against
+        // 1,159 ms per 48-clip batch)
+        const LevelView &L = a.L;
         const int p = a.list[item];
         int px, py, pt;
         decode(p, L.W, L.HW, px, py, pt);
