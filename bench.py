@@ -420,7 +420,7 @@ def run_gpu(args):
     mask_d = torch.from_numpy(clip.mask).cuda()
     out_d = torch.empty_like(rgb_d)
     stream = torch.cuda.current_stream()
-    storage = 1 if args.storage == "fp16" else 0
+    storage = {"fp32": 0, "fp16": 1, "fp16-all": 2}[args.storage]
     ctx = vi.Context(levels=clip.levels, use_texture=1, seed=1503 + rank, clip=rank,
                      stream=stream.cuda_stream, lanes_per_target=args.lanes, storage=storage,
                      rs_mode=1 if args.rs_mode == "multi" else 0, sub_sweeps=args.sub_sweeps)
@@ -642,7 +642,7 @@ def run_batch(args):
     n_hole = sum(int(c.mask.sum()) for c in clips)
     n_vox = sum(int(c.mask.size) for c in clips)
     stream = torch.cuda.current_stream()
-    storage = 1 if args.storage == "fp16" else 0
+    storage = {"fp32": 0, "fp16": 1, "fp16-all": 2}[args.storage]
     kw = dict(levels=0, lanes_per_target=args.lanes, storage=storage, sub_sweeps=args.sub_sweeps)
     b = vi.Batch(stream=stream.cuda_stream, **kw)
     counter = vi.Context(**kw)      # reads the library's launch counter
@@ -852,7 +852,7 @@ def run_serve(args):
     vox = [int(pool[i % len(pool)].mask.size) for i in range(n)]
     stream = torch.cuda.current_stream()
     budget = int(args.hbm_budget_gb * (1 << 30))
-    storage = 1 if args.storage == "fp16" else 0
+    storage = {"fp32": 0, "fp16": 1, "fp16-all": 2}[args.storage]
     native = args.serve_backend == "native"
     if args.serve_backend == "batch":
         backend = CudaBackend(stream=stream.cuda_stream, levels=0, use_texture=1, storage=storage)
@@ -1082,8 +1082,9 @@ def main():
     ap.add_argument("--serve-backend", default="native", choices=["streams", "batch", "native"],
                     help="serving: one stream per request by size priority (Python front), one shared batch, "
                          "or the library server (vi_server_*)")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
-                    help="channel storage: fp32, or fp16 copies screened before the FP32 distance")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp16-all"],
+                    help="channel storage: fp32; fp16 copies that screen random-search candidates before the "
+                         "FP32 distance at levels larger than L2 (fp16) or at every level (fp16-all)")
     ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],
                     help="random search: one radius per iteration (Eq. 3) or every radius")
     ap.add_argument("--sub-sweeps", type=int, default=2,

@@ -74,13 +74,17 @@ typedef struct {
     int weighted;        /* 1: weights of Eq. 5; 0: the unweighted mean (s = 1) */
     int use_texture;     /* 1: C = 5 channels (Sec. 3.3); 0: RGB only (C = 3) */
     int storage;         /* 0: FP32 channels. 1: FP32 channels plus an FP16 copy
-                            of channels c0..c3 (8 B per voxel); the PatchMatch
-                            step screens each random-search candidate on that
-                            copy with a rigorous error bound and computes the
-                            FP32 distance only when the candidate could beat
-                            the current best, so results are identical to
-                            storage 0 (the paper fixes no storage precision;
-                            this is a speed option for clips larger than L2). */
+                            of channels c0..c3 (8 B per voxel); at a level
+                            whose FP32 channels are larger than the L2 cache
+                            the PatchMatch step screens each random-search
+                            candidate on that copy with a rigorous error bound
+                            and computes the FP32 distance only when the
+                            candidate could beat the current best (levels that
+                            fit in L2 are searched as with storage 0). 2: the
+                            same, screening at every level. Results are
+                            identical to storage 0 in every mode (the paper
+                            fixes no storage precision; this is a speed option
+                            for clips larger than L2). */
     uint64_t seed;       /* Philox4x32-10 key (key words: low, high 32 bits) */
     uint32_t clip;       /* Philox counter word 2: distinguishes clips in a batch */
     int lanes_per_target; /* GPU lanes sharing one target in the search kernels:

@@ -153,7 +153,7 @@ __device__ __forceinline__ void try_candidate_g(const AnnArgs &a, int p, int px,
     const unsigned long long key = shift_key(cdx, cdy, cdt);
     if (key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key))
         return;
-    if (F16) {
+    if (F16 && a.L.h4) {
         ++n.screened;
         if (!group_screen<C5, G>(a.L, p, px, py, pt, s, d, D, sub, gmask, n.gathered_h)) {
             rej.add(key);
@@ -183,7 +183,7 @@ __device__ __forceinline__ void ann_one(const AnnArgs &a, int i, int k, int span
                                         unsigned gmask, StepCount &n)
 {
     const LevelView L = a.L;   // a register copy (the batch kernels read a from global memory)
-    const float D = F16 ? screen_d2bound(L) : 0.0f;
+    const float D = (F16 && L.h4) ? screen_d2bound(L) : 0.0f;
     const int p = a.targets[i];
     int px, py, pt;
     decode(p, L.W, L.HW, px, py, pt);
@@ -464,7 +464,10 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
     const LevelView L = a.L;   // a register copy (the batch kernels read a from global memory)
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const float D = (F16 && active) ? screen_d2bound(L) : 0.0f;
+    // with FP16 storage, a level whose view carries no FP16 copy is searched
+    // without screening (warp-uniform: a warp holds targets of one clip)
+    const bool screen = F16 && L.h4 != nullptr;
+    const float D = (screen && active) ? screen_d2bound(L) : 0.0f;
     const float INF = __int_as_float(0x7f800000);
     int p = 0, px = 0, py = 0, pt = 0;
     Shift cur;
@@ -541,7 +544,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
                     need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
                 }
             }
-            if (F16 && stage >= 3) {
+            if (screen && stage >= 3) {
                 const unsigned M = __ballot_sync(FULL, need);
                 if (M) {
                     const bool pass = warp_screen<C5>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);
@@ -651,7 +654,7 @@ __device__ __forceinline__ void ann_one_warp(const AnnArgs &a, bool active, int 
                 key = shift_key(cdx, cdy, cdt);
                 need = !(key == shift_key(cur.dx, cur.dy, cur.dt) || rej.has(key));
             }
-            if (F16) {
+            if (screen) {
                 const unsigned M = __ballot_sync(FULL, need);
                 if (M) {
                     const bool pass = warp_screen<C5>(L, M, lane, p, px, py, pt, s, d, D, n.gathered_h);

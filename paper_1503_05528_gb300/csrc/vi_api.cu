@@ -171,7 +171,7 @@ vi_status check_config(vi_ctx *ctx, const vi_config *c)
     if (!(c->lambda >= 0.0f) || c->n_pm < 0 || c->n_pm > 255 || c->levels < 0 || c->levels > 15 ||
         c->rs_mode < 0 || c->rs_mode > 1 || c->sub_sweeps < 1 || c->sub_sweeps > 16 ||
         c->time_subsample < 0 || c->time_subsample > 1 ||
-        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage != 0 && c->storage != 1) ||
+        c->max_outer < 0 || c->max_outer > 65535 || !(c->stop >= 0.0f) || (c->storage < 0 || c->storage > 2) ||
         !(c->lanes_per_target == 0 || c->lanes_per_target == 1 || c->lanes_per_target == 2 ||
           c->lanes_per_target == 4 || c->lanes_per_target == 8 || c->lanes_per_target == 32))
         return fail(ctx, VI_ERR_ARG, "invalid vi_config field");
@@ -259,6 +259,8 @@ AnnArgs sweep_args(vi_ctx *ctx, int level, const int *targets, int nT, const uin
     Level &l = ctx->lv[level];
     AnnArgs a;
     a.L = l.view();
+    if (!screen_level(ctx, l))
+        a.L.h4 = nullptr;   // the search runs the FP32 kernels at this level
     a.targets = targets;
     a.nT = nT;
     a.phi_in = l.phi[s & 1];
@@ -375,6 +377,26 @@ vi_status vote_level(vi_ctx *ctx, int level, double *change_dev)
 }  // namespace
 
 vi_status vi::ctx_ensure_partials(vi_ctx *ctx, int n) { return ensure_partials(ctx, n); }
+
+bool vi::screen_level(const vi_ctx *ctx, const Level &l)
+{
+    if (ctx->cfg.storage == 2)
+        return true;
+    if (ctx->cfg.storage != 1)
+        return false;
+    static long long l2 = -1;
+    if (l2 < 0) {
+        int dev = 0, bytes = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess || bytes <= 0) {
+            cudaGetLastError();
+            bytes = 128 << 20;
+        }
+        l2 = bytes;
+    }
+    const long long channel_bytes = (long long)l.V * (ctx->c5 ? 20 : 16);
+    return channel_bytes > l2;
+}
 
 vi_status vi::ctx_adopt_stream(vi_ctx *ctx, cudaStream_t st)
 {
@@ -540,7 +562,7 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
         // x4, x1, code, 2 shift + 2 distance + 2 change-flag buffers, three lists (upper bound),
         // FP16 copies
         total += V * (16 + (c5 ? 4 : 0) + 1 + 16 + 8 + 2 + 12);
-        if (cfg && cfg->storage == 1)
+        if (cfg && cfg->storage != 0)
             total += V * 8 + 256;
         w = (w + 1) / 2;
         h = (h + 1) / 2;
@@ -627,7 +649,7 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
         if (ctx->c5)
             TRY(dalloc(ctx, &lv.x1, V * sizeof(float)));
         TRY(dalloc(ctx, &lv.code, V));
-        if (ctx->cfg.storage == 1) {
+        if (ctx->cfg.storage != 0) {
             TRY(dalloc(ctx, &lv.h4, V * sizeof(uint2)));
             TRY(dalloc(ctx, &lv.hmax, 8 * sizeof(unsigned)));
         }
@@ -710,7 +732,7 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         CK_LAUNCH();
     }
     // FP16 storage: the copies of every level and their magnitude bounds
-    for (int l = 0; l < ctx->L && ctx->cfg.storage == 1; ++l) {
+    for (int l = 0; l < ctx->L && ctx->cfg.storage != 0; ++l) {
         CK(cudaMemsetAsync(ctx->lv[l].hmax, 0, 8 * sizeof(unsigned), st));
         launch_shadow_all(ctx->lv[l].view(), st);
         CK_LAUNCH();
@@ -1137,7 +1159,7 @@ static vi_status vi_load_state_body(vi_ctx *ctx, int level, const void *buf, siz
     p += V * 3 * sizeof(int32_t);
     CK(cudaMemcpyAsync(l.phi[0], ph.data(), V * sizeof(Shift), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(l.d2[0], p, V * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    if (ctx->cfg.storage == 1) {
+    if (ctx->cfg.storage != 0) {
         // the FP16 copies and their magnitude bounds follow the loaded channels
         CK(cudaMemsetAsync(l.hmax, 0, 8 * sizeof(unsigned), ctx->stream));
         launch_shadow_all(l.view(), ctx->stream);

@@ -442,6 +442,8 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
             AnnArgs a;
             std::memset(&a, 0, sizeof(a));
             a.L = l.view();
+            if (!screen_level(ctx, l))
+                a.L.h4 = nullptr;   // this clip's search needs no FP16 screening at this level
             a.targets = l.targets;
             a.nT = l.nT;
             a.tmask = l.code;
@@ -519,7 +521,7 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
             w.sweep = sweep;
             w.span = j > 0 ? 1 : (k >= 3 && J + 1 <= 8 ? J + 1 : 0);
             w.do_random = j == J - 1;
-            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, w, c5, b->cfg.storage == 1, b->counters + 1,
+            launch_ann_step_batch(b->d_clips, tpre, n, (int)tot_t, w, c5, b->cfg.storage != 0, b->counters + 1,
                                   lanes, st);
             if (b->profiling)
                 BCK(cudaEventRecord(e1, st));

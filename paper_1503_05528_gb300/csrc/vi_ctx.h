@@ -140,6 +140,12 @@ namespace vi {
 vi_status ctx_fail(vi_ctx *ctx, vi_status st, const std::string &msg);
 // Grows ctx->partials to hold at least n floats.
 vi_status ctx_ensure_partials(vi_ctx *ctx, int n);
+// Whether the search screens candidates on the FP16 copies at this level:
+// always with storage 2; with storage 1 when the level's FP32 channels are
+// larger than the L2 cache (smaller levels are served by L2, where halving a
+// gather's bytes does not pay for the extra screening gather); never with
+// FP32 storage.
+bool screen_level(const vi_ctx *ctx, const Level &l);
 // Moves a context onto stream st (which the caller keeps owning): its own
 // stream, if it had one, is drained and destroyed. Everything the context
 // queued before is complete when this returns.

@@ -50,8 +50,8 @@ def _state(lv, seed, level, rnd):
     return x, phi, d2
 
 
-@pytest.mark.parametrize("lanes,storage,sub_sweeps", [(0, 0, 1), (1, 0, 1), (32, 0, 1), (0, 1, 1), (32, 1, 1),
-                                                      (0, 0, 2), (32, 0, 2), (32, 1, 2), (1, 0, 3)])
+@pytest.mark.parametrize("lanes,storage,sub_sweeps", [(0, 0, 1), (1, 0, 1), (32, 0, 1), (0, 2, 1), (32, 2, 1),
+                                                      (0, 0, 2), (32, 0, 2), (32, 2, 2), (32, 1, 2), (1, 0, 3)])
 def test_batch_rounds_match_oracle_search_and_vote(lanes, storage, sub_sweeps):
     clips = _clips()
     pyrs = [O.build_pyramid(c.rgb, c.mask, c.levels, True) for c in clips]

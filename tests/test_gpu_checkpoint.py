@@ -50,7 +50,7 @@ def _resume(c, level, k0, state, **cfg):
         return r.fetch_result(), r.stats()["outer"]
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 2])
 def test_resume_at_every_level(storage):
     c = synth.layered_clip(96, 64, 16, 2, (10, 20), 0.08, 3, 1901)
     cfg = dict(levels=3, seed=77, clip=2, storage=storage)

@@ -1,10 +1,12 @@
-"""FP16 storage (vi_config.storage = 1). The PatchMatch step screens every
-candidate on FP16 copies of the channels under a rigorous error bound and
-takes its decision on the FP32 distance, so shift maps, distances and
-evaluation counts equal the oracle's bit for bit, and whole runs equal the
-FP32-storage runs bit for bit. The screening must reject most candidates
-(that is its point) and must let every candidate through when the channel
-magnitudes leave the FP16 range."""
+"""FP16 storage (vi_config.storage = 2: screening at every level; storage 1
+screens only levels larger than the L2 cache, so these small clips run it as
+FP32). The PatchMatch step screens the random-search candidates on FP16
+copies of the channels under a rigorous error bound and takes its decision
+on the FP32 distance, so shift maps, distances and evaluation counts equal
+the oracle's bit for bit, and whole runs equal the FP32-storage runs bit for
+bit. The screening must reject most candidates (that is its point) and must
+let every candidate through when the channel magnitudes leave the FP16
+range."""
 import numpy as np
 import pytest
 
@@ -37,7 +39,7 @@ def _make(case, seed, n_pm=10, lanes=0):
     spec = CASES[case]
     clip = spec["clip"]()
     pyr = O.build_pyramid(clip.rgb, clip.mask, spec["levels"], spec["tex"])
-    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=1, sub_sweeps=2,
+    ctx = vi.Context(levels=spec["levels"], use_texture=int(spec["tex"]), seed=seed, n_pm=n_pm, storage=2, sub_sweeps=2,
                      lanes_per_target=lanes)
     ctx.upload(clip.rgb, clip.mask)
     ctx.build_pyramid()
@@ -129,7 +131,9 @@ def test_run_fp16_equals_fp32(which):
             "fast": lambda: synth.fast_layered_clip(160, 96, 20, 0.06, seed=1602),
             "tiny": lambda: synth.tiny_translation_clip()}[which]()
     a = _run(clip, 0, 77, 1)
-    b = _run(clip, 1, 77, 1)
+    b = _run(clip, 2, 77, 1)      # screening at every level
+    c = _run(clip, 1, 77, 1)      # screening where a level exceeds L2: none of these
+    assert (a[0].view(np.uint32) == c[0].view(np.uint32)).all() and c[3]["screened"] == 0
     assert (a[0].view(np.uint32) == b[0].view(np.uint32)).all()
     assert (a[1] == b[1]).all() and (a[2].view(np.uint32) == b[2].view(np.uint32)).all()
     assert a[3]["outer"] == b[3]["outer"] and a[3]["evals"] == b[3]["evals"]
@@ -142,7 +146,7 @@ def test_run_fp16_equals_fp32(which):
 def test_batch_fp16_equals_alone_fp32():
     clips = [synth.fast_layered_clip(W, H, T, f, seed=1700 + i)
              for i, (W, H, T, f) in enumerate([(96, 64, 12, 0.06), (72, 56, 16, 0.08), (128, 80, 10, 0.05)])]
-    with vi.Batch(levels=0, storage=1) as b:
+    with vi.Batch(levels=0, storage=2) as b:
         ids = [b.add(c.rgb, c.mask, seed=90 + i, clip=i) for i, c in enumerate(clips)]
         b.run()
         for i, (cid, c) in enumerate(zip(ids, clips)):

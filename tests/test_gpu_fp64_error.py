@@ -51,7 +51,7 @@ def _d2_f64(x, phi, mask):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 2])
 def test_step_outputs_against_fp64(case, storage):
     clip = CASES[case]()
     lv = O.build_pyramid(clip.rgb, clip.mask, 1, True)[0]
@@ -101,7 +101,7 @@ def test_step_outputs_against_fp64(case, storage):
     assert dv.max() <= 1e-4 * math.sqrt(50.0) and dv[:, :3].max() <= 1e-4
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 2])
 def test_whole_inpainting_against_fp64(storage):
     clip = CASES["layered_72x56x14"]()
     L = 2

@@ -1,4 +1,7 @@
-"""Time slabs (vi_run_slabs) against the oracle rather than against vi_run:
+"""Whole inpaintings against the oracle rather than against vi_run: time slabs
+(vi_run_slabs), vi_run itself, the native request server and a batch.
+
+Time slabs (vi_run_slabs) against the oracle rather than against vi_run:
 a whole inpainting split by frames over 2 and 3 contexts, on two- and
 three-level clips, is compared voxel by voxel with the oracle's inpainting
 (Algorithm 4 with the Jacobi schedule, the same propagation sweeps, Philox
@@ -54,3 +57,48 @@ def test_slabbed_inpainting_matches_the_oracle(name, make, levels, n, seed):
     assert float(d.mean()) <= 1e-5
     known = ~h
     assert (got[known] == c.rgb[known]).all()
+
+
+def _oracle_for(c, levels, seed, clip, outer):
+    cfg = vi.default_config()
+    prm = O.Params(seed=seed, clip=clip, sub_sweeps=cfg.sub_sweeps,
+                   fixed_outer=[outer[lv] for lv in range(levels - 1, -1, -1)])
+    return O.inpaint(c.rgb, c.mask, levels, True, prm)
+
+
+def _close(got, want, mask, tag):
+    h = mask == 1
+    d = np.abs(got[h] - want[h]).max(axis=-1)
+    frac = float(np.mean(d <= 1e-4))
+    print(f"\n{tag}: voxels within 1e-4: {frac:.5f}; mean |diff| {float(d.mean()):.2e}")
+    assert frac >= 0.999 and float(d.mean()) <= 1e-5
+
+
+def test_run_server_and_batch_match_the_oracle():
+    # the whole method through vi_run, through the native request server and
+    # through a batch round loop, each against the oracle's inpainting with
+    # the per-level iteration counts vi_run's stopping rule chose (the server
+    # and the batch take the same decisions as vi_run)
+    clips = [synth.small_layered(W=72, H=56, T=14, levels=2, seed=1711),
+             synth.small_layered(W=56, H=48, T=10, levels=2, seed=1712)]
+    runs = []
+    for i, c in enumerate(clips):
+        with vi.Context(levels=2, seed=80 + i, clip=i) as ctx:
+            ctx.upload(c.rgb, c.mask)
+            ctx.run()
+            runs.append((ctx.fetch_result(), ctx.stats()["outer"][:2]))
+    with vi.Server(hbm_budget=8 << 30, max_slots=2) as srv:
+        tickets = [srv.submit(c.rgb, c.mask, levels=2, seed=80 + i, clip=i) for i, c in enumerate(clips)]
+        served = []
+        for t in tickets:
+            srv.wait(t)
+            served.append(srv.release(t))
+    with vi.Batch(levels=2) as b:
+        ids = b.add_many([(c.rgb, c.mask, dict(levels=2, seed=80 + i, clip=i)) for i, c in enumerate(clips)])
+        b.run()
+        batched = [b.fetch(cid) for cid in ids]
+    for i, c in enumerate(clips):
+        want = _oracle_for(c, 2, 80 + i, i, runs[i][1])
+        _close(runs[i][0], want, c.mask, f"clip {i} vi_run")
+        _close(served[i], want, c.mask, f"clip {i} server")
+        _close(batched[i], want, c.mask, f"clip {i} batch")
