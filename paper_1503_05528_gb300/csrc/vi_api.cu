@@ -258,9 +258,7 @@ AnnArgs sweep_args(vi_ctx *ctx, int level, const int *targets, int nT, const uin
 {
     Level &l = ctx->lv[level];
     AnnArgs a;
-    a.L = l.view();
-    if (!screen_level(ctx, l))
-        a.L.h4 = nullptr;   // the search runs the FP32 kernels at this level
+    a.L = l.view();   // h4 set only at a level the search screens (screen_level)
     a.targets = targets;
     a.nT = nT;
     a.phi_in = l.phi[s & 1];
@@ -649,7 +647,9 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
         if (ctx->c5)
             TRY(dalloc(ctx, &lv.x1, V * sizeof(float)));
         TRY(dalloc(ctx, &lv.code, V));
-        if (ctx->cfg.storage != 0) {
+        if (screen_level(ctx, lv)) {
+            // FP16 copies only where the search screens with them: a level
+            // that is never screened needs neither the copy nor its upkeep
             TRY(dalloc(ctx, &lv.h4, V * sizeof(uint2)));
             TRY(dalloc(ctx, &lv.hmax, 8 * sizeof(unsigned)));
         }
@@ -731,8 +731,10 @@ vi_status vi_build_pyramid(vi_ctx *ctx)
         launch_codes(ctx->lv[l].view(), ctx->tmpA, ctx->tmpB, st);
         CK_LAUNCH();
     }
-    // FP16 storage: the copies of every level and their magnitude bounds
-    for (int l = 0; l < ctx->L && ctx->cfg.storage != 0; ++l) {
+    // FP16 storage: the copies of the screened levels and their magnitude bounds
+    for (int l = 0; l < ctx->L; ++l) {
+        if (!ctx->lv[l].h4)
+            continue;
         CK(cudaMemsetAsync(ctx->lv[l].hmax, 0, 8 * sizeof(unsigned), st));
         launch_shadow_all(ctx->lv[l].view(), st);
         CK_LAUNCH();
@@ -1159,7 +1161,7 @@ static vi_status vi_load_state_body(vi_ctx *ctx, int level, const void *buf, siz
     p += V * 3 * sizeof(int32_t);
     CK(cudaMemcpyAsync(l.phi[0], ph.data(), V * sizeof(Shift), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(l.d2[0], p, V * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    if (ctx->cfg.storage != 0) {
+    if (l.h4) {
         // the FP16 copies and their magnitude bounds follow the loaded channels
         CK(cudaMemsetAsync(l.hmax, 0, 8 * sizeof(unsigned), ctx->stream));
         launch_shadow_all(l.view(), ctx->stream);

@@ -441,9 +441,7 @@ static vi_status vi_batch_step_body(vi_batch *b, int *n_active)
             BatchClip &bc = b->h_clips[i];
             AnnArgs a;
             std::memset(&a, 0, sizeof(a));
-            a.L = l.view();
-            if (!screen_level(ctx, l))
-                a.L.h4 = nullptr;   // this clip's search needs no FP16 screening at this level
+            a.L = l.view();   // h4 set only at a level the search screens (screen_level)
             a.targets = l.targets;
             a.nT = l.nT;
             a.tmask = l.code;
