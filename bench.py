@@ -4,11 +4,13 @@
 Default workload (batch48): 48 synthetic layered-motion clips of uneven sizes
 (W ~ logU[160, 640], H ~ logU[120, 480], frames ~ logU[20, 80], 3-12%
 occlusion tubes; 163M voxels, levels by the rule of Sec. 3.6), inpainted as
-one batch through the C ABI (vi_batch_add / vi_batch_run / vi_batch_fetch /
-vi_batch_remove): pyramids and features, initialisations, onion peels, per
-level the PatchMatch search and reconstruction rounds until each clip's
-stopping rule, level transitions and the final best-patch step. A step is
-the whole batch. --workload layered_320x240x60 / layered_1280x720x100 runs one
+one batch through the C ABI (vi_batch_add_many / vi_batch_run /
+vi_batch_fetch / vi_batch_remove): pyramids and features, initialisations,
+onion peels, per level the PatchMatch search and reconstruction rounds until
+each clip's stopping rule, level transitions and the final best-patch step.
+A step is the whole batch. Storage: FP16 copies screening the random-search
+candidates at levels larger than L2 (--storage fp16, the default; results
+identical to --storage fp32). --workload layered_320x240x60 / layered_1280x720x100 runs one
 clip per step through vi_run; serve_poisson4 the serving stream.
 
 Output: one JSON line (rank 0). `value` is inpainted (occluded) voxels per
@@ -1082,7 +1084,7 @@ def main():
     ap.add_argument("--serve-backend", default="native", choices=["streams", "batch", "native"],
                     help="serving: one stream per request by size priority (Python front), one shared batch, "
                          "or the library server (vi_server_*)")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "fp16-all"],
+    ap.add_argument("--storage", default="fp16", choices=["fp32", "fp16", "fp16-all"],
                     help="channel storage: fp32; fp16 copies that screen random-search candidates before the "
                          "FP32 distance at levels larger than L2 (fp16) or at every level (fp16-all)")
     ap.add_argument("--rs-mode", default="eq3", choices=["eq3", "multi"],
