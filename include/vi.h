@@ -306,10 +306,10 @@ vi_status vi_energy(vi_ctx *ctx, int level, double *E_H_host, double *E_Ht_host)
  * reloads the array: make the first call after a reset before any capture
  * too). A target counts when its source patch lies inside the video, whether
  * or not the source is in D~, exactly as in vi_energy: Eq. 1 is the energy of
- * any shift map; a source patch leaving the video gives +inf. Every call shares the
- * array, so calls that overlap on the GPU race; calls ordered on one stream
- * do not (each reads back only what it has just written). Asynchronous: the
- * result is in out_dev once the stream reaches it. Errors: VI_ERR_ARG (null
+ * any shift map; a source patch leaving the video gives +inf. Every call
+ * shares the array, so calls that overlap on the GPU race; calls ordered on
+ * one stream do not (each reads back only what it has just written).
+ * Asynchronous: the result is in out_dev once the stream reaches it. Errors: VI_ERR_ARG (null
  * pointer, C, sizes), VI_ERR_TOO_LARGE, VI_ERR_CUDA. */
 vi_status vi_energy_noalloc(const float *chans_dev, int C, const int32_t *phi_dev,
                             const uint8_t *code_dev, int W, int H, int T, double *out_dev,
