@@ -50,6 +50,8 @@ def test_config_defaults_are_the_papers(lib):
     assert cfg.lambda_ == 50.0 and cfg.n_pm == 10 and cfg.rho == 0.5
     assert cfg.max_outer == 20 and abs(cfg.stop - 0.1 / 255) < 1e-9
     assert cfg.weighted == 1 and cfg.use_texture == 1 and cfg.storage == 0
+    # two propagation sweeps per iteration (the paper's sequential scan has one;
+    # the parallel sweep needs two to stay within 2% of its energy)
     assert cfg.mem_limit == 0 and cfg.time_subsample == 0 and cfg.sub_sweeps == 2
 
 
