@@ -62,6 +62,11 @@ NCU_STEP_TRAFFIC = {
     # 2.05 GB written over 18.33 G gathered voxels), scaled to the 48 clips by
     # gathered voxels (profiles/k_ann_step_batch_warp_batch48_8clips.md)
     ("batch48", "fp32", 2): (61.89e9 + 2.045e9) / 18.33e9,
+    # 1,800 launches of one batch step of the first 14 clips with FP16
+    # storage (142.1 GB read + 9.68 GB written over 43.17 G gathered voxels:
+    # 39.45 G from FP32 channels, 3.71 G from FP16 copies), scaled the same way
+    # (profiles/k_ann_step_batch_warp_batch48_14clips_fp16.md)
+    ("batch48", "fp16", 2): (142.10e9 + 9.678e9) / 43.166e9,
 }
 
 # What the ncu counters of the step kernel show binds it (the roofline object
