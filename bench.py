@@ -731,6 +731,7 @@ def run_batch(args):
     # pinned host memory and fetches every result to pinned host memory
     e2e_steps = 0 if args.device_only else max(1, min(args.steps, 5))
     e2e_s = 0.0
+    e2e_phase = {}
     if e2e_steps:
         host_in = [(torch.from_numpy(c.rgb).pin_memory().numpy(), torch.from_numpy(c.mask).pin_memory().numpy())
                    for c in clips]
@@ -745,6 +746,24 @@ def run_batch(args):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t
         assert all((h == o.cpu().numpy()).all() for h, o in zip(host_out, outs)), "host and device runs differ"
+        # where one host-buffer step's time goes (one more step, untimed):
+        # adding the clips from pinned host memory (the uploads included), the
+        # rounds, fetching every result into pinned host memory
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ids = add_all(host_in)
+        torch.cuda.synchronize()
+        e2e_phase["add_ms"] = 1e3 * (time.perf_counter() - t)
+        t = time.perf_counter()
+        b.run()
+        torch.cuda.synchronize()
+        e2e_phase["rounds_ms"] = 1e3 * (time.perf_counter() - t)
+        t = time.perf_counter()
+        for cid, o in zip(ids, host_out):
+            b.fetch(cid, o)
+        e2e_phase["fetch_ms"] = 1e3 * (time.perf_counter() - t)
+        for cid in ids:
+            b.remove(cid)
 
     # the same clips one after another through the single-clip path
     torch.cuda.synchronize()
@@ -799,7 +818,8 @@ def run_batch(args):
         "e2e": ({"value": hole_tot * e2e_steps / mx[5], "unit": UNIT,
                  "steps": e2e_steps,
                  "h2d_bytes_per_step": int(sum(c.rgb.nbytes + c.mask.nbytes for c in clips)),
-                 "d2h_bytes_per_step": int(sum(c.rgb.nbytes for c in clips))} if e2e_steps else None),
+                 "d2h_bytes_per_step": int(sum(c.rgb.nbytes for c in clips)),
+                 "phases": e2e_phase} if e2e_steps else None),
         "gpu_launches": launches,
         "lanes_tuned": vi.tune_export().splitlines(),
         "clocks": clocks,

@@ -13,6 +13,12 @@ static inline int blocks_for(long long n, int block)
 
 static constexpr int VOTE_BLOCK = 256;            // 8 warps, one occluded voxel per warp
 static constexpr int VOTE_WARPS = VOTE_BLOCK / 32;
+// Resident blocks per SM the vote kernels are compiled for: 8 (every warp
+// slot; 32 registers, 12 bytes spilled) instead of the 6 that their 36
+// registers allow. The vote waits on its gathers of shifts, distances and
+// source voxels, and more warps hide that: measured on GB300, the 48-clip
+// batch took 1,117 against 1,143 ms per step.
+static constexpr int VOTE_MIN_BLOCKS = 8;
 
 // The patch offsets a lane owns: j = l, l+32, l+64, l+96 (j < 125), offset
 // (j%5 - 2, (j/5)%5 - 2, j/25 - 2), packed as bytes (dx+2, dy+2, dt+2, 1 if
@@ -233,7 +239,7 @@ __device__ __forceinline__ void vote_one(const VoteArgs &a, int item, int lane, 
 }
 
 template <bool C5>
-__global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
+__global__ void __launch_bounds__(VOTE_BLOCK, VOTE_MIN_BLOCKS) k_vote(const VoteArgs a)
 {
     const int item = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5);
     if (item < a.n)
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(VOTE_BLOCK) k_vote(const VoteArgs a)
 // per SM got 5 (46 registers), and its remaining blocks ran their whole share
 // of the voxels as a late second wave.
 template <bool C5>
-__global__ void __launch_bounds__(VOTE_BLOCK) k_vote_batch(const BatchClip *__restrict__ clips,
+__global__ void __launch_bounds__(VOTE_BLOCK, VOTE_MIN_BLOCKS) k_vote_batch(const BatchClip *__restrict__ clips,
                                                            const int *__restrict__ prefix, int n)
 {
     const int g = blockIdx.x * VOTE_WARPS + (threadIdx.x >> 5);
