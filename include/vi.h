@@ -31,6 +31,12 @@
  *    ptr_is_device = 1 they are device memory of the context's device. The
  *    caller owns every buffer it passes; the library copies what it keeps.
  *    The context owns all device state until vi_ctx_destroy.
+ *  - The video of vi_upload (and the batch and server calls that take one) and
+ *    the result of vi_fetch_result move between host and device by kernels
+ *    that read or write the host buffer through its device address when it is
+ *    registered with CUDA (cudaHostAlloc, cudaMallocHost, cudaHostRegister,
+ *    or a framework's pinned memory), and by the copy engine otherwise; the
+ *    results are the same either way.
  *  - Calls are ordered on the context's stream. Calls that return data to a
  *    host pointer synchronise that stream; the others are asynchronous unless
  *    stated otherwise.

@@ -174,6 +174,9 @@ void launch_onion_targets(LevelView L, const uint8_t *hp, const uint8_t *layer, 
 void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st);
 // Packing helpers between the library layout and the ABI layout.
 void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st);
+// dst[0 .. n) = src[0 .. n) by a kernel; both must be device-accessible
+// (device memory, or registered host memory through its device address).
+void launch_copy_bytes(void *dst, const void *src, long long n, cudaStream_t st);
 void launch_pack_voxels(LevelView L, const int *list, int n, float4 *buf4, float *buf1, bool unpack,
                         cudaStream_t st);
 void launch_get_channels(LevelView L, float *out, int C, cudaStream_t st);

@@ -592,21 +592,64 @@ void launch_count(const uint8_t *flags, int V, int *count_dev, cudaStream_t st)
 }
 
 // Layout packing: [V] float4 (+ float) <-> [V][C] float32.
+// One output float per thread, so that a warp writes 128 consecutive bytes:
+// the destination may be pinned host memory written across the chip-to-chip
+// link, where whole lines matter (three threads read each source voxel, from
+// L1).
 __global__ void k_pack_rgb(LevelView L, float *__restrict__ rgb)
 {
-    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < L.V;
-         v += (long long)gridDim.x * blockDim.x) {
-        const float4 a = L.x4[v];
-        rgb[3 * v] = a.x;
-        rgb[3 * v + 1] = a.y;
-        rgb[3 * v + 2] = a.z;
+    const long long n = 3ll * L.V;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
+         o += (long long)gridDim.x * blockDim.x) {
+        const long long v = o / 3;
+        const int c = (int)(o - 3 * v);
+        const float *a = reinterpret_cast<const float *>(L.x4 + v);
+        rgb[o] = a[c];
     }
 }
 
 void launch_pack_rgb(LevelView L, float *rgb, cudaStream_t st)
 {
+    long long g = (3ll * L.V + 255) / 256;
+    if (g > 152 * 16)
+        g = 152 * 16;
+    if (g < 1)
+        g = 1;
     VI_COUNT_LAUNCH();
-    k_pack_rgb<<<blocks_for(L.V, 256), 256, 0, st>>>(L, rgb);
+    k_pack_rgb<<<(int)g, 256, 0, st>>>(L, rgb);
+}
+
+// dst[0 .. n) = src[0 .. n): 16 bytes per thread and iteration when both
+// addresses are 16-byte aligned, else single bytes. src may be pinned host
+// memory read across the chip-to-chip link: many loads in flight, rather than
+// the copy engine's one stream of page translations.
+__global__ void k_copy_bytes(uint8_t *__restrict__ dst, const uint8_t *__restrict__ src, long long n, bool wide)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long done = 0;
+    if (wide) {
+        const long long n16 = n / 16;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (long long i = t0; i < n16; i += stride)
+            d4[i] = s4[i];
+        done = n16 * 16;
+    }
+    for (long long i = done + t0; i < n; i += stride)
+        dst[i] = src[i];
+}
+
+void launch_copy_bytes(void *dst, const void *src, long long n, cudaStream_t st)
+{
+    if (n <= 0)
+        return;
+    const bool wide = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) == 0;
+    long long g = (wide ? n / 16 : n) / 256 + 1;
+    if (g > 152 * 16)
+        g = 152 * 16;
+    VI_COUNT_LAUNCH();
+    k_copy_bytes<<<(int)g, 256, 0, st>>>(static_cast<uint8_t *>(dst), static_cast<const uint8_t *>(src), n, wide);
 }
 
 // The channels of list[0 .. n) packed into buf4[0 .. n) (c0..c3) and
