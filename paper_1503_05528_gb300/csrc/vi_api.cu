@@ -576,7 +576,7 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
 // the GPU has worked on its own memory for a while, the copy engine's first
 // pass over the host pages is slow (measured on GB300: 57 ms to fetch 1.96 GB
 // into pinned buffers after a 48-clip batch, 5 ms from device to device).
-static void *mapped_host(const void *p)
+static void *mapped_host_byte(const void *p)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -586,11 +586,24 @@ static void *mapped_host(const void *p)
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// The device address of a registered host buffer of `bytes` bytes, when its
+// first and its last byte are both registered and map to addresses `bytes - 1`
+// apart; nullptr otherwise (the copy engine then moves it).
+static void *mapped_host(const void *p, size_t bytes)
+{
+    void *d = mapped_host_byte(p);
+    if (!d || bytes == 0)
+        return d;
+    const void *last = static_cast<const char *>(p) + (bytes - 1);
+    void *dl = mapped_host_byte(last);
+    return dl == static_cast<char *>(d) + (bytes - 1) ? d : nullptr;
+}
+
 // bytes from a caller's buffer (device memory, or host memory) into dst.
 static cudaError_t copy_in(void *dst, const void *src, size_t bytes, int ptr_is_device, cudaStream_t st)
 {
     if (!ptr_is_device) {
-        if (const void *mapped = mapped_host(src)) {
+        if (const void *mapped = mapped_host(src, bytes)) {
             launch_copy_bytes(dst, mapped, (long long)bytes, st);
             return cudaGetLastError();
         }
@@ -1516,7 +1529,7 @@ vi_status vi_fetch_result(vi_ctx *ctx, float *rgb_out, int ptr_is_device)
         CK_LAUNCH();
         return VI_OK;
     }
-    if (void *mapped = mapped_host(rgb_out)) {
+    if (void *mapped = mapped_host(rgb_out, bytes)) {
         // registered host memory: packed straight into it
         launch_pack_rgb(l.view(), static_cast<float *>(mapped), ctx->stream);
         CK_LAUNCH();
