@@ -183,7 +183,10 @@ size_t vi_footprint_bytes(const vi_config *cfg, int W, int H, int T, long long h
 
 /* Copies a video and its occlusion mask into the context and allocates the
  * pyramid. rgb: [T][H][W][3] float32; mask: [T][H][W] uint8. Values of rgb
- * under the mask are never read. Replaces any previous upload.
+ * under the mask are never read. Replaces any previous upload. From host
+ * memory it returns once both buffers have been read (the context's stream
+ * is synchronised), so the caller may reuse them at once; from device memory
+ * it is stream-ordered like the other calls.
  * Errors: VI_ERR_ARG (sizes, null), VI_ERR_OOM, VI_ERR_CUDA. */
 vi_status vi_upload(vi_ctx *ctx, const float *rgb, const uint8_t *mask, int W, int H, int T,
                     int ptr_is_device);

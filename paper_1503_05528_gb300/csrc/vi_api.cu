@@ -631,6 +631,8 @@ static vi_status vi_upload_body(vi_ctx *ctx, const float *rgb, const uint8_t *ma
     TRY(dalloc(ctx, &ctx->mask, V0));
     CK(copy_in(ctx->rgb, rgb, V0 * 3 * sizeof(float), ptr_is_device, ctx->stream));
     CK(copy_in(ctx->mask, mask, V0, ptr_is_device, ctx->stream));
+    if (!ptr_is_device)
+        CK(cudaStreamSynchronize(ctx->stream));   // the caller may reuse its host buffers on return
 
     int L = ctx->cfg.levels;
     if (L <= 0) {
