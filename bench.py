@@ -19,7 +19,8 @@ the timed region starts; `evals_per_s` is the patch-distance evaluation rate
 of the same run (every candidate of Algorithm 1 that lands in D~, whether or
 not exact pruning let it skip its gather). `e2e` is the same metric with the
 inputs uploaded from pinned host buffers and every result fetched to host
-memory inside the timed region. `roofline` is the PatchMatch step kernel's
+memory inside the timed region (`e2e.phases`: one more such step, untimed,
+split into adding the clips, the rounds and fetching). `roofline` is the PatchMatch step kernel's
 gathered source bytes over its CUDA-event time against the measured HBM copy
 bandwidth, with the per-evaluation count beside it. `cpu_baseline` times the
 CPU oracle on the host cores, one clip per core, on a bounded sample of the
